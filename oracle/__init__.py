@@ -1,0 +1,237 @@
+"""CPU oracle for the signal-separation path (arXiv 2411.09515).
+
+TEST INFRASTRUCTURE ONLY: the plain FP64 statement of what the GPU library
+computes. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package. It shares no code with
+``paper_2411_09515_gb300`` and never imports it.
+
+The arithmetic lives in ``sep_oracle.c`` (compiled to
+``oracle/_build/liboracle.so``); this module only marshals numpy arrays.
+Every function's docstring names the passage of the paper it follows; the
+C source states the definitions in full.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build_cmd():
+    # -ffp-contract=off: no fused multiply-add anywhere (x86 and Arm alike);
+    # no -ffast-math: IEEE semantics for the binary32 correction.
+    return ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
+            "-Wall", os.path.join(_HERE, "sep_oracle.c"), "-lm", "-o", _SO]
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    src = os.path.join(_HERE, "sep_oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.run(build_cmd(), check=True)
+    return _SO
+
+
+class Geom(C.Structure):
+    _fields_ = [
+        ("rows", C.c_int32), ("cols", C.c_int32),
+        ("pixel_y", C.c_double), ("pixel_x", C.c_double),
+        ("dist", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+        ("wavelength", C.c_double),
+        ("unit", C.c_int32), ("nbins", C.c_int32), ("split", C.c_int32),
+        ("lo", C.c_double), ("hi", C.c_double),
+    ]
+
+
+class Peak(C.Structure):
+    _fields_ = [("idx", C.c_int32), ("y", C.c_double), ("x", C.c_double), ("I", C.c_double),
+                ("sigma", C.c_double), ("npix", C.c_int32)]
+
+
+PEAK_DTYPE = np.dtype([("idx", "<i4"), ("y", "<f8"), ("x", "<f8"), ("I", "<f8"), ("sigma", "<f8"),
+                       ("npix", "<i4")], align=True)
+assert PEAK_DTYPE.itemsize == C.sizeof(Peak)
+
+vp = C.c_void_p
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            build()
+        L = C.CDLL(_SO)
+        L.oracle_jf_photons.argtypes = [C.c_int64, vp, vp, vp, C.c_int64, vp]
+        L.oracle_jf_photons.restype = None
+        L.oracle_unit_range.argtypes = [C.POINTER(Geom), vp, vp, vp]
+        L.oracle_unit_range.restype = None
+        L.oracle_weights.argtypes = [C.POINTER(Geom), vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.oracle_weights.restype = C.c_int64
+        L.oracle_integrate_clip.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, C.c_int32, vp, vp,
+                                            C.c_int32, C.c_double, vp, vp, vp, vp, vp, vp]
+        L.oracle_integrate_clip.restype = C.c_int
+        L.oracle_moments_subset.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp]
+        L.oracle_moments_subset.restype = None
+        L.oracle_sparsify.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int64, vp, vp]
+        L.oracle_sparsify.restype = C.c_int64
+        L.oracle_peaks.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, C.c_double, C.c_int32,
+                                   C.c_int32, C.c_int64, vp]
+        L.oracle_peaks.restype = C.c_int64
+        L.oracle_process_frames.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, vp, C.c_int32,
+                                            C.c_int32, C.c_int32, vp, vp, vp, vp, C.c_int32, C.c_double,
+                                            C.c_double, C.c_int32, C.c_int32, vp, vp, vp, vp, C.c_int32]
+        L.oracle_process_frames.restype = C.c_int
+        L.oracle_max_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(vp)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def geom_of(det) -> Geom:
+    """Oracle geometry from a ``synth.Detector`` description."""
+    lo, hi = det.range
+    return Geom(det.rows, det.cols, det.pixel_m[0], det.pixel_m[1], det.dist_m, det.center_px[0],
+                det.center_px[1], det.wavelength_m, det.unit, det.nbins, det.split, lo, hi)
+
+
+def jf_photons(raw, ped, gain):
+    """Detector correction of Section 1.2 (dark subtraction of Eq. 1 and the
+    gain of the level in the raw word's top two bits), binary32."""
+    raw = _c(raw, np.uint16).reshape(-1)
+    n = raw.size
+    ped = _c(ped, np.float32).reshape(3, -1)
+    gain = _c(gain, np.float32).reshape(3, -1)
+    assert ped.shape[1] == n and gain.shape[1] == n
+    out = np.empty(n, np.float32)
+    lib().oracle_jf_photons(n, _p(raw), _p(ped), _p(gain), n, _p(out))
+    return out
+
+
+def unit_range(det, mask=None):
+    g = geom_of(det)
+    lo, hi = C.c_double(), C.c_double()
+    lib().oracle_unit_range(C.byref(g), _p(_c(mask, np.uint8)), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+class Weights:
+    """Pixel-to-bin coefficients c_{i,r} of Section 2.2 (area fraction by
+    s x s sub-pixel centres), pixel-major."""
+
+    def __init__(self, pix, b, c, bin_of_pixel, rng, nbins, npix):
+        self.pix, self.bin, self.c = pix, b, c
+        self.bin_of_pixel, self.range, self.nbins, self.npix = bin_of_pixel, rng, nbins, npix
+
+
+def weights(det, mask=None) -> Weights:
+    g = geom_of(det)
+    m = _c(mask, np.uint8)
+    npix = det.rows * det.cols
+    cap = npix * det.split * det.split
+    pix = np.empty(cap, np.int32)
+    b = np.empty(cap, np.int32)
+    c = np.empty(cap, np.float64)
+    bop = np.empty(npix, np.int32)
+    rng = np.empty(2, np.float64)
+    n = lib().oracle_weights(C.byref(g), _p(m), cap, _p(pix), _p(b), _p(c), _p(bop), _p(rng))
+    assert n <= cap
+    return Weights(pix[:n].copy(), b[:n].copy(), c[:n].copy(), bop, (rng[0], rng[1]), det.nbins, npix)
+
+
+def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=False):
+    """Integration (Eqs. 2, 8-13) and sigma-clipping (Eq. 19, Section 2.4) of one frame.
+
+    Returns dict(mean, sigma, count, iters, band[, keep]) per bin."""
+    sig = _c(signal, np.float32).reshape(-1)
+    nrm = _c(norm, np.float32)
+    B = W.nbins
+    out = {"mean": np.zeros(B), "sigma": np.zeros(B), "count": np.zeros(B, np.int32),
+           "iters": np.zeros(B, np.int32), "band": np.zeros(B)}
+    keep = np.zeros(W.pix.size, np.uint8) if want_keep else None
+    rc = lib().oracle_integrate_clip(W.npix, W.pix.size, _p(W.pix), _p(W.bin), _p(W.c), B, _p(sig),
+                                     _p(nrm), n_iter, k, _p(out["mean"]), _p(out["sigma"]),
+                                     _p(out["count"]), _p(out["iters"]), _p(out["band"]), _p(keep))
+    assert rc == 0
+    if want_keep:
+        out["keep"] = keep
+    return out
+
+
+def moments_subset(pix, c, sel, signal, norm=None):
+    """(mu, sigma, count) of an explicit set of entries (Eqs. 8-13)."""
+    pix = _c(pix, np.int32)
+    c = _c(c, np.float64)
+    sel = _c(sel, np.uint8)
+    o = np.zeros(3)
+    lib().oracle_moments_subset(pix.size, _p(pix), _p(c), _p(sel), _p(_c(signal, np.float32)),
+                                _p(_c(norm, np.float32)), _p(o))
+    return o[0], o[1], int(o[2])
+
+
+def sparsify(W: Weights, signal, mean, sigma, k_pick=3.0, norm=None):
+    """Pixels above mu + k_pick sigma of their radial bin (Section 3), ascending."""
+    sig = _c(signal, np.float32).reshape(-1)
+    mean = _c(mean, np.float64)
+    sigma = _c(sigma, np.float64)
+    nrm = _c(norm, np.float32)
+    n = lib().oracle_sparsify(W.npix, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick,
+                              0, None, None)
+    idx = np.empty(n, np.int32)
+    val = np.empty(n, np.float64)
+    lib().oracle_sparsify(W.npix, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, n,
+                          _p(idx), _p(val))
+    return idx, val
+
+
+def peaks(det, W: Weights, signal, mean, sigma, k_pick=3.0, patch=3, min_count=3, norm=None):
+    """Peak picking of Section 4 over the kept pixels; structured array."""
+    sig = _c(signal, np.float32).reshape(-1)
+    mean = _c(mean, np.float64)
+    sigma = _c(sigma, np.float64)
+    nrm = _c(norm, np.float32)
+    args = (det.rows, det.cols, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, patch,
+            min_count)
+    n = lib().oracle_peaks(*args, 0, None)
+    out = np.zeros(n, PEAK_DTYPE)
+    lib().oracle_peaks(*args, n, _p(out))
+    return out
+
+
+def process_frames(det, W: Weights, frames, calib=None, norm=None, n_iter=5, k_clip=3.0, k_pick=3.0,
+                   patch=3, min_count=3, threads=0):
+    """Whole frames end to end: per-bin mean/sigma, kept count and peak count."""
+    F = frames.shape[0]
+    is_raw = frames.dtype == np.uint16
+    fr = np.ascontiguousarray(frames)
+    ped = gain = None
+    if is_raw:
+        ped = _c(calib[0], np.float32)
+        gain = _c(calib[1], np.float32)
+    mean = np.zeros((F, W.nbins))
+    sigma = np.zeros((F, W.nbins))
+    nk = np.zeros(F, np.int32)
+    npk = np.zeros(F, np.int32)
+    rc = lib().oracle_process_frames(det.rows, det.cols, W.pix.size, _p(W.pix), _p(W.bin), _p(W.c),
+                                     _p(W.bin_of_pixel), W.nbins, F, int(is_raw), _p(fr), _p(ped), _p(gain),
+                                     _p(_c(norm, np.float32)), n_iter, k_clip, k_pick, patch, min_count,
+                                     _p(mean), _p(sigma), _p(nk), _p(npk), threads)
+    assert rc == 0
+    return mean, sigma, nk, npk
+
+
+def max_threads() -> int:
+    return lib().oracle_max_threads()
