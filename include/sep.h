@@ -1,0 +1,231 @@
+/*
+ * sep.h - C ABI of libsep, the GB300 (sm_103a) signal-separation library.
+ *
+ * The library implements the per-frame path of Kieffer et al., "Application
+ * of signal separation to diffraction image compression and serial
+ * crystallography" (arXiv 2411.09515): Jungfrau detector correction,
+ * CSR azimuthal integration with per-bin weighted moments, iterative
+ * sigma-clipping, sparsification and peak picking.
+ *
+ * Conventions (every function):
+ *  - Frame, output and count buffers passed to compute calls are DEVICE
+ *    pointers owned by the caller. Host pointers are only accepted where a
+ *    parameter says "_host".
+ *  - Handles (sep_ctx, sep_csr, sep_calib) are owned by the library and freed
+ *    with the matching *_destroy; destroying NULL is a no-op.
+ *  - Compute calls are asynchronous on the given stream (a cudaStream_t;
+ *    NULL = the legacy default stream). They return a sep_status for errors
+ *    detected on the host before any launch (bad argument, CUDA launch
+ *    error). Conditions found on the device (capacity exceeded, a bounded
+ *    wait that gave up) are OR-ed into the context's device status word,
+ *    read and cleared with sep_get_device_status.
+ *  - sep_last_error(ctx) describes the last host-side failure on ctx.
+ *  - The library never exits, aborts or traps.
+ *  - Not thread-safe per context: calls on one sep_ctx must not overlap in
+ *    host threads.
+ */
+#ifndef SEP_H_
+#define SEP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int32_t sep_status;
+#define SEP_OK            0
+#define SEP_ERR_ARG       1   /* invalid argument (NULL, size, range, mismatch) */
+#define SEP_ERR_CUDA      2   /* a CUDA runtime call or launch failed */
+#define SEP_ERR_OOM       3   /* device or host allocation failed */
+#define SEP_ERR_CAPACITY  4   /* device flag: more results than the output capacity */
+#define SEP_ERR_TIMEOUT   5   /* device flag: a bounded wait gave up */
+#define SEP_ERR_CSR       6   /* CSR invalid or a bin too large for the kernels */
+#define SEP_ERR_STATE     7   /* handle used with the wrong context/device */
+
+/* device status word bits (sep_get_device_status) */
+#define SEP_DEV_CAPACITY  0x1 /* some frame had more kept pixels or peaks than capacity */
+#define SEP_DEV_TIMEOUT   0x2
+
+/* ---- enums ------------------------------------------------------------- */
+#define SEP_UNIT_2TH_DEG  0   /* scattering angle 2theta, degrees */
+#define SEP_UNIT_Q_NM     1   /* q = 4 pi sin(theta) / lambda, nm^-1 */
+#define SEP_UNIT_R_MM     2   /* radius on the detector, mm */
+
+#define SEP_DTYPE_F32     0   /* float32 corrected signal (photons) per pixel */
+#define SEP_DTYPE_U16_JF  1   /* raw Jungfrau word: 2 gain bits (15:14) + 14-bit ADC */
+
+/* Precision of the per-bin moments (Section 2.2's reductions):
+ * PLAIN: plain FP32 per-thread sums, FP32 merges and finalisation.
+ * KAHAN: Kahan-compensated FP32 per-thread sums, error-free (two-sum) FP32
+ *        warp merges, FP32 cross-warp merge and finalisation.
+ * FP64MERGE: as KAHAN up to the warp, then FP64 cross-warp merge and FP64
+ *        mean / deviation / clip bounds (the default). */
+#define SEP_PREC_PLAIN     0
+#define SEP_PREC_KAHAN     1
+#define SEP_PREC_FP64MERGE 2
+
+/* ---- opaque handles ---------------------------------------------------- */
+typedef struct sep_ctx sep_ctx;
+typedef struct sep_csr sep_csr;
+typedef struct sep_calib sep_calib;
+typedef struct CUstream_st* sep_stream; /* identical to cudaStream_t */
+
+/* ---- plain structs ----------------------------------------------------- */
+/*
+ * Flat detector normal to the beam (Section 2.2). Pixel (row, col) covers
+ * [row, row+1) x [col, col+1) in pixel units; its centre is (row+0.5, col+0.5).
+ */
+typedef struct {
+  int32_t rows, cols;        /* image shape, rows * cols <= SEP_MAX_PIXELS */
+  double pixel_m[2];         /* pixel size (y, x) in metres */
+  double dist_m;             /* sample-detector distance, metres */
+  double center_px[2];       /* beam centre (x = column, y = row) in pixels */
+  double wavelength_m;       /* metres (used by SEP_UNIT_Q_NM) */
+  int32_t unit;              /* SEP_UNIT_* radial unit of the bins */
+  int32_t nbins;             /* number of radial bins, 1 .. SEP_MAX_BINS */
+  int32_t split;             /* 1: no splitting; 2: 2 x 2 sub-pixel centres */
+  double range[2];           /* [lo, hi] in the unit; NaN = automatic (min/max over valid sub-pixel centres) */
+} sep_geometry;
+
+#define SEP_MAX_PIXELS (1 << 25)
+#define SEP_MAX_BINS   32767
+
+/* Parameters of clipping and of the two consumers (Sections 2.4, 3, 4). */
+typedef struct {
+  int32_t n_iter;            /* maximum rejection steps (Section 2.4), >= 0 */
+  float k_clip;              /* clip cut-off n of Eq. 19, > 0 */
+  float k_pick;              /* sparsification cut-off (Section 3), >= 0 */
+  int32_t patch;             /* peak patch side, odd, 1 .. 15 (Section 4) */
+  int32_t min_count;         /* minimum kept pixels in the patch, >= 1 */
+  int32_t precision;         /* SEP_PREC_* */
+  int32_t reserved[4];       /* must be 0 */
+} sep_params;
+
+/* One peak (Section 4). y, x: centroid in pixel units (row, column axes,
+ * pixel centres at idx + 0.5); I: background-subtracted sum over the kept
+ * patch pixels; sigma: propagated deviation sqrt(sum sigma_b^2). */
+typedef struct {
+  int32_t idx;               /* pixel index row * cols + col of the local maximum */
+  float y, x, I, sigma;
+  int32_t npix;              /* kept pixels in the patch */
+} sep_peak;
+
+/* ---- context ------------------------------------------------------------ */
+const char* sep_version(void);
+
+/* Create a context on CUDA device `device`. Allocates a 4-byte device status word. */
+sep_status sep_ctx_create(int32_t device, sep_ctx** out);
+void sep_ctx_destroy(sep_ctx* ctx);
+/* Message of the last host-side failure on ctx (never NULL; "" if none). */
+const char* sep_last_error(const sep_ctx* ctx);
+/* Wait for `stream`, copy the device status word (SEP_DEV_* bits) to
+ * *status_out and clear it. */
+sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* status_out);
+
+/* ---- integration matrix (Section 2.2) ------------------------------------ */
+/*
+ * Build the CSR matrix of coefficients c_{i,r} (the fraction of pixel i in
+ * radial bin r, Section 2.2, measured by split x split sub-pixel centres)
+ * on the host and upload it to the context's device.
+ *  mask_host: rows*cols bytes, nonzero = masked pixel (never used); may be NULL.
+ *  norm_host: rows*cols floats, the normalisation of Eq. 1 (denominator);
+ *             may be NULL (= 1 everywhere). Must be > 0 on valid pixels.
+ * Rows of the matrix are bins; columns within a row ascend. Every valid
+ * pixel also gets its centre bin (the bin its threshold is taken from in
+ * sparsification, Section 3); where that bin has no coefficient of the
+ * pixel, an entry of weight 0 is added for it.
+ * ctx may be NULL: the matrix is then built on the host only, for
+ * inspection with sep_csr_info / sep_csr_export; compute calls need a matrix
+ * built with a context (SEP_ERR_STATE otherwise).
+ * Errors: SEP_ERR_ARG for invalid geometry; SEP_ERR_OOM.
+ */
+sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* mask_host,
+                         const float* norm_host, sep_csr** out);
+void sep_csr_destroy(sep_csr* csr);
+/* Sizes: pixels, bins, nonzeros, largest row; range[2] as used. Any out pointer may be NULL. */
+sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64_t* nnz,
+                        int32_t* max_row, double* range);
+/* Host copies for inspection (any pointer may be NULL):
+ * rowptr [nbins+1], col [nnz], coef [nnz] (c_{i,r}, 0 for centre-only entries),
+ * bin_of_pixel [npix] (-1 = masked), bin_centers [nbins]. */
+sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, float* coef,
+                          int32_t* bin_of_pixel, float* bin_centers);
+
+/* ---- detector calibration (Section 1.2) ---------------------------------- */
+/*
+ * Upload per-pixel pedestals and gains of the three Jungfrau gain levels,
+ * plane-major: ped_host[g * npix + i], gain_host[g * npix + i], g = 0, 1, 2.
+ * A raw word with gain code 0 uses level 0, code 1 level 1, codes 2 and 3
+ * level 2. The corrected value is RN32(RN32(adc - ped) / gain).
+ */
+sep_status sep_calib_create(sep_ctx* ctx, const sep_csr* csr, const float* ped_host,
+                            const float* gain_host, sep_calib** out);
+void sep_calib_destroy(sep_calib* calib);
+
+/* ---- compute calls -------------------------------------------------------- */
+/*
+ * Integrate and sigma-clip n_frames frames (Eqs. 2, 8-13, 19; Section 2.4).
+ *  frames_dev: [n_frames][npix] of dtype (uint16 raw words need calib,
+ *              float32 ignores calib).
+ *  Outputs (device, [n_frames][nbins]): mean_dev (clipped weighted mean),
+ *  sigma_dev (clipped deviation sqrt(VV / OmegaOmega), Eq. 13), count_dev
+ *  (entries of nonzero weight in the final set).
+ *  bounds_dev: optional [n_frames][nbins][2] float32 interval [L, H] such
+ *  that the final set is every entry with L <= value <= H; may be NULL.
+ *  iters_dev: optional [n_frames][nbins] int32 rejection steps taken; may be NULL.
+ */
+sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
+                              const void* frames_dev, int32_t dtype, int32_t n_frames,
+                              const sep_params* params, float* mean_dev, float* sigma_dev,
+                              int32_t* count_dev, float* bounds_dev, int32_t* iters_dev,
+                              sep_stream stream);
+
+/*
+ * Sparsify (Section 3): keep valid pixel i when value_i > mean_b + k_pick sigma_b,
+ * b = centre bin of i. Writes, per frame, the first `capacity` kept pixels in
+ * ascending index order: idx_dev [n_frames][capacity] (int32) and val_dev
+ * [n_frames][capacity] (float32 value), and the true count n_kept_dev
+ * [n_frames]. A count above capacity sets SEP_DEV_CAPACITY.
+ */
+sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
+                        const void* frames_dev, int32_t dtype, int32_t n_frames,
+                        const sep_params* params, const float* mean_dev, const float* sigma_dev,
+                        int32_t* idx_dev, float* val_dev, int64_t capacity, int32_t* n_kept_dev,
+                        sep_stream stream);
+
+/*
+ * Peak picking (Section 4) over the kept pixels given by a previous
+ * sep_sparsify (idx_dev, n_kept_dev, kept_capacity). A kept pixel is a peak
+ * when it is the maximum of its patch (ties: the lowest index wins) and at
+ * least min_count patch pixels are kept. Writes the first `capacity` peaks
+ * per frame in ascending index order to peaks_dev [n_frames][capacity] and
+ * the true count to n_peaks_dev [n_frames].
+ */
+sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
+                        const void* frames_dev, int32_t dtype, int32_t n_frames,
+                        const sep_params* params, const float* mean_dev, const float* sigma_dev,
+                        const int32_t* idx_dev, const int32_t* n_kept_dev, int64_t kept_capacity,
+                        sep_peak* peaks_dev, int64_t capacity, int32_t* n_peaks_dev,
+                        sep_stream stream);
+
+/*
+ * The whole path on a batch in one call: integrate + clip, sparsify and peak
+ * picking, with the kept-pixel map passed between the steps on the device.
+ * Outputs as in the three calls above. The launch sequence is captured once
+ * per (csr, calib, dtype, n_frames, capacities, params) into a CUDA graph and
+ * replayed on later calls with the same shapes (use_graph = 1).
+ */
+sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
+                             const void* frames_dev, int32_t dtype, int32_t n_frames,
+                             const sep_params* params, float* mean_dev, float* sigma_dev,
+                             int32_t* count_dev, int32_t* idx_dev, float* val_dev,
+                             int64_t kept_capacity, int32_t* n_kept_dev, sep_peak* peaks_dev,
+                             int64_t peak_capacity, int32_t* n_peaks_dev, int32_t use_graph,
+                             sep_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEP_H_ */

@@ -1,0 +1,175 @@
+"""GB300-native signal separation for diffraction frames (arXiv 2411.09515).
+
+The compute path lives in ``libsep.so`` (hand-written CUDA for sm_103a behind
+the C ABI of ``include/sep.h``); this package is the thin Python face of it:
+``_binding`` marshals arguments to the C entry points, and :class:`Separator`
+owns the handles and allocates output tensors with PyTorch.
+
+Per frame (Kieffer et al., Sections 2-4): Jungfrau correction, CSR
+azimuthal integration with weighted moments, iterative sigma-clipping,
+sparsification and peak picking.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (PEAK_DTYPE, SEP_DTYPE_F32, SEP_DTYPE_U16_JF, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN,
+                       SEP_PREC_PLAIN, SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM, SepError)
+
+__all__ = ["Separator", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
+           "SEP_PREC_PLAIN", "SEP_PREC_KAHAN", "SEP_PREC_FP64MERGE", "SEP_UNIT_2TH_DEG", "SEP_UNIT_Q_NM",
+           "SEP_UNIT_R_MM"]
+
+
+def peaks_to_numpy(peaks, n):
+    """Peak records of one frame (an int32 tensor [cap, 6]) as a structured array of the first n."""
+    a = peaks[: int(n)].contiguous().cpu().numpy()
+    return a.view(PEAK_DTYPE).reshape(-1)
+
+
+class Separator:
+    """One detector on one GPU: integration matrix, optional calibration, parameters.
+
+    geometry: dict with rows, cols, pixel_m (y, x), dist_m, center_px (x, y),
+    wavelength_m, unit, nbins, split, range (lo, hi; NaN = automatic).
+    """
+
+    def __init__(self, geometry: dict, mask=None, norm=None, calib=None, device: int = 0, n_iter=5, k_clip=3.0,
+                 k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_FP64MERGE):
+        import torch  # device memory and streams
+        self.torch = torch
+        self.device = device
+        self.ctx = B.sep_ctx_create(device)
+        g = geometry
+        self.geom = B.make_geometry(g["rows"], g["cols"], g["pixel_m"], g["dist_m"], g["center_px"],
+                                    g["wavelength_m"], g["unit"], g["nbins"], g["split"], g["range"])
+        self.csr = B.sep_build_csr(self.ctx, self.geom, mask, norm)
+        self.info = B.sep_csr_info(self.csr)
+        self.rows, self.cols = g["rows"], g["cols"]
+        self.npix = self.info["npix"]
+        self.nbins = self.info["nbins"]
+        self.calib = None
+        if calib is not None:
+            self.calib = B.sep_calib_create(self.ctx, self.csr, calib[0], calib[1])
+        self.params = B.make_params(n_iter, k_clip, k_pick, patch, min_count, precision)
+        self._outs = {}
+
+    @classmethod
+    def from_detector(cls, det, mask=None, **kw):
+        """From a ``synth.Detector``-like object (rows, cols, pixel_m, ...)."""
+        g = dict(rows=det.rows, cols=det.cols, pixel_m=det.pixel_m, dist_m=det.dist_m, center_px=det.center_px,
+                 wavelength_m=det.wavelength_m, unit=det.unit, nbins=det.nbins, split=det.split, range=det.range)
+        return cls(g, mask=mask, **kw)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.sep_calib_destroy(self.calib)
+            B.sep_csr_destroy(self.csr)
+            B.sep_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+
+    # ------------------------------------------------------------------
+    def _dtype(self, frames):
+        t = self.torch
+        if frames.dtype == t.uint16 or frames.dtype == t.int16:
+            return SEP_DTYPE_U16_JF
+        if frames.dtype == t.float32:
+            return SEP_DTYPE_F32
+        raise TypeError(f"frames must be uint16 (raw Jungfrau) or float32, not {frames.dtype}")
+
+    def _check_frames(self, frames):
+        if not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous CUDA tensor")
+        if frames.numel() % self.npix:
+            raise ValueError("frames size is not a multiple of the detector's pixel count")
+        return frames.numel() // self.npix
+
+    def export_csr(self):
+        return B.sep_csr_export(self.csr)
+
+    def integrate_clip(self, frames, bounds=False, iters=False, stream=None):
+        t = self.torch
+        F = self._check_frames(frames)
+        dev = frames.device
+        mean = t.empty((F, self.nbins), dtype=t.float32, device=dev)
+        sigma = t.empty_like(mean)
+        count = t.empty((F, self.nbins), dtype=t.int32, device=dev)
+        bnd = t.empty((F, self.nbins, 2), dtype=t.float32, device=dev) if bounds else None
+        its = t.empty((F, self.nbins), dtype=t.int32, device=dev) if iters else None
+        B.sep_integrate_clip(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, self.params, mean, sigma,
+                             count, bnd, its, stream)
+        out = {"mean": mean, "sigma": sigma, "count": count}
+        if bounds:
+            out["bounds"] = bnd
+        if iters:
+            out["iters"] = its
+        return out
+
+    def sparsify(self, frames, mean, sigma, capacity, stream=None):
+        t = self.torch
+        F = self._check_frames(frames)
+        dev = frames.device
+        idx = t.empty((F, capacity), dtype=t.int32, device=dev)
+        val = t.empty((F, capacity), dtype=t.float32, device=dev)
+        n_kept = t.empty(F, dtype=t.int32, device=dev)
+        B.sep_sparsify(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, self.params, mean, sigma, idx,
+                       val, capacity, n_kept, stream)
+        return {"idx": idx, "val": val, "n_kept": n_kept}
+
+    def peakfind(self, frames, mean, sigma, idx, n_kept, capacity, stream=None):
+        t = self.torch
+        F = self._check_frames(frames)
+        dev = frames.device
+        peaks = t.empty((F, capacity, 6), dtype=t.int32, device=dev)
+        n_peaks = t.empty(F, dtype=t.int32, device=dev)
+        B.sep_peakfind(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, self.params, mean, sigma, idx,
+                       n_kept, idx.shape[1], peaks, capacity, n_peaks, stream)
+        return {"peaks": peaks, "n_peaks": n_peaks}
+
+    def alloc_outputs(self, F, kept_capacity, peak_capacity, device=None):
+        t = self.torch
+        dev = device if device is not None else t.device("cuda", self.device)
+        return {"mean": t.empty((F, self.nbins), dtype=t.float32, device=dev),
+                "sigma": t.empty((F, self.nbins), dtype=t.float32, device=dev),
+                "count": t.empty((F, self.nbins), dtype=t.int32, device=dev),
+                "idx": t.empty((F, kept_capacity), dtype=t.int32, device=dev),
+                "val": t.empty((F, kept_capacity), dtype=t.float32, device=dev),
+                "n_kept": t.empty(F, dtype=t.int32, device=dev),
+                "peaks": t.empty((F, peak_capacity, 6), dtype=t.int32, device=dev),
+                "n_peaks": t.empty(F, dtype=t.int32, device=dev)}
+
+    def process_batch(self, frames, kept_capacity, peak_capacity, out=None, use_graph=True, stream=None):
+        """The whole path (integrate + clip, sparsify, peaks) on a device batch."""
+        F = self._check_frames(frames)
+        o = out if out is not None else self.alloc_outputs(F, kept_capacity, peak_capacity, frames.device)
+        B.sep_process_batch(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, self.params, o["mean"],
+                            o["sigma"], o["count"], o["idx"], o["val"], kept_capacity, o["n_kept"], o["peaks"],
+                            peak_capacity, o["n_peaks"], int(use_graph), stream)
+        return o
+
+    def process_host(self, frames_host, dev_frames, out, host_out, kept_capacity, peak_capacity, stream=None):
+        """End to end from host memory: copy the batch in (pinned host ->
+        device), run the path, copy the per-frame results back (counts,
+        background profiles, kept lists and peaks)."""
+        t = self.torch
+        s = stream if stream is not None else t.cuda.current_stream()
+        with t.cuda.stream(s):
+            dev_frames.copy_(frames_host, non_blocking=True)
+            self.process_batch(dev_frames, kept_capacity, peak_capacity, out=out, stream=s)
+            for k, v in host_out.items():
+                v.copy_(out[k], non_blocking=True)
+        return host_out
+
+    def device_status(self, stream=None):
+        return B.sep_get_device_status(self.ctx, stream)

@@ -1,0 +1,235 @@
+"""ctypes binding of libsep (include/sep.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls. Device
+buffers are torch CUDA tensors (PyTorch provides memory and streams); their
+pointers and the current stream are passed straight to the library. Nothing
+here computes anything of the path: a missing library raises instead of
+falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsep.so")
+
+SEP_OK, SEP_ERR_ARG, SEP_ERR_CUDA, SEP_ERR_OOM, SEP_ERR_CAPACITY, SEP_ERR_TIMEOUT, SEP_ERR_CSR, SEP_ERR_STATE = range(8)
+SEP_DEV_CAPACITY, SEP_DEV_TIMEOUT = 0x1, 0x2
+SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM = 0, 1, 2
+SEP_DTYPE_F32, SEP_DTYPE_U16_JF = 0, 1
+SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE = 0, 1, 2
+
+STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OOM", 4: "SEP_ERR_CAPACITY",
+                5: "SEP_ERR_TIMEOUT", 6: "SEP_ERR_CSR", 7: "SEP_ERR_STATE"}
+
+# every symbol include/sep.h declares
+EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error", "sep_get_device_status",
+           "sep_build_csr", "sep_csr_destroy", "sep_csr_info", "sep_csr_export", "sep_calib_create",
+           "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch"]
+
+
+class SepError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sep_geometry(C.Structure):
+    _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("pixel_m", C.c_double * 2), ("dist_m", C.c_double),
+                ("center_px", C.c_double * 2), ("wavelength_m", C.c_double), ("unit", C.c_int32),
+                ("nbins", C.c_int32), ("split", C.c_int32), ("range", C.c_double * 2)]
+
+
+class sep_params(C.Structure):
+    _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
+                ("min_count", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+PEAK_DTYPE = np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"), ("I", "<f4"), ("sigma", "<f4"), ("npix", "<i4")])
+PEAK_BYTES = 24
+
+_vp = C.c_void_p
+_lib = None
+
+
+def lib():
+    """Load libsep.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsep.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    L.sep_version.restype = C.c_char_p
+    L.sep_ctx_create.argtypes = [C.c_int32, C.POINTER(_vp)]
+    L.sep_ctx_destroy.argtypes = [_vp]
+    L.sep_ctx_destroy.restype = None
+    L.sep_last_error.argtypes = [_vp]
+    L.sep_last_error.restype = C.c_char_p
+    L.sep_get_device_status.argtypes = [_vp, _vp, C.POINTER(C.c_int32)]
+    L.sep_build_csr.argtypes = [_vp, C.POINTER(sep_geometry), _vp, _vp, C.POINTER(_vp)]
+    L.sep_csr_destroy.argtypes = [_vp]
+    L.sep_csr_destroy.restype = None
+    L.sep_csr_info.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    L.sep_csr_export.argtypes = [_vp] * 6
+    L.sep_calib_create.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(_vp)]
+    L.sep_calib_destroy.argtypes = [_vp]
+    L.sep_calib_destroy.restype = None
+    L.sep_integrate_clip.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
+                                     _vp, _vp, _vp]
+    L.sep_sparsify.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
+                               C.c_int64, _vp, _vp]
+    L.sep_peakfind.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
+                               C.c_int64, _vp, C.c_int64, _vp, _vp]
+    L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
+                                    _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("sep_version", "sep_last_error", "sep_ctx_destroy", "sep_csr_destroy", "sep_calib_destroy"):
+            f.restype = C.c_int32
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(_vp)
+    return _vp(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _check(ctx, st):
+    if st != SEP_OK:
+        msg = lib().sep_last_error(ctx).decode() if ctx else ""
+        raise SepError(st, msg)
+
+
+def sep_version() -> str:
+    return lib().sep_version().decode()
+
+
+def sep_ctx_create(device: int = 0):
+    h = _vp()
+    st = lib().sep_ctx_create(device, C.byref(h))
+    if st != SEP_OK:
+        raise SepError(st, f"cannot create a context on device {device}")
+    return h
+
+
+def sep_ctx_destroy(ctx):
+    lib().sep_ctx_destroy(ctx)
+
+
+def sep_last_error(ctx) -> str:
+    return lib().sep_last_error(ctx).decode()
+
+
+def sep_get_device_status(ctx, stream=None) -> int:
+    v = C.c_int32(0)
+    _check(ctx, lib().sep_get_device_status(ctx, _stream(stream), C.byref(v)))
+    return v.value
+
+
+def make_geometry(rows, cols, pixel_m, dist_m, center_px, wavelength_m, unit, nbins, split, rng):
+    g = sep_geometry()
+    g.rows, g.cols = rows, cols
+    g.pixel_m[0], g.pixel_m[1] = pixel_m
+    g.dist_m = dist_m
+    g.center_px[0], g.center_px[1] = center_px
+    g.wavelength_m = wavelength_m
+    g.unit, g.nbins, g.split = unit, nbins, split
+    g.range[0], g.range[1] = rng
+    return g
+
+
+def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_FP64MERGE):
+    p = sep_params()
+    p.n_iter, p.k_clip, p.k_pick, p.patch, p.min_count, p.precision = n_iter, k_clip, k_pick, patch, min_count, precision
+    return p
+
+
+def sep_build_csr(ctx, geom: sep_geometry, mask=None, norm=None):
+    h = _vp()
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    n = None if norm is None else np.ascontiguousarray(norm, np.float32)
+    _check(ctx, lib().sep_build_csr(ctx, C.byref(geom), _ptr(m), _ptr(n), C.byref(h)))
+    return h
+
+
+def sep_csr_destroy(csr):
+    lib().sep_csr_destroy(csr)
+
+
+def sep_csr_info(csr):
+    npix, nnz = C.c_int64(), C.c_int64()
+    nbins, max_row = C.c_int32(), C.c_int32()
+    rng = (C.c_double * 2)()
+    st = lib().sep_csr_info(csr, C.byref(npix), C.byref(nbins), C.byref(nnz), C.byref(max_row), rng)
+    if st != SEP_OK:
+        raise SepError(st, "sep_csr_info")
+    return {"npix": npix.value, "nbins": nbins.value, "nnz": nnz.value, "max_row": max_row.value,
+            "range": (rng[0], rng[1])}
+
+
+def sep_csr_export(csr):
+    info = sep_csr_info(csr)
+    rowptr = np.zeros(info["nbins"] + 1, np.int32)
+    col = np.zeros(info["nnz"], np.int32)
+    coef = np.zeros(info["nnz"], np.float32)
+    bop = np.zeros(info["npix"], np.int32)
+    centers = np.zeros(info["nbins"], np.float32)
+    st = lib().sep_csr_export(csr, _ptr(rowptr), _ptr(col), _ptr(coef), _ptr(bop), _ptr(centers))
+    if st != SEP_OK:
+        raise SepError(st, "sep_csr_export")
+    return {"rowptr": rowptr, "col": col, "coef": coef, "bin_of_pixel": bop, "bin_centers": centers, **info}
+
+
+def sep_calib_create(ctx, csr, ped, gain):
+    h = _vp()
+    p = np.ascontiguousarray(ped, np.float32)
+    g = np.ascontiguousarray(gain, np.float32)
+    _check(ctx, lib().sep_calib_create(ctx, csr, _ptr(p), _ptr(g), C.byref(h)))
+    return h
+
+
+def sep_calib_destroy(calib):
+    lib().sep_calib_destroy(calib)
+
+
+def sep_integrate_clip(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, count, bounds=None, iters=None,
+                       stream=None):
+    _check(ctx, lib().sep_integrate_clip(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
+                                         _ptr(sigma), _ptr(count), _ptr(bounds), _ptr(iters), _stream(stream)))
+
+
+def sep_sparsify(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, val, capacity, n_kept,
+                 stream=None):
+    _check(ctx, lib().sep_sparsify(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
+                                   _ptr(sigma), _ptr(idx), _ptr(val), capacity, _ptr(n_kept), _stream(stream)))
+
+
+def sep_peakfind(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, n_kept, kept_capacity, peaks,
+                 capacity, n_peaks, stream=None):
+    _check(ctx, lib().sep_peakfind(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
+                                   _ptr(sigma), _ptr(idx), _ptr(n_kept), kept_capacity, _ptr(peaks), capacity,
+                                   _ptr(n_peaks), _stream(stream)))
+
+
+def sep_process_batch(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, count, idx, val, kept_capacity,
+                      n_kept, peaks, peak_capacity, n_peaks, use_graph=1, stream=None):
+    _check(ctx, lib().sep_process_batch(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
+                                        _ptr(sigma), _ptr(count), _ptr(idx), _ptr(val), kept_capacity, _ptr(n_kept),
+                                        _ptr(peaks), peak_capacity, _ptr(n_peaks), int(use_graph), _stream(stream)))

@@ -1,0 +1,188 @@
+// Host construction of the integration matrix (Section 2.2).
+//
+// The coefficient c_{i,r} is the fraction of pixel i falling into radial bin
+// r; it is measured with split x split sub-pixel centres, so c = k / split^2
+// with k the number of centres of pixel i inside bin r. The radial value of a
+// point and its bin follow one fixed sequence of binary64 operations (the
+// definition the tests compare against):
+//   dy = (row + fy - cy) * pixel_y,  dx = (col + fx - cx) * pixel_x,
+//   r = sqrt(dx*dx + dy*dy),  2theta = atan2(r, dist)
+//   2theta unit: 2theta * (180 / pi);  q unit: 4 pi sin(2theta / 2) / (lambda * 1e9);
+//   r unit: r * 1e3
+//   bin = floor((x - lo) / (hi - lo) * nbins), the top edge going to nbins - 1,
+//   values outside [lo, hi] dropped; sub-pixel offsets f = (a + 0.5) / split.
+// Compiled with -ffp-contract=off so no multiply-add is fused.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <limits>
+
+#include "sep_internal.h"
+
+namespace sep {
+namespace {
+
+struct Geo {
+  double py, px, dist, cx, cy, lam;
+  int unit;
+};
+
+inline double radial(const Geo& g, int64_t row, int64_t col, double fy, double fx) {
+  double dy = ((double)row + fy - g.cy) * g.py;
+  double dx = ((double)col + fx - g.cx) * g.px;
+  double r = sqrt(dx * dx + dy * dy);
+  if (g.unit == SEP_UNIT_R_MM) return r * 1.0e3;
+  double tth = atan2(r, g.dist);
+  if (g.unit == SEP_UNIT_2TH_DEG) return tth * (180.0 / M_PI);
+  return 4.0 * M_PI * sin(0.5 * tth) / (g.lam * 1.0e9);
+}
+
+inline int32_t bin_index(double x, double lo, double hi, int32_t B) {
+  if (!(x >= lo && x <= hi)) return -1;
+  double t = (x - lo) / (hi - lo) * (double)B;
+  double fl = floor(t);
+  int64_t b = (int64_t)fl;
+  if (b >= B) b = B - 1;
+  if (b < 0) b = 0;
+  return (int32_t)b;
+}
+
+}  // namespace
+
+std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const float* norm, HostCsr* out) {
+  const int64_t rows = gm.rows, cols = gm.cols;
+  if (rows <= 0 || cols <= 0) return "rows and cols must be positive";
+  if (rows * cols > (int64_t)SEP_MAX_PIXELS) return "rows * cols exceeds SEP_MAX_PIXELS";
+  if (gm.nbins < 1 || gm.nbins > SEP_MAX_BINS) return "nbins out of range";
+  if (gm.split != 1 && gm.split != 2) return "split must be 1 or 2";
+  if (gm.unit < 0 || gm.unit > 2) return "unknown unit";
+  if (!(gm.dist_m > 0) || !(gm.pixel_m[0] > 0) || !(gm.pixel_m[1] > 0)) return "distance and pixel size must be > 0";
+  if (gm.unit == SEP_UNIT_Q_NM && !(gm.wavelength_m > 0)) return "wavelength must be > 0 for q";
+  const int64_t npix = rows * cols;
+  const int s = gm.split;
+  Geo g{gm.pixel_m[0], gm.pixel_m[1], gm.dist_m, gm.center_px[0], gm.center_px[1], gm.wavelength_m, gm.unit};
+  double off[2];
+  for (int a = 0; a < s; ++a) off[a] = ((double)a + 0.5) / (double)s;
+
+  if (norm) {
+    for (int64_t i = 0; i < npix; ++i)
+      if ((!mask || !mask[i]) && !(norm[i] > 0.0f)) return "norm must be > 0 on valid pixels";
+  }
+
+  // range: automatic = min / max over valid sub-pixel centres
+  double lo = gm.range[0], hi = gm.range[1];
+  if (isnan(lo) || isnan(hi)) {
+    double mn = std::numeric_limits<double>::infinity(), mx = -mn;
+#pragma omp parallel for reduction(min : mn) reduction(max : mx) schedule(static)
+    for (int64_t row = 0; row < rows; ++row)
+      for (int64_t col = 0; col < cols; ++col) {
+        if (mask && mask[row * cols + col]) continue;
+        for (int a = 0; a < s; ++a)
+          for (int b = 0; b < s; ++b) {
+            double x = radial(g, row, col, off[a], off[b]);
+            mn = x < mn ? x : mn;
+            mx = x > mx ? x : mx;
+          }
+      }
+    if (isnan(lo)) lo = mn;
+    if (isnan(hi)) hi = mx;
+  }
+  if (!(hi > lo)) return "empty radial range (no valid pixel, or lo >= hi)";
+  const int32_t B = gm.nbins;
+
+  // per pixel: up to s*s (bin, k) pairs + centre bin
+  const int maxe = s * s + 1;
+  std::vector<int32_t> pb((size_t)npix * maxe, -1);
+  std::vector<uint8_t> pk((size_t)npix * maxe, 0);
+  std::vector<uint8_t> pn((size_t)npix, 0);
+  std::vector<int32_t> bop((size_t)npix, -1);
+#pragma omp parallel for schedule(static)
+  for (int64_t row = 0; row < rows; ++row) {
+    for (int64_t col = 0; col < cols; ++col) {
+      const int64_t i = row * cols + col;
+      if (mask && mask[i]) continue;
+      // centre bin: the bin of the pixel centre, clamped into [0, B-1]
+      double xc = radial(g, row, col, 0.5, 0.5);
+      int32_t bc = xc < lo ? 0 : (xc > hi ? B - 1 : bin_index(xc, lo, hi, B));
+      bop[i] = bc;
+      int32_t sb[4];
+      int m = 0;
+      for (int a = 0; a < s; ++a)
+        for (int b = 0; b < s; ++b) sb[m++] = bin_index(radial(g, row, col, off[a], off[b]), lo, hi, B);
+      std::sort(sb, sb + m);
+      int32_t* eb = &pb[(size_t)i * maxe];
+      uint8_t* ek = &pk[(size_t)i * maxe];
+      int n = 0;
+      bool has_centre = false;
+      for (int t = 0; t < m; ++t) {
+        if (sb[t] < 0) continue;
+        if (n > 0 && eb[n - 1] == sb[t]) {
+          ek[n - 1] += 1;
+        } else {
+          eb[n] = sb[t];
+          ek[n] = 1;
+          ++n;
+        }
+        if (sb[t] == bc) has_centre = true;
+      }
+      if (!has_centre) {  // threshold carrier of zero weight, kept in bin order
+        int p = n;
+        while (p > 0 && eb[p - 1] > bc) {
+          eb[p] = eb[p - 1];
+          ek[p] = ek[p - 1];
+          --p;
+        }
+        eb[p] = bc;
+        ek[p] = 0;
+        ++n;
+      }
+      pn[i] = (uint8_t)n;
+    }
+  }
+
+  // counting sort by bin; pixels visited in ascending order keep columns sorted
+  std::vector<int64_t> cnt((size_t)B + 1, 0);
+  for (int64_t i = 0; i < npix; ++i)
+    for (int t = 0; t < pn[i]; ++t) cnt[(size_t)pb[(size_t)i * maxe + t] + 1] += 1;
+  for (int32_t b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
+  const int64_t nnz = cnt[B];
+  if (nnz > (int64_t)std::numeric_limits<int32_t>::max()) return "too many nonzeros";
+  out->rowptr.assign((size_t)B + 1, 0);
+  int32_t max_row = 0;
+  for (int32_t b = 0; b <= B; ++b) out->rowptr[b] = (int32_t)cnt[b];
+  for (int32_t b = 0; b < B; ++b) max_row = std::max(max_row, out->rowptr[b + 1] - out->rowptr[b]);
+  out->ent.assign((size_t)nnz, 0);
+  out->coef.assign((size_t)nnz, 0.0f);
+  if (norm) out->w.assign((size_t)nnz, 0.0f);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  const double inv = 1.0 / (double)(s * s);
+  for (int64_t i = 0; i < npix; ++i) {
+    for (int t = 0; t < pn[i]; ++t) {
+      int32_t b = pb[(size_t)i * maxe + t];
+      int k = pk[(size_t)i * maxe + t];
+      int64_t e = fill[b]++;
+      uint32_t u = (uint32_t)i;
+      if (k == 0) u |= kZero;
+      else u |= (uint32_t)(k - 1) << kKShift;
+      if (b == bop[i]) u |= kCentre;
+      out->ent[e] = u;
+      double c = (double)k * inv;
+      out->coef[e] = (float)c;
+      if (norm) out->w[e] = (float)(c * (double)norm[i]);
+    }
+  }
+  out->rows = gm.rows;
+  out->cols = gm.cols;
+  out->nbins = B;
+  out->split = s;
+  out->lo = lo;
+  out->hi = hi;
+  out->max_row = max_row;
+  out->bop.swap(bop);
+  out->centers.resize(B);
+  for (int32_t b = 0; b < B; ++b) out->centers[b] = (float)(lo + ((double)b + 0.5) * (hi - lo) / (double)B);
+  return std::string();
+}
+
+}  // namespace sep

@@ -1,0 +1,135 @@
+// Internal declarations of libsep (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sep.h"
+
+// ---- packed CSR entry ---------------------------------------------------
+// One 32-bit word per nonzero of the integration matrix:
+//   bits  0..24  pixel index (column of the matrix), < 2^25
+//   bits 25..26  k - 1 where k / split^2 is the coefficient c_{i,r} (k = 1..4)
+//   bit  27      the entry's bin is the pixel's centre bin (threshold bin)
+//   bit  28      zero coefficient: the entry exists only to carry bit 27
+namespace sep {
+constexpr uint32_t kColBits = 25;
+constexpr uint32_t kColMask = (1u << kColBits) - 1u;
+constexpr uint32_t kKShift = 25;
+constexpr uint32_t kCentre = 1u << 27;
+constexpr uint32_t kZero = 1u << 28;
+
+// Host-built matrix (own FP64 implementation of Section 2.2's coefficients).
+struct HostCsr {
+  int32_t rows = 0, cols = 0, nbins = 0, split = 1;
+  double lo = 0, hi = 0;
+  std::vector<int32_t> rowptr;   // [nbins + 1]
+  std::vector<uint32_t> ent;     // [nnz] packed
+  std::vector<float> coef;       // [nnz] c_{i,r} (0 for centre-only entries)
+  std::vector<float> w;          // [nnz] c * norm (only with a norm)
+  std::vector<int32_t> bop;      // [npix] centre bin, -1 masked
+  std::vector<float> centers;    // [nbins]
+  int32_t max_row = 0;
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const float* norm, HostCsr* out);
+
+// ---- kernel launch parameters -------------------------------------------
+struct ClipArgs {
+  const int32_t* rowptr;
+  const uint32_t* ent;
+  const float* w;          // per-entry weight c * norm (NORM variant)
+  const float* norm;       // per-pixel norm (NORM variant)
+  const void* frames;
+  int64_t npix;
+  int32_t nbins, n_frames, frames_per_cta, cap;
+  const float* ped;        // [3][npix] (raw input)
+  const float* gain;       // [3][npix]
+  int32_t n_iter;
+  float k_clip, k_pick;
+  float* mean;
+  float* sigma;
+  int32_t* count;
+  float* bounds;           // optional [F][B][2]
+  int32_t* iters;          // optional [F][B]
+  uint32_t* bitmap;        // optional kept-pixel map [F][words]
+  int64_t words;           // bitmap words per frame
+};
+
+struct PixArgs {           // what the consumers need to recompute a pixel value
+  const void* frames;
+  int64_t npix;
+  int32_t rows, cols, dtype;
+  const float* ped;
+  const float* gain;
+  const float* norm;       // may be null
+  const int32_t* bop;      // [npix], -1 masked
+};
+
+// mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
+// only (call before a stream capture); 2: launch only.
+cudaError_t launch_integrate_clip(const ClipArgs& a, int32_t dtype, bool split, bool has_norm,
+                                  int32_t precision, int mode, cudaStream_t s);
+size_t clip_smem_bytes(int32_t cap, bool weighted);
+cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
+                              cudaStream_t s);
+cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* thr, uint32_t* bitmap,
+                        int64_t words, cudaStream_t s);
+cudaError_t launch_compact(const PixArgs& p, int32_t n_frames, const uint32_t* bitmap, int64_t words,
+                           int32_t* idx, float* val, int64_t cap, int32_t* n_kept, int32_t* status,
+                           cudaStream_t s);
+cudaError_t launch_scatter_list(int32_t n_frames, const int32_t* idx, const int32_t* n_kept, int64_t kcap,
+                                int64_t npix, uint32_t* bitmap, int64_t words, cudaStream_t s);
+cudaError_t launch_peaks(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* mean, const float* sigma,
+                         const uint32_t* bitmap, int64_t words, const int32_t* idx,
+                         const int32_t* n_kept, int64_t kcap, int32_t patch, int32_t min_count,
+                         sep_peak* peaks, int64_t pcap, int32_t* n_peaks, int32_t* status, cudaStream_t s);
+}  // namespace sep
+
+// ---- handles --------------------------------------------------------------
+struct sep_graph_entry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+};
+
+struct sep_ctx {
+  int32_t device = 0;
+  int num_sms = 0;
+  int32_t* d_status = nullptr;
+  std::string err;
+  // scratch owned by the context, grown on demand (never inside a capture)
+  uint32_t* d_bitmap = nullptr;
+  size_t bitmap_words = 0;
+  float* d_thr = nullptr;
+  size_t thr_len = 0;
+  // captured batches, keyed by every launch argument
+  std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
+  uint64_t use_clock = 0;
+};
+
+struct sep_csr {
+  sep_ctx* ctx = nullptr;
+  sep::HostCsr h;
+  int64_t npix = 0, nnz = 0;
+  bool has_norm = false;
+  int32_t* d_rowptr = nullptr;
+  uint32_t* d_ent = nullptr;
+  float* d_w = nullptr;
+  float* d_norm = nullptr;
+  int32_t* d_bop = nullptr;
+};
+
+struct sep_calib {
+  sep_ctx* ctx = nullptr;
+  const sep_csr* csr = nullptr;
+  int64_t npix = 0;
+  float* d_ped = nullptr;
+  float* d_gain = nullptr;
+};

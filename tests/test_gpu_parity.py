@@ -1,0 +1,217 @@
+"""GPU path against the CPU oracle, element by element, through the C ABI.
+
+Sizes: the 256 x 256 frame (ten seeds), a two-module Jungfrau-shaped detector
+with raw words and 2 x 2 splitting (several hundred bins, a ragged last
+tile), and the exhaustive correction table; edge cases below."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import Frame, check_clip, check_kept, check_peaks
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2411_09515_gb300 import (SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator,  # noqa: E402
+                                    peaks_to_numpy)
+
+
+def run_batch(sep, frames_np, kcap, pcap, use_graph=True):
+    if frames_np.dtype == np.uint16:
+        frames_np = frames_np.view(np.int16)   # raw words travel as 16-bit integers
+    fr = torch.from_numpy(np.ascontiguousarray(frames_np)).cuda()
+    out = sep.process_batch(fr, kcap, pcap, use_graph=use_graph)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}, fr
+
+
+def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None):
+    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm)
+    if bounds is None:
+        bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
+    nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
+    excused = check_kept(fr, o["idx"][f], o["val"][f], o["n_kept"][f], moved, capacity=kcap)
+    peaks = o["peaks"][f][: int(o["n_peaks"][f])].copy().view(np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"),
+                                                                      ("I", "<f4"), ("sigma", "<f4"),
+                                                                      ("npix", "<i4")])).reshape(-1)
+    check_peaks(det, fr, peaks, excused)
+    return nb, len(moved), len(excused)
+
+
+def test_config1_ten_seeds_batch():
+    det = synth.det_config1()
+    W = oracle.weights(det)
+    fr = np.concatenate([synth.frames(det, synth.spec_config1(s), 0, 1)[0] for s in range(10)])
+    sep = Separator.from_detector(det)
+    o, dfr = run_batch(sep, fr, 8192, 512)
+    # the bounds of the final sets come from the standalone call (same kernel)
+    ic = sep.integrate_clip(dfr, bounds=True, iters=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(ic["mean"].cpu().numpy(), o["mean"])
+    assert np.array_equal(ic["count"].cpu().numpy(), o["count"])
+    bnd = ic["bounds"].cpu().numpy()
+    for f in range(10):
+        check_frame(det, W, fr[f], o, f, kcap=8192, bounds=bnd[f])
+    assert sep.device_status() == 0
+    assert (o["n_peaks"] >= 11).all()
+
+
+def test_standalone_calls_equal_the_batch():
+    det = synth.det_config1()
+    fr = np.concatenate([synth.frames(det, synth.spec_config1(s), 0, 1)[0] for s in range(3)])
+    sep = Separator.from_detector(det)
+    o, dfr = run_batch(sep, fr, 8192, 512, use_graph=False)
+    ic = sep.integrate_clip(dfr)
+    sp = sep.sparsify(dfr, ic["mean"], ic["sigma"], 8192)
+    pk = sep.peakfind(dfr, ic["mean"], ic["sigma"], sp["idx"], sp["n_kept"], 512)
+    torch.cuda.synchronize()
+    assert np.array_equal(ic["mean"].cpu().numpy(), o["mean"])
+    assert np.array_equal(ic["sigma"].cpu().numpy(), o["sigma"])
+    # the standalone sparsify takes float32 profiles: its thresholds may differ
+    # from the fused ones by a rounding of the mean, hence by band pixels only
+    nk = sp["n_kept"].cpu().numpy()
+    assert np.all(np.abs(nk - o["n_kept"]) <= 2)
+    assert np.all(np.abs(pk["n_peaks"].cpu().numpy() - o["n_peaks"]) <= 1)
+
+
+def test_graph_replay_is_deterministic():
+    det = synth.det_config1()
+    fr = synth.frames(det, synth.spec_config1(4), 0, 2)[0]
+    sep = Separator.from_detector(det)
+    d = torch.from_numpy(fr).cuda()
+    out = sep.alloc_outputs(2, 4096, 256)
+    res = []
+    for _ in range(3):
+        sep.process_batch(d, 4096, 256, out=out, use_graph=True)
+        torch.cuda.synchronize()
+        res.append({k: v.cpu().numpy().copy() for k, v in out.items()})
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]) and np.array_equal(res[0][k], res[2][k]), k
+
+
+@pytest.fixture(scope="module")
+def jf_small():
+    det = synth.det_small_jf(split=2, nbins=300)
+    mask = det.mask()
+    cal = synth.jf_calib(det.npix, seed=7)
+    spec = synth.spec_jf_serial(11)
+    spec.hit_rate = 0.5
+    fr, _, _ = synth.frames(det, spec, 0, 6, calib=cal, mask=mask)
+    W = oracle.weights(det, mask)
+    return det, mask, cal, fr, W
+
+
+@pytest.mark.parametrize("precision", [SEP_PREC_FP64MERGE, SEP_PREC_KAHAN])
+def test_jungfrau_raw_split_parity(jf_small, precision):
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)
+    kcap = det.npix // 4
+    o, dfr = run_batch(sep, fr, kcap, 20000)
+    bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+    tot_band = 0
+    for f in range(fr.shape[0]):
+        sig = oracle.jf_photons(fr[f], cal[0], cal[1])
+        nb, nm, ne = check_frame(det, W, sig, o, f, kcap=kcap, bounds=bnd[f])
+        tot_band += nb
+    assert sep.device_status() == 0
+
+
+def test_plain_precision_error_is_reported_not_hidden(jf_small):
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal, precision=SEP_PREC_PLAIN)
+    o, _ = run_batch(sep, fr[:2], det.npix // 4, 20000)
+    sig = oracle.jf_photons(fr[0], cal[0], cal[1])
+    ref = oracle.integrate_clip(W, sig)
+    ok = ref["count"] > 0
+    rel = np.abs(o["mean"][0][ok] - ref["mean"][ok]) / np.abs(ref["mean"][ok])
+    assert np.median(rel) < 1e-4
+
+
+def test_correction_bit_exact_all_raw_codes():
+    """Every 16-bit raw word through the GPU correction, against the oracle's
+    binary32 definition, bit for bit (values come back as kept pixels with a
+    threshold below everything)."""
+    rows, cols = 256, 256
+    det = synth.Detector("codes", rows, cols, dist_m=0.1, center_px=(128.3, 120.7), nbins=8, split=1)
+    rng = np.random.default_rng(9)
+    ped = np.stack([rng.normal(m, s, rows * cols) for m, s in ((1500, 50), (14000, 200), (15000, 200))]).astype(np.float32)
+    gain = np.stack([40 * (1 + rng.uniform(-.02, .02, rows * cols)), -1.5 * (1 + rng.uniform(-.02, .02, rows * cols)),
+                     -0.1 * (1 + rng.uniform(-.02, .02, rows * cols))]).astype(np.float32)
+    raw = np.arange(rows * cols, dtype=np.uint32).astype(np.uint16)[None]
+    sep = Separator.from_detector(det, calib=(ped, gain), k_pick=0.0)
+    d = torch.from_numpy(raw.astype(np.int16)).cuda()
+    mean = torch.full((1, 8), -1e30, dtype=torch.float32, device="cuda")
+    sigma = torch.zeros((1, 8), dtype=torch.float32, device="cuda")
+    sp = sep.sparsify(d, mean, sigma, rows * cols)
+    torch.cuda.synchronize()
+    assert int(sp["n_kept"][0]) == rows * cols
+    got = sp["val"][0].cpu().numpy()
+    want = oracle.jf_photons(raw[0], ped, gain)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_edge_cases():
+    det = synth.Detector("e", 40, 50, dist_m=0.05, center_px=(20.3, 18.7), nbins=30, split=2, unit=synth.UNIT_R_MM)
+    mask = np.zeros(det.npix, np.uint8)
+    W0 = oracle.weights(det, mask)
+    # mask every pixel of bin 5: an empty bin
+    mask[np.unique(W0.pix[W0.bin == 5])] = 1
+    sep = Separator.from_detector(det, mask=mask)
+    W = oracle.weights(det, mask)
+    # empty batch: nothing launched, nothing written
+    out = sep.alloc_outputs(1, 16, 16)
+    sep.process_batch(torch.zeros((0, det.npix), dtype=torch.float32, device="cuda"), 16, 16)
+    # constant frame: mean = constant, sigma = 0, nothing rejected, nothing kept
+    const = np.full((1, det.npix), 7.25, np.float32)
+    o, _ = run_batch(sep, const, 16, 16)
+    ref = oracle.integrate_clip(W, const[0])
+    has = ref["count"] > 0
+    assert np.allclose(o["mean"][0][has], 7.25, rtol=1e-6) and np.all(o["sigma"][0] <= 1e-5)
+    assert np.array_equal(o["count"][0], ref["count"]) and o["count"][0][5] == 0
+    assert o["mean"][0][5] == 0 and o["sigma"][0][5] == 0
+    assert o["n_kept"][0] == 0 and o["n_peaks"][0] == 0
+    # capacity overflow: true count reported, first `cap` entries written, flag raised
+    rng = np.random.default_rng(1)
+    fr = rng.normal(10, 1, (1, det.npix)).astype(np.float32)
+    fr[0, ::7] += 40
+    o, _ = run_batch(sep, fr, 16, 4)
+    assert o["n_kept"][0] > 16
+    assert sep.device_status() & 1
+    full, _ = run_batch(sep, fr, det.npix, 1000)
+    assert np.array_equal(o["idx"][0][:16], full["idx"][0][:16])
+    assert sep.device_status() == 0
+    # no clipping at all
+    sep.set_params(n_iter=0)
+    o, _ = run_batch(sep, fr, det.npix, 1000)
+    check_frame(det, W, fr[0], o, 0, n_iter=0, kcap=det.npix)
+
+
+def test_norm_weights():
+    det = synth.det_config1()
+    rng = np.random.default_rng(2)
+    norm = rng.uniform(0.5, 2.0, det.npix).astype(np.float32)
+    fr = synth.frames(det, synth.spec_config1(3), 0, 2)[0] * norm
+    fr = fr.astype(np.float32)
+    sep = Separator.from_detector(det, norm=norm)
+    o, dfr = run_batch(sep, fr, 8192, 512)
+    bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+    W = oracle.weights(det)
+    for f in range(2):
+        check_frame(det, W, fr[f], o, f, kcap=8192, bounds=bnd[f], norm=norm)
+
+
+def test_invalid_arguments_raise_before_launch():
+    from paper_2411_09515_gb300 import SepError
+    det = synth.det_config1()
+    sep = Separator.from_detector(det)
+    d = torch.zeros((1, det.npix), dtype=torch.float32, device="cuda")
+    sep.set_params(patch=4)
+    with pytest.raises(SepError):
+        sep.process_batch(d, 16, 16)
+    sep.set_params(patch=3, k_clip=0.0)
+    with pytest.raises(SepError):
+        sep.integrate_clip(d)
+    sep.set_params(k_clip=3.0)
+    with pytest.raises(SepError):   # raw frames without a calibration
+        sep.integrate_clip(torch.zeros((1, det.npix), dtype=torch.int16, device="cuda"))

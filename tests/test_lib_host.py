@@ -1,0 +1,115 @@
+"""Host-side checks of libsep that need no GPU: the library loads and
+exports every symbol include/sep.h declares, argument errors are reported
+before any launch, and the host-built integration matrix equals the oracle's
+independently computed coefficients entry for entry."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2411_09515_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2411_09515_gb300 import build
+    build.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "sep.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sep_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = header_functions()
+    assert sorted(B.EXPORTS) == names
+    L = B.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert "sm_103a" in B.sep_version()
+
+
+def test_struct_layouts_match_header():
+    import ctypes as C
+    assert C.sizeof(B.sep_geometry) == 4 * 2 + 8 * 2 + 8 + 8 * 2 + 8 + 4 * 3 + 4 + 8 * 2  # padded before range
+    assert C.sizeof(B.sep_params) == 40
+    assert B.PEAK_DTYPE.itemsize == B.PEAK_BYTES == 24
+
+
+def geom_of(det):
+    return B.make_geometry(det.rows, det.cols, det.pixel_m, det.dist_m, det.center_px, det.wavelength_m, det.unit,
+                           det.nbins, det.split, det.range)
+
+
+@pytest.mark.parametrize("bad", [dict(rows=0), dict(nbins=0), dict(split=3), dict(unit=7), dict(dist_m=0.0),
+                                 dict(rows=8192, cols=8192)])
+def test_invalid_geometry_rejected(bad):
+    det = synth.det_config1()
+    for k, v in bad.items():
+        setattr(det, k, v)
+    with pytest.raises(B.SepError) as e:
+        B.sep_build_csr(None, geom_of(det))
+    assert e.value.status == B.SEP_ERR_ARG
+
+
+def compare_with_oracle(det, mask=None):
+    csr = B.sep_build_csr(None, geom_of(det), mask)
+    try:
+        ex = B.sep_csr_export(csr)
+    finally:
+        B.sep_csr_destroy(csr)
+    W = oracle.weights(det, mask)
+    assert ex["range"] == W.range
+    assert np.array_equal(ex["bin_of_pixel"], W.bin_of_pixel)
+    rows = np.repeat(np.arange(det.nbins), np.diff(ex["rowptr"]))
+    nz = ex["coef"] != 0
+    got = sorted(zip(ex["col"][nz].tolist(), rows[nz].tolist(), ex["coef"][nz].astype(np.float64).tolist()))
+    want = sorted(zip(W.pix.tolist(), W.bin.tolist(), W.c.tolist()))
+    assert got == want
+    # columns ascend within every row
+    for b in range(det.nbins):
+        c = ex["col"][ex["rowptr"][b]:ex["rowptr"][b + 1]]
+        assert np.all(np.diff(c) > 0)
+    # zero-coefficient entries exist only to carry a pixel's centre bin
+    zc, zr = ex["col"][~nz], rows[~nz]
+    assert np.array_equal(W.bin_of_pixel[zc], zr)
+    have = set(zip(W.pix.tolist(), W.bin.tolist()))
+    assert all((int(p), int(b)) not in have for p, b in zip(zc, zr))
+    valid = np.flatnonzero(W.bin_of_pixel >= 0)
+    centre_pairs = set(zip(ex["col"].tolist(), rows.tolist()))
+    assert all((int(i), int(W.bin_of_pixel[i])) in centre_pairs for i in valid[:: max(1, valid.size // 5000)])
+    return ex
+
+
+def test_csr_config1_equals_oracle():
+    ex = compare_with_oracle(synth.det_config1())
+    assert ex["nnz"] == 65536 and ex["max_row"] > 0
+
+
+@pytest.mark.parametrize("unit", [synth.UNIT_2TH_DEG, synth.UNIT_Q_NM, synth.UNIT_R_MM])
+def test_csr_split2_equals_oracle(unit):
+    det = synth.det_small_jf(split=2, nbins=150)
+    det.unit = unit
+    compare_with_oracle(det, det.mask())
+
+
+def test_csr_centre_only_entries_near_beam_centre():
+    # many narrow bins around a centre inside the image force pixels whose
+    # centre bin holds none of their sub-pixels
+    det = synth.Detector("c", 24, 24, dist_m=0.05, center_px=(12.0, 12.0), unit=synth.UNIT_R_MM, nbins=200, split=2)
+    ex = compare_with_oracle(det)
+    assert (ex["coef"] == 0).sum() > 0
+
+
+def test_csr_explicit_range_drops_outside():
+    det = synth.det_config1()
+    det.range = (1.0, 5.0)
+    det.nbins = 20
+    compare_with_oracle(det)
