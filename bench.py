@@ -132,7 +132,8 @@ def run_ours(args):
     t0 = time.time()
     det, mask, cal, frames_np = setup_workload(F, rank)
     t_gen = time.time() - t0
-    sep = Separator.from_detector(det, mask=mask, calib=cal, device=local)
+    prec = {"plain": B.SEP_PREC_PLAIN, "kahan": B.SEP_PREC_KAHAN, "fp64merge": B.SEP_PREC_FP64MERGE}[args.precision]
+    sep = Separator.from_detector(det, mask=mask, calib=cal, device=local, precision=prec)
     info = sep.info
     kcap, pcap = args.kept_capacity, args.peak_capacity
     host = torch.from_numpy(frames_np.view(np.int16)).pin_memory()
@@ -222,11 +223,11 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u16->f32 (fp64 merge)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16->f32",
             "data": "synthetic (seeded Jungfrau-4M-shaped raw frames; no dataset)",
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "nnz": info["nnz"], "max_row": info["max_row"],
                        "l2": "inputs larger than L2 (4.58 GB/batch), no flush", "parallelism": f"replicas x{world}",
-                       "kept_capacity": kcap, "peak_capacity": pcap},
+                       "kept_capacity": kcap, "peak_capacity": pcap, "precision": args.precision},
             "roofline": {"bound": "hbm", "kernel": "k_integrate_clip", "achieved": round(achieved, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": None,
@@ -298,6 +299,7 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge"], default="fp64merge")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

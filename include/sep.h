@@ -57,11 +57,13 @@ typedef int32_t sep_status;
 #define SEP_DTYPE_U16_JF  1   /* raw Jungfrau word: 2 gain bits (15:14) + 14-bit ADC */
 
 /* Precision of the per-bin moments (Section 2.2's reductions):
- * PLAIN: plain FP32 per-thread sums, FP32 merges and finalisation.
- * KAHAN: Kahan-compensated FP32 per-thread sums, error-free (two-sum) FP32
- *        warp merges, FP32 cross-warp merge and finalisation.
- * FP64MERGE: as KAHAN up to the warp, then FP64 cross-warp merge and FP64
- *        mean / deviation / clip bounds (the default). */
+ * PLAIN:     plain FP32 per-thread sums, FP32 merges and finalisation.
+ * KAHAN:     Kahan-compensated FP32 per-thread sums, error-free FP32 pair
+ *            merges (warp and cross-warp), FP64 finalisation on one thread.
+ * FP64MERGE: plain FP32 per-thread sums and warp shuffles, FP64 cross-warp
+ *            merge, FP64 finalisation on one thread (the default).
+ * With KAHAN and FP64MERGE the clip bounds are rounded outward-exact, so a
+ * float value is compared with the FP64 bound itself. */
 #define SEP_PREC_PLAIN     0
 #define SEP_PREC_KAHAN     1
 #define SEP_PREC_FP64MERGE 2
@@ -132,7 +134,9 @@ sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* statu
  *  mask_host: rows*cols bytes, nonzero = masked pixel (never used); may be NULL.
  *  norm_host: rows*cols floats, the normalisation of Eq. 1 (denominator);
  *             may be NULL (= 1 everywhere). Must be > 0 on valid pixels.
- * Rows of the matrix are bins; columns within a row ascend. Every valid
+ * Rows of the matrix are bins. Within a row, entries are grouped by
+ * coefficient (largest first, then weight-0 entries), columns ascending in
+ * a group, each group padded to a multiple of 4 entries. Every valid
  * pixel also gets its centre bin (the bin its threshold is taken from in
  * sparsification, Section 3); where that bin has no coefficient of the
  * pixel, an entry of weight 0 is added for it.
@@ -148,7 +152,8 @@ void sep_csr_destroy(sep_csr* csr);
 sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64_t* nnz,
                         int32_t* max_row, double* range);
 /* Host copies for inspection (any pointer may be NULL):
- * rowptr [nbins+1], col [nnz], coef [nnz] (c_{i,r}, 0 for centre-only entries),
+ * rowptr [nbins+1], col [nnz] (-1 for padding), coef [nnz] (c_{i,r}; 0 for
+ * padding and centre-only entries),
  * bin_of_pixel [npix] (-1 = masked), bin_centers [nbins]. */
 sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, float* coef,
                           int32_t* bin_of_pixel, float* bin_centers);

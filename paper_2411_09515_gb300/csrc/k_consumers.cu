@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sep_device.cuh"
 #include "sep_internal.h"
 
@@ -64,54 +66,94 @@ __global__ void k_mark(PixArgs p, int32_t nbins, const float* thr, uint32_t* bit
 
 constexpr int kCompactThreads = 1024;
 constexpr int kWordsPerThread = 8;
+constexpr int64_t kTileWords = (int64_t)kCompactThreads * kWordsPerThread;   // bitmap words per CTA
 
-// One CTA per frame: walk the bitmap in tiles, write kept pixels in order.
-template <int DT, bool NORM>
-__global__ void __launch_bounds__(kCompactThreads) k_compact(PixArgs p, const uint32_t* bitmap, int64_t words,
-                                                             int32_t* idx, float* val, int64_t cap,
-                                                             int32_t* n_kept, int32_t* status) {
-  __shared__ int sh[kCompactThreads / 32];
-  const int64_t f = blockIdx.x;
+// Phase 1 of the ordered compaction: kept pixels per tile of the bitmap.
+__global__ void __launch_bounds__(256) k_count_bits(const uint32_t* bitmap, int64_t words, int32_t* tile_cnt,
+                                                    int32_t n_tiles) {
+  const int64_t f = blockIdx.y;
+  const int64_t w0 = (int64_t)blockIdx.x * kTileWords;
   const uint32_t* bm = bitmap + f * words;
-  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
-  int64_t total = 0;
-  for (int64_t base = 0; base < words; base += (int64_t)kCompactThreads * kWordsPerThread) {
-    const int64_t w0 = base + (int64_t)threadIdx.x * kWordsPerThread;
-    uint32_t wv[kWordsPerThread];
-    int cnt = 0;
-    if (w0 + kWordsPerThread <= words) {
-      const uint4* q = reinterpret_cast<const uint4*>(bm + w0);
-      uint4 a = q[0], b = q[1];
-      wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-      wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < kWordsPerThread; ++j) wv[j] = (w0 + j < words) ? bm[w0 + j] : 0u;
+  int cnt = 0;
+  for (int64_t w = w0 + 4 * (int64_t)threadIdx.x; w < w0 + kTileWords && w < words; w += 4 * 256) {
+    // words is a multiple of 8, so a 4-word vector never runs past the frame
+    const uint4 q = *reinterpret_cast<const uint4*>(bm + w);
+    cnt += __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
+  }
+  __shared__ int sh[8];
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < 8; ++i) t += sh[i];
+    tile_cnt[f * n_tiles + blockIdx.x] = t;
+  }
+}
+
+// Phase 2: each CTA writes its tile's kept pixels (ascending) after the
+// pixels of all earlier tiles of the frame; values are recomputed from the
+// frame exactly as the clip kernel computed them.
+template <int DT, bool NORM>
+__global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const uint32_t* bitmap, int64_t words,
+                                                               const int32_t* tile_cnt, int32_t n_tiles, int32_t* idx,
+                                                               float* val, int64_t cap, int32_t* n_kept,
+                                                               int32_t* status) {
+  __shared__ int sh[kCompactThreads / 32];
+  __shared__ int64_t base_s;
+  const int64_t f = blockIdx.y;
+  const int tile = blockIdx.x;
+  if (threadIdx.x < 32) {
+    int64_t before = 0, all = 0;
+    for (int t = threadIdx.x; t < n_tiles; t += 32) {
+      const int c = tile_cnt[f * n_tiles + t];
+      all += c;
+      if (t < tile) before += c;
     }
-#pragma unroll
-    for (int j = 0; j < kWordsPerThread; ++j) cnt += __popc(wv[j]);
-    int tile_total;
-    int off = block_exclusive_scan<kCompactThreads>(cnt, &tile_total, sh);
-    int64_t pos = total + off;
-#pragma unroll
-    for (int j = 0; j < kWordsPerThread; ++j) {
-      uint32_t m = wv[j];
-      while (m) {
-        int bit = __ffs(m) - 1;
-        m &= m - 1u;
-        int64_t i = (w0 + j) * 32 + bit;
-        if (pos < cap) {
-          idx[f * cap + pos] = (int32_t)i;
-          val[f * cap + pos] = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
-        }
-        ++pos;
+    for (int o = 16; o > 0; o >>= 1) {
+      before += __shfl_xor_sync(0xffffffffu, before, o);
+      all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if (threadIdx.x == 0) {
+      base_s = before;
+      if (tile == 0) {
+        n_kept[f] = (int32_t)all;
+        if (all > cap) atomicOr(status, SEP_DEV_CAPACITY);
       }
     }
-    total += tile_total;
   }
-  if (threadIdx.x == 0) {
-    n_kept[f] = (int32_t)total;
-    if (total > cap) atomicOr(status, SEP_DEV_CAPACITY);
+  __syncthreads();
+  const int64_t base = base_s;
+  if (base >= cap) return;
+  const uint32_t* bm = bitmap + f * words;
+  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
+  const int64_t w0 = (int64_t)tile * kTileWords + (int64_t)threadIdx.x * kWordsPerThread;
+  uint32_t wv[kWordsPerThread];
+  if (w0 + kWordsPerThread <= words) {
+    const uint4* q = reinterpret_cast<const uint4*>(bm + w0);
+    const uint4 a = q[0], b = q[1];
+    wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+    wv[4] = b.x; wv[5] = b.y; wv[6] = b.z; wv[7] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kWordsPerThread; ++j) wv[j] = (w0 + j < words) ? bm[w0 + j] : 0u;
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kWordsPerThread; ++j) cnt += __popc(wv[j]);
+  int tile_total;
+  int64_t pos = base + block_exclusive_scan<kCompactThreads>(cnt, &tile_total, sh);
+#pragma unroll
+  for (int j = 0; j < kWordsPerThread; ++j) {
+    uint32_t m = wv[j];
+    while (m && pos < cap) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1u;
+      const int64_t i = (w0 + j) * 32 + bit;
+      idx[f * cap + pos] = (int32_t)i;
+      val[f * cap + pos] = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
+      ++pos;
+    }
   }
 }
 
@@ -129,81 +171,142 @@ __global__ void k_scatter_list(const int32_t* idx, const int32_t* n_kept, int64_
 }
 
 constexpr int kPeakThreads = 256;
+constexpr int kPeakChunk = 256;          // kept entries per flag chunk (8 flag words)
+constexpr int kPeakCtasPerFrame = 64;
 
 __device__ __forceinline__ bool is_kept(const uint32_t* bm, int64_t j) { return (bm[j >> 5] >> (j & 31)) & 1u; }
 
-// One CTA per frame: each thread tests one kept pixel; peaks are written in
-// ascending index order through a block scan per tile.
+// Is kept pixel i a peak (Section 4)? At least min_count kept pixels in the
+// patch, and i the maximum of the patch's valid pixels (ties: lowest index).
 template <int DT, bool NORM>
-__global__ void __launch_bounds__(kPeakThreads) k_peaks(PixArgs p, int32_t nbins, const float* mean,
-                                                        const float* sigma, const uint32_t* bitmap, int64_t words,
-                                                        const int32_t* idx, const int32_t* n_kept, int64_t kcap, int32_t patch,
-                                                        int32_t min_count, sep_peak* peaks, int64_t pcap,
-                                                        int32_t* n_peaks, int32_t* status) {
-  __shared__ int sh[kPeakThreads / 32];
-  const int64_t f = blockIdx.x;
+__device__ __forceinline__ bool peak_test(const PixArgs& p, const void* frame, const uint32_t* bm, int64_t i, int h,
+                                          int32_t min_count, float vi, int& nk_out) {
+  const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
+  const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
+  const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
+  int nk = 0;
+  for (int r = rlo; r <= rhi; ++r)
+    for (int c = clo; c <= chi; ++c) nk += is_kept(bm, (int64_t)r * p.cols + c);
+  nk_out = nk;
+  if (nk < min_count) return false;
+  for (int r = rlo; r <= rhi; ++r)
+    for (int c = clo; c <= chi; ++c) {
+      const int64_t j = (int64_t)r * p.cols + c;
+      if (j == i || __ldg(p.bop + j) < 0) continue;
+      const float vj = pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
+      if (!(vi > vj || (vi == vj && i < j))) return false;
+    }
+  return true;
+}
+
+// Phase 1: one flag bit per kept-list entry, and peaks per chunk of 256.
+template <int DT, bool NORM>
+__global__ void __launch_bounds__(kPeakThreads) k_peak_flags(PixArgs p, const uint32_t* bitmap, int64_t words,
+                                                             const int32_t* idx, const int32_t* n_kept, int64_t kcap,
+                                                             int32_t patch, int32_t min_count, uint32_t* flags,
+                                                             int32_t* chunk_cnt, int32_t n_chunks) {
+  const int64_t f = blockIdx.y;
   const uint32_t* bm = bitmap + f * words;
   const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
-  const float* mu = mean + f * nbins;
-  const float* sd = sigma + f * nbins;
   int64_t n = n_kept[f];
   if (n > kcap) n = kcap;
   const int h = patch >> 1;
-  int64_t total = 0;
-  for (int64_t base = 0; base < n; base += kPeakThreads) {
-    const int64_t k = base + threadIdx.x;
-    int flag = 0;
-    sep_peak rec;
+  for (int64_t ch = blockIdx.x; ch * kPeakChunk < n; ch += gridDim.x) {
+    const int64_t k = ch * kPeakChunk + threadIdx.x;
+    bool peak = false;
     const int64_t i = k < n ? idx[f * kcap + k] : -1;
     if (i >= 0 && i < p.npix && __ldg(p.bop + i) >= 0) {
+      int nk;
       const float vi = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
-      const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
-      const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
-      const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
-      int nk = 0;
-      for (int r = rlo; r <= rhi; ++r)
-        for (int c = clo; c <= chi; ++c) nk += is_kept(bm, (int64_t)r * p.cols + c);
-      bool ok = nk >= min_count;
-      // the maximum of the patch over valid pixels; ties go to the lowest index
-      for (int r = rlo; ok && r <= rhi; ++r)
-        for (int c = clo; ok && c <= chi; ++c) {
-          const int64_t j = (int64_t)r * p.cols + c;
-          if (j == i || __ldg(p.bop + j) < 0) continue;
-          const float vj = pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
-          if (!(vi > vj || (vi == vj && i < j))) ok = false;
-        }
-      if (ok) {
-        float I = 0.f, sy = 0.f, sx = 0.f, s2 = 0.f;
-        for (int r = rlo; r <= rhi; ++r)
-          for (int c = clo; c <= chi; ++c) {
-            const int64_t j = (int64_t)r * p.cols + c;
-            if (!is_kept(bm, j)) continue;
-            const int32_t bj = __ldg(p.bop + j);
-            const float vj = j == i ? vi : pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
-            const float w = vj - __ldg(mu + bj);
-            const float s = __ldg(sd + bj);
-            I += w;
-            sy += w * ((float)r + 0.5f);
-            sx += w * ((float)c + 0.5f);
-            s2 += s * s;
-          }
-        rec.idx = (int32_t)i;
-        rec.I = I;
-        rec.y = sy / I;
-        rec.x = sx / I;
-        rec.sigma = sqrtf(s2);
-        rec.npix = nk;
-        flag = 1;
-      }
+      peak = peak_test<DT, NORM>(p, frame, bm, i, h, min_count, vi, nk);
     }
-    int tile_total;
-    int off = block_exclusive_scan<kPeakThreads>(flag, &tile_total, sh);
-    if (flag && total + off < pcap) peaks[f * pcap + total + off] = rec;
-    total += tile_total;
+    const uint32_t m = __ballot_sync(0xffffffffu, peak);
+    if ((threadIdx.x & 31) == 0) flags[f * ((int64_t)n_chunks * 8) + ch * 8 + (threadIdx.x >> 5)] = m;
+    const int c = __syncthreads_count(peak);
+    if (threadIdx.x == 0) chunk_cnt[f * n_chunks + ch] = c;
   }
+}
+
+// Phase 2 (one CTA per frame): prefix over chunk counts, then every flagged
+// entry writes its record at its rank: ascending pixel order, since the
+// kept list ascends.
+template <int DT, bool NORM>
+__global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, const float* mean, const float* sigma,
+                                                    const uint32_t* bitmap, int64_t words, const int32_t* idx,
+                                                    const int32_t* n_kept, int64_t kcap, int32_t patch,
+                                                    const uint32_t* flags, int32_t* chunk_cnt, int32_t n_chunks,
+                                                    sep_peak* peaks, int64_t pcap, int32_t* n_peaks,
+                                                    int32_t* status) {
+  __shared__ int sh[32];
+  const int64_t f = blockIdx.x;
+  int64_t n = n_kept[f];
+  if (n > kcap) n = kcap;
+  const int nch = (int)((n + kPeakChunk - 1) / kPeakChunk);
+  // chunk counts become chunk offsets, in place (a count <= kcap < 2^31)
+  int32_t* chunk_base = chunk_cnt + f * n_chunks;
+  int64_t total = 0;
+  for (int c0 = 0; c0 < nch; c0 += 1024) {
+    const int c = c0 + threadIdx.x;
+    const int x = c < nch ? chunk_base[c] : 0;
+    int tt;
+    const int off = block_exclusive_scan<1024>(x, &tt, sh);
+    if (c < nch) chunk_base[c] = (int32_t)(total + off);
+    total += tt;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     n_peaks[f] = (int32_t)total;
     if (total > pcap) atomicOr(status, SEP_DEV_CAPACITY);
+  }
+  const uint32_t* bm = bitmap + f * words;
+  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
+  const float* mu = mean + (int64_t)f * nbins;
+  const float* sd = sigma + (int64_t)f * nbins;
+  const int h = patch >> 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t* fl = flags + f * ((int64_t)n_chunks * 8);
+  // one warp per chunk; one lane per flag bit of a word
+  for (int c = warp; c < nch; c += 32) {
+    int64_t rank = chunk_base[c];
+    for (int wd = 0; wd < 8; ++wd) {
+      const uint32_t m = fl[c * 8 + wd];
+      if (m == 0) continue;
+      if ((m >> lane) & 1u) {
+        const int64_t pos = rank + __popc(m & ((1u << lane) - 1u));
+        const int64_t k = (int64_t)c * kPeakChunk + wd * 32 + lane;
+        const int64_t i = idx[f * kcap + k];
+        if (pos < pcap) {
+          const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
+          const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
+          const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
+          float I = 0.f, sy = 0.f, sx = 0.f, s2 = 0.f;
+          int nk = 0;
+          for (int r = rlo; r <= rhi; ++r)
+            for (int cc = clo; cc <= chi; ++cc) {
+              const int64_t j = (int64_t)r * p.cols + cc;
+              if (!is_kept(bm, j)) continue;
+              const int32_t bj = __ldg(p.bop + j);
+              const float vj = pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
+              const float w = vj - __ldg(mu + bj);
+              const float s = __ldg(sd + bj);
+              ++nk;
+              I += w;
+              sy += w * ((float)r + 0.5f);
+              sx += w * ((float)cc + 0.5f);
+              s2 += s * s;
+            }
+          sep_peak rec;
+          rec.idx = (int32_t)i;
+          rec.I = I;
+          rec.y = sy / I;
+          rec.x = sx / I;
+          rec.sigma = sqrtf(s2);
+          rec.npix = nk;
+          peaks[f * pcap + pos] = rec;
+        }
+      }
+      rank += __popc(m);
+    }
   }
 }
 
@@ -231,17 +334,26 @@ cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const
   return cudaGetLastError();
 }
 
+int32_t compact_tiles(int64_t words) { return (int32_t)((words + kTileWords - 1) / kTileWords); }
+int32_t peak_chunks(int64_t kcap) { return (int32_t)((kcap + kPeakChunk - 1) / kPeakChunk); }
+
 cudaError_t launch_compact(const PixArgs& p, int32_t n_frames, const uint32_t* bitmap, int64_t words, int32_t* idx,
-                           float* val, int64_t cap, int32_t* n_kept, int32_t* status, cudaStream_t s) {
+                           float* val, int64_t cap, int32_t* n_kept, int32_t* scratch, int32_t* status,
+                           cudaStream_t s) {
   if (n_frames <= 0) return cudaSuccess;
+  const int32_t nt = compact_tiles(words);
+  dim3 grid((unsigned)nt, (unsigned)n_frames);
+  k_count_bits<<<grid, 256, 0, s>>>(bitmap, words, scratch, nt);
   const bool nrm = p.norm != nullptr;
+#define SEP_EMIT_ARGS p, bitmap, words, scratch, nt, idx, val, cap, n_kept, status
   if (p.dtype == SEP_DTYPE_U16_JF) {
-    if (nrm) k_compact<SEP_DTYPE_U16_JF, true><<<n_frames, kCompactThreads, 0, s>>>(p, bitmap, words, idx, val, cap, n_kept, status);
-    else k_compact<SEP_DTYPE_U16_JF, false><<<n_frames, kCompactThreads, 0, s>>>(p, bitmap, words, idx, val, cap, n_kept, status);
+    if (nrm) k_emit_kept<SEP_DTYPE_U16_JF, true><<<grid, kCompactThreads, 0, s>>>(SEP_EMIT_ARGS);
+    else k_emit_kept<SEP_DTYPE_U16_JF, false><<<grid, kCompactThreads, 0, s>>>(SEP_EMIT_ARGS);
   } else {
-    if (nrm) k_compact<SEP_DTYPE_F32, true><<<n_frames, kCompactThreads, 0, s>>>(p, bitmap, words, idx, val, cap, n_kept, status);
-    else k_compact<SEP_DTYPE_F32, false><<<n_frames, kCompactThreads, 0, s>>>(p, bitmap, words, idx, val, cap, n_kept, status);
+    if (nrm) k_emit_kept<SEP_DTYPE_F32, true><<<grid, kCompactThreads, 0, s>>>(SEP_EMIT_ARGS);
+    else k_emit_kept<SEP_DTYPE_F32, false><<<grid, kCompactThreads, 0, s>>>(SEP_EMIT_ARGS);
   }
+#undef SEP_EMIT_ARGS
   return cudaGetLastError();
 }
 
@@ -254,21 +366,44 @@ cudaError_t launch_scatter_list(int32_t n_frames, const int32_t* idx, const int3
 }
 
 cudaError_t launch_peaks(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* mean, const float* sigma,
-                         const uint32_t* bitmap, int64_t words, const int32_t* idx,
-                         const int32_t* n_kept, int64_t kcap, int32_t patch, int32_t min_count, sep_peak* peaks,
-                         int64_t pcap, int32_t* n_peaks, int32_t* status, cudaStream_t s) {
+                         const uint32_t* bitmap, int64_t words, const int32_t* idx, const int32_t* n_kept, int64_t kcap,
+                         int32_t patch, int32_t min_count, sep_peak* peaks, int64_t pcap, int32_t* n_peaks,
+                         int32_t* scratch, int32_t* status, cudaStream_t s) {
   if (n_frames <= 0) return cudaSuccess;
+  const int32_t nch = peak_chunks(kcap);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(scratch);
+  int32_t* cnt = scratch + (int64_t)n_frames * nch * 8;
+  dim3 g1((unsigned)std::min<int32_t>(std::max<int32_t>(nch, 1), kPeakCtasPerFrame), (unsigned)n_frames);
   const bool nrm = p.norm != nullptr;
-#define SEP_PEAK_ARGS p, nbins, mean, sigma, bitmap, words, idx, n_kept, kcap, patch, min_count, peaks, pcap, n_peaks, status
+#define SEP_FLAG_ARGS p, bitmap, words, idx, n_kept, kcap, patch, min_count, flags, cnt, nch
+#define SEP_PEMIT_ARGS p, nbins, mean, sigma, bitmap, words, idx, n_kept, kcap, patch, flags, cnt, nch, peaks, pcap, n_peaks, status
   if (p.dtype == SEP_DTYPE_U16_JF) {
-    if (nrm) k_peaks<SEP_DTYPE_U16_JF, true><<<n_frames, kPeakThreads, 0, s>>>(SEP_PEAK_ARGS);
-    else k_peaks<SEP_DTYPE_U16_JF, false><<<n_frames, kPeakThreads, 0, s>>>(SEP_PEAK_ARGS);
+    if (nrm) {
+      k_peak_flags<SEP_DTYPE_U16_JF, true><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
+      k_peak_emit<SEP_DTYPE_U16_JF, true><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+    } else {
+      k_peak_flags<SEP_DTYPE_U16_JF, false><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
+      k_peak_emit<SEP_DTYPE_U16_JF, false><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+    }
   } else {
-    if (nrm) k_peaks<SEP_DTYPE_F32, true><<<n_frames, kPeakThreads, 0, s>>>(SEP_PEAK_ARGS);
-    else k_peaks<SEP_DTYPE_F32, false><<<n_frames, kPeakThreads, 0, s>>>(SEP_PEAK_ARGS);
+    if (nrm) {
+      k_peak_flags<SEP_DTYPE_F32, true><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
+      k_peak_emit<SEP_DTYPE_F32, true><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+    } else {
+      k_peak_flags<SEP_DTYPE_F32, false><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
+      k_peak_emit<SEP_DTYPE_F32, false><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+    }
   }
-#undef SEP_PEAK_ARGS
+#undef SEP_FLAG_ARGS
+#undef SEP_PEMIT_ARGS
   return cudaGetLastError();
+}
+
+// scratch words needed by launch_compact and launch_peaks for F frames
+int64_t consumer_scratch_words(int32_t n_frames, int64_t words, int64_t kcap) {
+  const int64_t a = (int64_t)n_frames * compact_tiles(words);
+  const int64_t b = (int64_t)n_frames * peak_chunks(kcap) * 9;
+  return a > b ? a : b;
 }
 
 }  // namespace sep

@@ -50,7 +50,15 @@ int64_t bitmap_words(int64_t npix) {
   return (w + 7) & ~(int64_t)7;   // 32-byte multiple: vector loads per frame stay aligned
 }
 
-sep_status ensure_scratch(sep_ctx* ctx, int64_t bitmap_total, int64_t thr_total) {
+sep_status ensure_scratch(sep_ctx* ctx, int64_t bitmap_total, int64_t thr_total, int64_t aux_total = 0) {
+  if ((size_t)aux_total > ctx->aux_len) {
+    if (ctx->d_aux) cudaFree(ctx->d_aux);
+    ctx->d_aux = nullptr;
+    ctx->aux_len = 0;
+    cudaError_t e = cudaMalloc((void**)&ctx->d_aux, (size_t)aux_total * 4);
+    if (e != cudaSuccess) return fail(ctx, SEP_ERR_OOM, "consumer scratch allocation failed");
+    ctx->aux_len = (size_t)aux_total;
+  }
   if ((size_t)bitmap_total > ctx->bitmap_words) {
     if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
     ctx->d_bitmap = nullptr;
@@ -120,8 +128,7 @@ sep::PixArgs pix_args(const sep_csr* csr, const sep_calib* calib, const void* fr
 sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
   int optin = 0;
   SEP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  const bool weighted = csr->h.split > 1 || csr->has_norm;
-  const size_t need = sep::clip_smem_bytes(csr->h.max_row, weighted) + 1024;  // + static shared memory
+  const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->has_norm) + 1024;  // + static shared memory
   if (need > (size_t)optin) {
     char buf[160];
     snprintf(buf, sizeof buf, "largest bin (%d entries) needs %zu bytes of shared memory, device allows %d",
@@ -143,6 +150,8 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
                         float* bounds, int32_t* iters, uint32_t* bitmap, int64_t words) {
   sep::ClipArgs a;
   a.rowptr = csr->d_rowptr;
+  a.grp = csr->d_grp;
+  a.cal0 = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_cal0 : nullptr;
   a.ent = csr->d_ent;
   a.w = csr->d_w;
   a.norm = csr->d_norm;
@@ -204,6 +213,7 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
+  if (ctx->d_aux) cudaFree(ctx->d_aux);
   delete ctx;
 }
 
@@ -254,6 +264,7 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
   if ((st = upload(ctx, &c->d_rowptr, c->h.rowptr.data(), c->h.rowptr.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_ent, c->h.ent.data(), c->h.ent.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
       (c->has_norm && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
       (c->has_norm && (st = upload(ctx, &c->d_norm, norm_host, (size_t)c->npix)) != SEP_OK)) {
     sep_csr_destroy(c);
@@ -275,6 +286,7 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_w);
   cudaFree(csr->d_norm);
   cudaFree(csr->d_bop);
+  cudaFree(csr->d_grp);
   delete csr;
 }
 
@@ -298,7 +310,8 @@ sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, flo
   const HostCsr& h = csr->h;
   if (rowptr) memcpy(rowptr, h.rowptr.data(), h.rowptr.size() * 4);
   if (col)
-    for (size_t e = 0; e < h.ent.size(); ++e) col[e] = (int32_t)(h.ent[e] & sep::kColMask);
+    for (size_t e = 0; e < h.ent.size(); ++e)
+      col[e] = (h.ent[e] & sep::kPad) ? -1 : (int32_t)(h.ent[e] & sep::kColMask);
   if (coef) memcpy(coef, h.coef.data(), h.coef.size() * 4);
   if (bin_of_pixel) memcpy(bin_of_pixel, h.bop.data(), h.bop.size() * 4);
   if (bin_centers) memcpy(bin_centers, h.centers.data(), h.centers.size() * 4);
@@ -323,6 +336,27 @@ sep_status sep_calib_create(sep_ctx* ctx, const sep_csr* csr, const float* ped_h
     sep_calib_destroy(c);
     return st;
   }
+  // level-0 pedestal and gain copied into matrix-row order: the clip kernel
+  // reads them with the entries (coalesced) instead of gathering by pixel
+  try {
+    const sep::HostCsr& h = csr->h;
+    std::vector<float2> cal0(h.ent.size());
+    for (size_t e = 0; e < h.ent.size(); ++e) {
+      if (h.ent[e] & sep::kPad) {
+        cal0[e] = make_float2(0.0f, 1.0f);
+      } else {
+        const size_t col = h.ent[e] & sep::kColMask;
+        cal0[e] = make_float2(ped_host[col], gain_host[col]);
+      }
+    }
+    if ((st = upload(ctx, &c->d_cal0, cal0.data(), cal0.size())) != SEP_OK) {
+      sep_calib_destroy(c);
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    sep_calib_destroy(c);
+    return fail(ctx, SEP_ERR_OOM, "host allocation failed");
+  }
   *out = c;
   return SEP_OK;
 }
@@ -332,6 +366,7 @@ void sep_calib_destroy(sep_calib* calib) {
   if (calib->ctx) cudaSetDevice(calib->ctx->device);
   cudaFree(calib->d_ped);
   cudaFree(calib->d_gain);
+  cudaFree(calib->d_cal0);
   delete calib;
 }
 
@@ -363,14 +398,16 @@ sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
     return fail(ctx, SEP_ERR_ARG, "NULL argument");
   if (n_frames == 0) return SEP_OK;
   const int64_t words = bitmap_words(csr->npix);
-  if ((st = ensure_scratch(ctx, words * n_frames, (int64_t)n_frames * csr->h.nbins)) != SEP_OK) return st;
+  if ((st = ensure_scratch(ctx, words * n_frames, (int64_t)n_frames * csr->h.nbins,
+                           sep::consumer_scratch_words(n_frames, words, capacity))) != SEP_OK)
+    return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
   cudaError_t e = sep::launch_thresholds(mean_dev, sigma_dev, params->k_pick, (int64_t)n_frames * csr->h.nbins,
                                          ctx->d_thr, s);
   if (e == cudaSuccess) e = sep::launch_mark(p, n_frames, csr->h.nbins, ctx->d_thr, ctx->d_bitmap, words, s);
   if (e == cudaSuccess)
-    e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, capacity, n_kept_dev,
+    e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, capacity, n_kept_dev, ctx->d_aux,
                             ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparsify launch");
   return SEP_OK;
@@ -389,7 +426,9 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
     return fail(ctx, SEP_ERR_ARG, "NULL argument");
   if (n_frames == 0) return SEP_OK;
   const int64_t words = bitmap_words(csr->npix);
-  if ((st = ensure_scratch(ctx, words * n_frames, 0)) != SEP_OK) return st;
+  if ((st = ensure_scratch(ctx, words * n_frames, 0, sep::consumer_scratch_words(n_frames, words, kept_capacity))) !=
+      SEP_OK)
+    return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
   cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
@@ -398,7 +437,7 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   if (e == cudaSuccess)
     e = sep::launch_peaks(p, n_frames, csr->h.nbins, mean_dev, sigma_dev, ctx->d_bitmap, words, idx_dev, n_kept_dev,
                           kept_capacity, params->patch, params->min_count, peaks_dev, capacity, n_peaks_dev,
-                          ctx->d_status, s);
+                          ctx->d_aux, ctx->d_status, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "peakfind launch");
   return SEP_OK;
 }
@@ -417,7 +456,9 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
   const int64_t words = bitmap_words(csr->npix);
-  if ((st = ensure_scratch(ctx, words * n_frames, 0)) != SEP_OK) return st;
+  if ((st = ensure_scratch(ctx, words * n_frames, 0, sep::consumer_scratch_words(n_frames, words, kept_capacity))) !=
+      SEP_OK)
+    return st;
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
@@ -429,11 +470,11 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
       e = sep::launch_integrate_clip(a, dtype, csr->h.split > 1, csr->has_norm, params->precision, mode, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
-                              ctx->d_status, s);
+                              ctx->d_aux, ctx->d_status, s);
     if (e == cudaSuccess)
       e = sep::launch_peaks(p, n_frames, csr->h.nbins, mean_dev, sigma_dev, ctx->d_bitmap, words, idx_dev,
                             n_kept_dev, kept_capacity, params->patch, params->min_count, peaks_dev, peak_capacity,
-                            n_peaks_dev, ctx->d_status, s);
+                            n_peaks_dev, ctx->d_aux, ctx->d_status, s);
     return e;
   };
 
@@ -449,7 +490,8 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)(uintptr_t)idx_dev, (uint64_t)(uintptr_t)val_dev, (uint64_t)kept_capacity,
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev,
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
-                               (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)s};
+                               (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
+                               (uint64_t)(uintptr_t)s};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));

@@ -141,35 +141,57 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     }
   }
 
-  // counting sort by bin; pixels visited in ascending order keep columns sorted
-  std::vector<int64_t> cnt((size_t)B + 1, 0);
+  // Row layout (one row per bin): entries grouped by coefficient class,
+  // largest coefficient first (class c holds k = s*s - c sub-pixels, c = 0 ..
+  // s*s - 1), then the weight-0 centre carriers; columns ascend inside a
+  // group; every group is padded with flagged entries to a multiple of 4 so
+  // the kernels move 4 entries per vector access and apply a class's weight
+  // once per group instead of once per entry.
+  const int NC = s * s + 1;                 // coefficient classes + carriers
+  std::vector<int64_t> cc((size_t)B * NC, 0);
   for (int64_t i = 0; i < npix; ++i)
-    for (int t = 0; t < pn[i]; ++t) cnt[(size_t)pb[(size_t)i * maxe + t] + 1] += 1;
-  for (int32_t b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
-  const int64_t nnz = cnt[B];
-  if (nnz > (int64_t)std::numeric_limits<int32_t>::max()) return "too many nonzeros";
+    for (int t = 0; t < pn[i]; ++t) {
+      const int k = pk[(size_t)i * maxe + t];
+      const int c = k == 0 ? NC - 1 : s * s - k;
+      cc[(size_t)pb[(size_t)i * maxe + t] * NC + c] += 1;
+    }
+  auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
   out->rowptr.assign((size_t)B + 1, 0);
+  out->grp.assign((size_t)B * 4, 0);
+  std::vector<int64_t> fill((size_t)B * NC, 0);
+  int64_t pos = 0;
   int32_t max_row = 0;
-  for (int32_t b = 0; b <= B; ++b) out->rowptr[b] = (int32_t)cnt[b];
-  for (int32_t b = 0; b < B; ++b) max_row = std::max(max_row, out->rowptr[b + 1] - out->rowptr[b]);
-  out->ent.assign((size_t)nnz, 0);
+  for (int32_t b = 0; b < B; ++b) {
+    const int64_t r0 = pos;
+    for (int c = 0; c < NC; ++c) {
+      fill[(size_t)b * NC + c] = pos;
+      pos += pad4(cc[(size_t)b * NC + c]);
+      if (c < 4) out->grp[(size_t)b * 4 + c] = (int32_t)(pos - r0);
+    }
+    for (int c = NC - 1; c < 4; ++c) out->grp[(size_t)b * 4 + c] = out->grp[(size_t)b * 4 + (NC - 2)];
+    if (pos > (int64_t)std::numeric_limits<int32_t>::max()) return "too many nonzeros";
+    out->rowptr[b + 1] = (int32_t)pos;
+    max_row = std::max(max_row, (int32_t)(pos - r0));
+  }
+  const int64_t nnz = pos;
+  out->ent.assign((size_t)nnz, kPad);
   out->coef.assign((size_t)nnz, 0.0f);
   if (norm) out->w.assign((size_t)nnz, 0.0f);
-  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
   const double inv = 1.0 / (double)(s * s);
   for (int64_t i = 0; i < npix; ++i) {
     for (int t = 0; t < pn[i]; ++t) {
-      int32_t b = pb[(size_t)i * maxe + t];
-      int k = pk[(size_t)i * maxe + t];
-      int64_t e = fill[b]++;
+      const int32_t b = pb[(size_t)i * maxe + t];
+      const int k = pk[(size_t)i * maxe + t];
+      const int c = k == 0 ? NC - 1 : s * s - k;
+      const int64_t e = fill[(size_t)b * NC + c]++;
       uint32_t u = (uint32_t)i;
       if (k == 0) u |= kZero;
       else u |= (uint32_t)(k - 1) << kKShift;
       if (b == bop[i]) u |= kCentre;
       out->ent[e] = u;
-      double c = (double)k * inv;
-      out->coef[e] = (float)c;
-      if (norm) out->w[e] = (float)(c * (double)norm[i]);
+      const double cf = (double)k * inv;
+      out->coef[e] = (float)cf;
+      if (norm) out->w[e] = (float)(cf * (double)norm[i]);
     }
   }
   out->rows = gm.rows;

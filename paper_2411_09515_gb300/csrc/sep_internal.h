@@ -17,18 +17,21 @@
 //   bits 25..26  k - 1 where k / split^2 is the coefficient c_{i,r} (k = 1..4)
 //   bit  27      the entry's bin is the pixel's centre bin (threshold bin)
 //   bit  28      zero coefficient: the entry exists only to carry bit 27
+//   bit  29      padding (no pixel): groups are padded to 4 entries
 namespace sep {
 constexpr uint32_t kColBits = 25;
 constexpr uint32_t kColMask = (1u << kColBits) - 1u;
 constexpr uint32_t kKShift = 25;
 constexpr uint32_t kCentre = 1u << 27;
 constexpr uint32_t kZero = 1u << 28;
+constexpr uint32_t kPad = 1u << 29;
 
 // Host-built matrix (own FP64 implementation of Section 2.2's coefficients).
 struct HostCsr {
   int32_t rows = 0, cols = 0, nbins = 0, split = 1;
   double lo = 0, hi = 0;
-  std::vector<int32_t> rowptr;   // [nbins + 1]
+  std::vector<int32_t> rowptr;   // [nbins + 1], multiples of 4
+  std::vector<int32_t> grp;      // [nbins][4]: end of coefficient class 0..3 within the row
   std::vector<uint32_t> ent;     // [nnz] packed
   std::vector<float> coef;       // [nnz] c_{i,r} (0 for centre-only entries)
   std::vector<float> w;          // [nnz] c * norm (only with a norm)
@@ -43,6 +46,8 @@ std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const flo
 // ---- kernel launch parameters -------------------------------------------
 struct ClipArgs {
   const int32_t* rowptr;
+  const int32_t* grp;      // [nbins][4] class ends within a row
+  const float2* cal0;      // per entry (ped, gain) of level 0 (raw input)
   const uint32_t* ent;
   const float* w;          // per-entry weight c * norm (NORM variant)
   const float* norm;       // per-pixel norm (NORM variant)
@@ -81,15 +86,21 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
                               cudaStream_t s);
 cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* thr, uint32_t* bitmap,
                         int64_t words, cudaStream_t s);
+// Ordered compaction of the kept-pixel bitmap (two launches; scratch holds
+// per-tile counts) and peak picking over the kept list (two launches;
+// scratch holds flag bits and per-chunk counts). consumer_scratch_words gives
+// the int32 scratch both need.
 cudaError_t launch_compact(const PixArgs& p, int32_t n_frames, const uint32_t* bitmap, int64_t words,
-                           int32_t* idx, float* val, int64_t cap, int32_t* n_kept, int32_t* status,
-                           cudaStream_t s);
+                           int32_t* idx, float* val, int64_t cap, int32_t* n_kept, int32_t* scratch,
+                           int32_t* status, cudaStream_t s);
+int64_t consumer_scratch_words(int32_t n_frames, int64_t words, int64_t kcap);
 cudaError_t launch_scatter_list(int32_t n_frames, const int32_t* idx, const int32_t* n_kept, int64_t kcap,
                                 int64_t npix, uint32_t* bitmap, int64_t words, cudaStream_t s);
 cudaError_t launch_peaks(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* mean, const float* sigma,
                          const uint32_t* bitmap, int64_t words, const int32_t* idx,
                          const int32_t* n_kept, int64_t kcap, int32_t patch, int32_t min_count,
-                         sep_peak* peaks, int64_t pcap, int32_t* n_peaks, int32_t* status, cudaStream_t s);
+                         sep_peak* peaks, int64_t pcap, int32_t* n_peaks, int32_t* scratch, int32_t* status,
+                         cudaStream_t s);
 }  // namespace sep
 
 // ---- handles --------------------------------------------------------------
@@ -109,6 +120,8 @@ struct sep_ctx {
   size_t bitmap_words = 0;
   float* d_thr = nullptr;
   size_t thr_len = 0;
+  int32_t* d_aux = nullptr;    // consumer scratch (tile counts, flag bits)
+  size_t aux_len = 0;
   // captured batches, keyed by every launch argument
   std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
   uint64_t use_clock = 0;
@@ -124,6 +137,7 @@ struct sep_csr {
   float* d_w = nullptr;
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
+  int32_t* d_grp = nullptr;
 };
 
 struct sep_calib {
@@ -132,4 +146,5 @@ struct sep_calib {
   int64_t npix = 0;
   float* d_ped = nullptr;
   float* d_gain = nullptr;
+  float2* d_cal0 = nullptr;    // per matrix entry: (pedestal, gain) of level 0, in row order
 };

@@ -23,11 +23,16 @@ PEAK_RTOL = 1e-4
 
 
 def close(a, b, rtol=RTOL, sd=None):
+    """|a - b| <= rtol |b|; where the bin's deviation sd is 0 the bound is
+    1e-6 max(1, |b|); with a deviation, an absolute floor of 1e-7 sd (one
+    FP32 rounding of the bin's spread) covers means that sit near zero
+    relative to their spread, which have no relative precision in FP32."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     tol = rtol * np.abs(b)
     if sd is not None:
-        tol = np.where(sd == 0, 1e-6 * np.maximum(1.0, np.abs(b)), tol)
+        sd = np.asarray(sd, np.float64)
+        tol = np.where(sd == 0, 1e-6 * np.maximum(1.0, np.abs(b)), tol + 1e-7 * sd)
     return np.abs(a - b) <= tol + 1e-30
 
 
