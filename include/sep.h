@@ -230,6 +230,32 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                              int64_t peak_capacity, int32_t* n_peaks_dev, int32_t use_graph,
                              sep_stream stream);
 
+/*
+ * sep_sparsify with no allocation during the call (the paper has no
+ * counterpart; this is an interface for callers, not part of the method).
+ * sep_sparsify grows context-owned scratch with cudaMalloc when a batch needs
+ * more; callers that must not allocate at call time (code being recorded into
+ * a CUDA graph, real-time acquisition threads, processes whose device memory
+ * is fixed after start-up) use this variant instead. Its scratch is one
+ * static 16 MiB device array in the library, which every GPU that loads the
+ * library holds until exit. Arguments, outputs and results are those of
+ * sep_sparsify.
+ *  - Limit: n_frames * (bitmap bytes ceil(npix/32)*4 rounded up to 32, plus
+ *    4 * nbins, plus 4 per 8192 bitmap words) must fit 16 MiB (about 28
+ *    Jungfrau-4M frames, about 1900 frames of 256 x 256); larger batches
+ *    return SEP_ERR_ARG before any launch (split the batch).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, no allocation); make that first call before any
+ *    stream capture.
+ *  - All calls share the array, which keeps the last call's contents; calls
+ *    that overlap on the GPU (other streams or host threads) race on it.
+ */
+sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
+                                const void* frames_dev, int32_t dtype, int32_t n_frames,
+                                const sep_params* params, const float* mean_dev,
+                                const float* sigma_dev, int32_t* idx_dev, float* val_dev,
+                                int64_t capacity, int32_t* n_kept_dev, sep_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

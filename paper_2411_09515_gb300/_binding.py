@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OO
 # every symbol include/sep.h declares
 EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error", "sep_get_device_status",
            "sep_build_csr", "sep_csr_destroy", "sep_csr_info", "sep_csr_export", "sep_calib_create",
-           "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch"]
+           "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch",
+           "sep_sparsify_noalloc"]
 
 
 class SepError(RuntimeError):
@@ -83,6 +84,8 @@ def lib():
                                      _vp, _vp, _vp]
     L.sep_sparsify.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
                                C.c_int64, _vp, _vp]
+    L.sep_sparsify_noalloc.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
+                                       _vp, C.c_int64, _vp, _vp]
     L.sep_peakfind.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
@@ -219,6 +222,13 @@ def sep_sparsify(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, 
                  stream=None):
     _check(ctx, lib().sep_sparsify(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
                                    _ptr(sigma), _ptr(idx), _ptr(val), capacity, _ptr(n_kept), _stream(stream)))
+
+
+def sep_sparsify_noalloc(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, val, capacity, n_kept,
+                         stream=None):
+    _check(ctx, lib().sep_sparsify_noalloc(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params),
+                                           _ptr(mean), _ptr(sigma), _ptr(idx), _ptr(val), capacity, _ptr(n_kept),
+                                           _stream(stream)))
 
 
 def sep_peakfind(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, n_kept, kept_capacity, peaks,
