@@ -231,6 +231,31 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                              sep_stream stream);
 
 /*
+ * Schedule of the integrate + clip kernel for one matrix (a tuning choice,
+ * results do not depend on it): bins are grouped by row length into
+ * n_classes size classes (1..4; class i holds rows with thresholds[i-1] < n
+ * <= thresholds[i], ascending, n_classes - 1 thresholds), each launched with
+ * tpb[i] threads per block (64, 128 or 256) and shared memory for its own
+ * longest row; classes run as parallel branches. Default: one class, 256.
+ */
+sep_status sep_csr_set_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds,
+                            const int32_t* tpb);
+/* Current plan: *n_classes, thresholds[n_classes-1], tpb[n_classes] (arrays of 4). */
+sep_status sep_csr_get_plan(const sep_csr* csr, int32_t* n_classes, int32_t* thresholds, int32_t* tpb);
+/*
+ * Time candidate plans (single class at 64/128/256 threads; two classes split
+ * at 1024/2048/4096/8192 entries with every block-size pair) on a sample
+ * batch of device frames with sep_integrate_clip's work, keep the fastest on
+ * csr and report its time per call in *best_ms (may be NULL). cache_path
+ * (may be NULL): a text file keyed by detector shape, matrix, dtype,
+ * precision and device name; a plan found there is applied without timing,
+ * a new one is appended. Allocates and frees a temporary output buffer.
+ */
+sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, const void* frames_dev,
+                        int32_t dtype, int32_t n_frames, const sep_params* params, const char* cache_path,
+                        float* best_ms, sep_stream stream);
+
+/*
  * sep_sparsify with no allocation during the call (the paper has no
  * counterpart; this is an interface for callers, not part of the method).
  * sep_sparsify grows context-owned scratch with cudaMalloc when a batch needs

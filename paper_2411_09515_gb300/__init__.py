@@ -75,6 +75,19 @@ class Separator:
         except Exception:
             pass
 
+    def set_plan(self, tpb, thresholds=()):
+        """Clip-kernel schedule: size classes of bins and threads per block."""
+        B.sep_csr_set_plan(self.ctx, self.csr, tpb, thresholds)
+
+    def get_plan(self):
+        return B.sep_csr_get_plan(self.csr)
+
+    def autotune(self, frames, cache_path=None, stream=None):
+        """Time candidate schedules on a sample batch and keep the fastest."""
+        F = self._check_frames(frames)
+        return B.sep_autotune(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, self.params,
+                              cache_path, stream)
+
     def set_params(self, **kw):
         for k, v in kw.items():
             setattr(self.params, k, v)

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OO
 EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error", "sep_get_device_status",
            "sep_build_csr", "sep_csr_destroy", "sep_csr_info", "sep_csr_export", "sep_calib_create",
            "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch",
-           "sep_sparsify_noalloc"]
+           "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune"]
 
 
 class SepError(RuntimeError):
@@ -86,6 +86,10 @@ def lib():
                                C.c_int64, _vp, _vp]
     L.sep_sparsify_noalloc.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
                                        _vp, C.c_int64, _vp, _vp]
+    L.sep_csr_set_plan.argtypes = [_vp, _vp, C.c_int32, _vp, _vp]
+    L.sep_csr_get_plan.argtypes = [_vp, _vp, _vp, _vp]
+    L.sep_autotune.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), C.c_char_p,
+                               C.POINTER(C.c_float), _vp]
     L.sep_peakfind.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
@@ -229,6 +233,31 @@ def sep_sparsify_noalloc(ctx, csr, calib, frames, dtype, n_frames, params, mean,
     _check(ctx, lib().sep_sparsify_noalloc(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params),
                                            _ptr(mean), _ptr(sigma), _ptr(idx), _ptr(val), capacity, _ptr(n_kept),
                                            _stream(stream)))
+
+
+def sep_csr_set_plan(ctx, csr, tpb, thresholds=()):
+    t = np.ascontiguousarray(list(thresholds) + [0] * (4 - len(thresholds)), np.int32)
+    b = np.ascontiguousarray(list(tpb) + [256] * (4 - len(tpb)), np.int32)
+    _check(ctx, lib().sep_csr_set_plan(ctx, csr, len(tpb), _ptr(t), _ptr(b)))
+
+
+def sep_csr_get_plan(csr):
+    n = np.zeros(1, np.int32)
+    t = np.zeros(4, np.int32)
+    b = np.zeros(4, np.int32)
+    st = lib().sep_csr_get_plan(csr, _ptr(n), _ptr(t), _ptr(b))
+    if st != SEP_OK:
+        raise SepError(st, "sep_csr_get_plan")
+    k = int(n[0])
+    return {"tpb": b[:k].tolist(), "thresholds": t[: k - 1].tolist()}
+
+
+def sep_autotune(ctx, csr, calib, frames, dtype, n_frames, params, cache_path=None, stream=None):
+    ms = C.c_float(0)
+    _check(ctx, lib().sep_autotune(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params),
+                                   None if cache_path is None else str(cache_path).encode(), C.byref(ms),
+                                   _stream(stream)))
+    return ms.value
 
 
 def sep_peakfind(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, n_kept, kept_capacity, peaks,

@@ -1,7 +1,8 @@
 // Fused detector correction + CSR azimuthal integration + sigma-clipping.
 //
-// One CTA (256 threads) owns one radial bin (a row of the integration
-// matrix) and walks up to 8 frames. Per frame it gathers the bin's pixels
+// One CTA (64, 128 or 256 threads: a tuning choice per size class of bins)
+// owns one radial bin (a row of the integration matrix) and walks a group of
+// frames. Per frame it gathers the bin's pixels
 // once from the frame, corrects them (Section 1.2), and keeps the values in
 // shared memory; every clipping pass (Eq. 19, Section 2.4) then runs on chip.
 //
@@ -39,8 +40,6 @@
 namespace sep {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 
 enum { MODE_UNIT = 0, MODE_CLASS = 1, MODE_ENTRY = 2 };
 
@@ -128,7 +127,7 @@ __device__ __forceinline__ void clip_bounds(double mu, double sd, float k, float
 // Sum NV per-thread values over the CTA; lanes v < NV of warp 0 hold total v
 // on return (as double). Ends without a barrier: the caller's warp 0 works
 // on the totals and then synchronises.
-template <int NV, int PREC>
+template <int NV, int PREC, int kWarps>
 __device__ __forceinline__ double block_sum(float (&s)[NV], float (&c)[NV], float (*red_s)[kWarps],
                                             float (*red_c)[kWarps]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,8 +172,9 @@ __device__ __forceinline__ double block_sum(float (&s)[NV], float (&c)[NV], floa
   return tot;
 }
 
-template <int DT, int MODE, int PREC>
+template <int DT, int MODE, int PREC, int kThreads>
 __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
+  constexpr int kWarps = kThreads / 32;
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
   // MODE_UNIT: one class of weight 1; sums (count, S1, S2).
   // MODE_CLASS / MODE_ENTRY: sums (count, Omega, A1, OO, B1, B2).
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
   __shared__ float red_s[NV][kWarps], red_c[NV][kWarps];
   __shared__ Bcast st;
 
-  const int b = blockIdx.x;
+  const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
   const int f0 = blockIdx.y * a.frames_per_cta;
   const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
   const int r0 = __ldg(a.rowptr + b);
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
       s0[2] = v2;
     }
     {
-      const double t = block_sum<NV, SEP_PREC_PLAIN>(s0, c0, red_s, red_c);
+      const double t = block_sum<NV, SEP_PREC_PLAIN, kWarps>(s0, c0, red_s, red_c);
       // lanes 0, 1, 2 of warp 0 hold Omega, V, sum w v^2
       const double Om = __shfl_sync(0xffffffffu, t, 0);
       const double V = __shfl_sync(0xffffffffu, t, 1);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         ss[1] = om.s; cc[1] = om.c; ss[2] = a1.s; cc[2] = a1.c; ss[3] = oo.s; cc[3] = oo.c;
         ss[4] = b1.s; cc[4] = b1.c; ss[5] = b2.s; cc[5] = b2.c;
       }
-      const double tot = block_sum<NV, PREC>(ss, cc, red_s, red_c);
+      const double tot = block_sum<NV, PREC, kWarps>(ss, cc, red_s, red_c);
       if (warp == 0) {
         double t[NV];
 #pragma unroll
@@ -483,32 +483,43 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
 
 // mode 0: set the shared-memory attribute and launch; 1: attribute only
 // (done eagerly before a stream capture); 2: launch only.
-template <int DT, int MODE, int PREC>
-cudaError_t launch_t(const ClipArgs& a, int mode, cudaStream_t s) {
+template <int DT, int MODE, int PREC, int TPB>
+cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
   const size_t smem = clip_smem_bytes(a.cap, MODE == MODE_ENTRY);
-  auto k = k_integrate_clip<DT, MODE, PREC>;
+  auto k = k_integrate_clip<DT, MODE, PREC, TPB>;
   if (mode != 2) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess || mode == 1) return e;
   }
-  dim3 grid(a.nbins, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
-  k<<<grid, kThreads, smem, s>>>(a);
+  dim3 grid(n_ctas, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
+  k<<<grid, TPB, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+template <int DT, int MODE, int PREC>
+cudaError_t launch_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
+  switch (tpb) {
+    case 64: return launch_t<DT, MODE, PREC, 64>(a, n_ctas, mode, s);
+    case 128: return launch_t<DT, MODE, PREC, 128>(a, n_ctas, mode, s);
+    default: return launch_t<DT, MODE, PREC, 256>(a, n_ctas, mode, s);
+  }
+}
+
 template <int DT, int MODE>
-cudaError_t launch_p(const ClipArgs& a, int32_t prec, int mode, cudaStream_t s) {
+cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
   switch (prec) {
-    case SEP_PREC_PLAIN: return launch_t<DT, MODE, SEP_PREC_PLAIN>(a, mode, s);
-    case SEP_PREC_KAHAN: return launch_t<DT, MODE, SEP_PREC_KAHAN>(a, mode, s);
-    default: return launch_t<DT, MODE, SEP_PREC_FP64MERGE>(a, mode, s);
+    case SEP_PREC_PLAIN: return launch_b<DT, MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_KAHAN: return launch_b<DT, MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);
+    default: return launch_b<DT, MODE, SEP_PREC_FP64MERGE>(a, n_ctas, tpb, mode, s);
   }
 }
 
 template <int DT>
-cudaError_t launch_d(const ClipArgs& a, bool split, bool norm, int32_t prec, int mode, cudaStream_t s) {
-  if (norm) return launch_p<DT, MODE_ENTRY>(a, prec, mode, s);
-  return split ? launch_p<DT, MODE_CLASS>(a, prec, mode, s) : launch_p<DT, MODE_UNIT>(a, prec, mode, s);
+cudaError_t launch_d(const ClipArgs& a, int n_ctas, int tpb, bool split, bool norm, int32_t prec, int mode,
+                     cudaStream_t s) {
+  if (norm) return launch_p<DT, MODE_ENTRY>(a, n_ctas, tpb, prec, mode, s);
+  return split ? launch_p<DT, MODE_CLASS>(a, n_ctas, tpb, prec, mode, s)
+               : launch_p<DT, MODE_UNIT>(a, n_ctas, tpb, prec, mode, s);
 }
 
 }  // namespace
@@ -518,11 +529,11 @@ size_t clip_smem_bytes(int32_t cap, bool weighted) {
   return (smem + 15) & ~(size_t)15;
 }
 
-cudaError_t launch_integrate_clip(const ClipArgs& a, int32_t dtype, bool split, bool has_norm, int32_t precision,
-                                  int mode, cudaStream_t s) {
-  if (a.n_frames <= 0 || a.nbins <= 0) return cudaSuccess;
-  if (dtype == SEP_DTYPE_U16_JF) return launch_d<SEP_DTYPE_U16_JF>(a, split, has_norm, precision, mode, s);
-  return launch_d<SEP_DTYPE_F32>(a, split, has_norm, precision, mode, s);
+cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, int32_t dtype, bool split, bool has_norm,
+                                  int32_t precision, int mode, cudaStream_t s) {
+  if (a.n_frames <= 0 || n_ctas <= 0) return cudaSuccess;
+  if (dtype == SEP_DTYPE_U16_JF) return launch_d<SEP_DTYPE_U16_JF>(a, n_ctas, tpb, split, has_norm, precision, mode, s);
+  return launch_d<SEP_DTYPE_F32>(a, n_ctas, tpb, split, has_norm, precision, mode, s);
 }
 
 }  // namespace sep

@@ -138,6 +138,49 @@ sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
   return SEP_OK;
 }
 
+void free_plan(sep_csr* csr) {
+  for (auto& c : csr->plan) cudaFree(c.d_bins);
+  csr->plan.clear();
+}
+
+// Partition the bins by row length at the given thresholds (ascending); class
+// i holds rows with thr[i-1] < n <= thr[i], the last class everything longer.
+sep_status make_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds, const int32_t* tpb) {
+  if (n_classes < 1 || n_classes > 4) return fail(ctx, SEP_ERR_ARG, "1 to 4 classes");
+  for (int i = 0; i < n_classes; ++i) {
+    if (tpb[i] != 64 && tpb[i] != 128 && tpb[i] != 256) return fail(ctx, SEP_ERR_ARG, "threads per block: 64, 128 or 256");
+    if (i + 1 < n_classes && (thresholds[i] < 1 || (i > 0 && thresholds[i] <= thresholds[i - 1])))
+      return fail(ctx, SEP_ERR_ARG, "thresholds must ascend");
+  }
+  std::vector<std::vector<int32_t>> bins(n_classes);
+  const auto& rp = csr->h.rowptr;
+  for (int32_t b = 0; b < csr->h.nbins; ++b) {
+    const int32_t n = rp[b + 1] - rp[b];
+    int c = 0;
+    while (c + 1 < n_classes && n > thresholds[c]) ++c;
+    bins[c].push_back(b);
+  }
+  free_plan(csr);
+  for (int c = 0; c < n_classes; ++c) {
+    sep_clip_class k;
+    k.tpb = tpb[c];
+    k.threshold = c + 1 < n_classes ? thresholds[c] : 0;
+    if (bins[c].empty()) continue;
+    std::stable_sort(bins[c].begin(), bins[c].end(),
+                     [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+    k.n_bins = (int32_t)bins[c].size();
+    k.cap = std::max(rp[bins[c][0] + 1] - rp[bins[c][0]], 4);
+    sep_status st = upload(ctx, &k.d_bins, bins[c].data(), bins[c].size());
+    if (st != SEP_OK) {
+      free_plan(csr);
+      return st;
+    }
+    csr->plan.push_back(k);
+  }
+  csr->plan_version += 1;
+  return SEP_OK;
+}
+
 int frames_per_cta(const sep_ctx* ctx, int32_t n_frames, int32_t nbins) {
   // enough CTAs to fill the GPU several times over, at most 8 frames per CTA
   int64_t target = (int64_t)ctx->num_sms * 16;
@@ -176,6 +219,45 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   return a;
 }
 
+
+// Launch the clip kernel for every size class of the plan: one class on the
+// caller's stream, several as parallel branches (fork / join through events,
+// which a stream capture records as graph edges).
+cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int32_t dtype, int32_t precision,
+                         int mode, cudaStream_t s) {
+  const bool split = csr->h.split > 1;
+  if (csr->plan.empty()) {
+    a.bin_list = nullptr;
+    a.cap = std::max(csr->h.max_row, 4);
+    return sep::launch_integrate_clip(a, csr->h.nbins, 256, dtype, split, csr->has_norm, precision, mode, s);
+  }
+  const int nc = (int)csr->plan.size();
+  if (nc == 1 || mode == 1) {
+    for (const auto& k : csr->plan) {
+      a.bin_list = k.d_bins;
+      a.cap = k.cap;
+      a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
+      cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, dtype, split, csr->has_norm, precision, mode, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, s);
+  for (int i = 0; i < nc && e == cudaSuccess; ++i) {
+    const auto& k = csr->plan[i];
+    cudaStream_t si = i == 0 ? s : ctx->aux[i];
+    if (i > 0) e = cudaStreamWaitEvent(si, ctx->ev_fork, 0);
+    a.bin_list = k.d_bins;
+    a.cap = k.cap;
+    a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
+    if (e == cudaSuccess)
+      e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, dtype, split, csr->has_norm, precision, mode, si);
+    if (e == cudaSuccess && i > 0) e = cudaEventRecord(ctx->ev_join[i], si);
+  }
+  for (int i = 1; i < nc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, ctx->ev_join[i], 0);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -194,6 +276,9 @@ sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+  for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
     delete c;
@@ -214,6 +299,11 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
+  for (int i = 1; i < 4; ++i) {
+    if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
+    if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   delete ctx;
 }
 
@@ -281,6 +371,7 @@ void sep_csr_destroy(sep_csr* csr) {
     return;
   }
   cudaSetDevice(csr->ctx->device);
+  free_plan(csr);
   cudaFree(csr->d_rowptr);
   cudaFree(csr->d_ent);
   cudaFree(csr->d_w);
@@ -381,8 +472,7 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
   if (n_frames == 0) return SEP_OK;
   sep::ClipArgs a = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
                               bounds_dev, iters_dev, nullptr, 0);
-  cudaError_t e = sep::launch_integrate_clip(a, dtype, csr->h.split > 1, csr->has_norm, params->precision, 0,
-                                             (cudaStream_t)stream);
+  cudaError_t e = enqueue_clip(ctx, csr, a, dtype, params->precision, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "integrate_clip launch");
   return SEP_OK;
 }
@@ -467,7 +557,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
     cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
     if (e == cudaSuccess)
-      e = sep::launch_integrate_clip(a, dtype, csr->h.split > 1, csr->has_norm, params->precision, mode, s);
+      e = enqueue_clip(ctx, csr, a, dtype, params->precision, mode, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
                               ctx->d_aux, ctx->d_status, s);
@@ -491,7 +581,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev,
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
                                (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
-                               (uint64_t)(uintptr_t)s};
+                               (uint64_t)(uintptr_t)s, csr->plan_version};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));
@@ -510,7 +600,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
     // the kernel attribute is set before the capture, which then records launches only
     sep::ClipArgs a0 = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
                                  nullptr, nullptr, ctx->d_bitmap, words);
-    cudaError_t e = sep::launch_integrate_clip(a0, dtype, csr->h.split > 1, csr->has_norm, params->precision, 1, s);
+    cudaError_t e = enqueue_clip(ctx, csr, a0, dtype, params->precision, 1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute");
     sep_graph_entry g;
     SEP_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -531,6 +621,123 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   }
   it->second.last_use = ++ctx->use_clock;
   SEP_CUDA(ctx, cudaGraphLaunch(it->second.exec, s));
+  return SEP_OK;
+}
+
+
+sep_status sep_csr_set_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds,
+                            const int32_t* tpb) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (!csr || csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr missing or from another context");
+  if (!tpb || (n_classes > 1 && !thresholds)) return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  return make_plan(ctx, csr, n_classes, thresholds, tpb);
+}
+
+sep_status sep_csr_get_plan(const sep_csr* csr, int32_t* n_classes, int32_t* thresholds, int32_t* tpb) {
+  if (!csr || !n_classes) return SEP_ERR_ARG;
+  if (csr->plan.empty()) {
+    *n_classes = 1;
+    if (tpb) tpb[0] = 256;
+    return SEP_OK;
+  }
+  *n_classes = (int32_t)csr->plan.size();
+  for (size_t i = 0; i < csr->plan.size(); ++i) {
+    if (tpb) tpb[i] = csr->plan[i].tpb;
+    if (thresholds && i + 1 < csr->plan.size()) thresholds[i] = csr->plan[i].threshold;
+  }
+  return SEP_OK;
+}
+
+sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, const void* frames_dev, int32_t dtype,
+                        int32_t n_frames, const sep_params* params, const char* cache_path, float* best_ms,
+                        sep_stream stream) {
+  sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
+  if (st != SEP_OK) return st;
+  if (n_frames < 1) return fail(ctx, SEP_ERR_ARG, "autotuning needs at least one sample frame");
+  if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  SEP_CUDA(ctx, cudaGetDeviceProperties(&prop, ctx->device));
+  char key[512];
+  snprintf(key, sizeof key, "%dx%d|bins=%d|split=%d|nnz=%lld|max=%d|norm=%d|dtype=%d|prec=%d|%s", csr->h.rows,
+           csr->h.cols, csr->h.nbins, csr->h.split, (long long)csr->nnz, csr->h.max_row, (int)csr->has_norm, dtype,
+           params->precision, prop.name);
+  // a plan already tuned for this detector and device
+  if (cache_path) {
+    FILE* fp = fopen(cache_path, "r");
+    if (fp) {
+      char line[1024];
+      while (fgets(line, sizeof line, fp)) {
+        char* tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        if (strcmp(line, key) != 0) continue;
+        int nc = 0, t[4] = {0, 0, 0, 0}, b[4] = {256, 256, 256, 256};
+        float ms = 0;
+        if (sscanf(tab + 1, "%d %d %d %d %d %d %d %d %f", &nc, &t[0], &t[1], &t[2], &b[0], &b[1], &b[2], &b[3],
+                   &ms) >= 8 &&
+            nc >= 1 && nc <= 4) {
+          fclose(fp);
+          if (best_ms) *best_ms = ms;
+          return make_plan(ctx, csr, nc, t, b);
+        }
+      }
+      fclose(fp);
+    }
+  }
+  // timed search over size-class splits and block sizes
+  struct Cand { int nc; int t[3]; int b[4]; };
+  std::vector<Cand> cands;
+  for (int b0 : {64, 128, 256}) cands.push_back({1, {0, 0, 0}, {b0, 0, 0, 0}});
+  for (int thr : {1024, 2048, 4096, 8192})
+    for (int b0 : {64, 128, 256})
+      for (int b1 : {128, 256}) cands.push_back({2, {thr, 0, 0}, {b0, b1, 0, 0}});
+  float* d_out = nullptr;
+  const size_t per = (size_t)n_frames * csr->h.nbins;
+  SEP_CUDA(ctx, cudaMalloc((void**)&d_out, per * 12));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_i = -1;
+  sep::ClipArgs base = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, d_out, d_out + per,
+                                 reinterpret_cast<int32_t*>(d_out + 2 * per), nullptr, nullptr, nullptr, 0);
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand& c = cands[i];
+    if ((st = make_plan(ctx, csr, c.nc, c.t, c.b)) != SEP_OK) break;
+    cudaError_t e = enqueue_clip(ctx, csr, base, dtype, params->precision, 0, s);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = enqueue_clip(ctx, csr, base, dtype, params->precision, 2, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(ctx, e, "autotune trial");
+      break;
+    }
+    ms *= 0.5f;
+    if (ms < best) {
+      best = ms;
+      best_i = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_out);
+  if (st != SEP_OK) return st;
+  const Cand& w = cands[best_i];
+  if ((st = make_plan(ctx, csr, w.nc, w.t, w.b)) != SEP_OK) return st;
+  if (best_ms) *best_ms = best;
+  if (cache_path) {
+    FILE* fp = fopen(cache_path, "a");
+    if (fp) {
+      fprintf(fp, "%s\t%d %d %d %d %d %d %d %d %.4f\n", key, w.nc, w.t[0], w.t[1], w.t[2], w.b[0], w.b[1], w.b[2],
+              w.b[3], best);
+      fclose(fp);
+    }
+  }
   return SEP_OK;
 }
 

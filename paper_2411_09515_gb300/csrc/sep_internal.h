@@ -45,6 +45,7 @@ std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const flo
 
 // ---- kernel launch parameters -------------------------------------------
 struct ClipArgs {
+  const int32_t* bin_list; // bins handled by this launch (blockIdx.x indexes it); null = all, in order
   const int32_t* rowptr;
   const int32_t* grp;      // [nbins][4] class ends within a row
   const float2* cal0;      // per entry (ped, gain) of level 0 (raw input)
@@ -79,7 +80,7 @@ struct PixArgs {           // what the consumers need to recompute a pixel value
 
 // mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
 // only (call before a stream capture); 2: launch only.
-cudaError_t launch_integrate_clip(const ClipArgs& a, int32_t dtype, bool split, bool has_norm,
+cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, int32_t dtype, bool split, bool has_norm,
                                   int32_t precision, int mode, cudaStream_t s);
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
@@ -113,6 +114,10 @@ struct sep_graph_entry {
 struct sep_ctx {
   int32_t device = 0;
   int num_sms = 0;
+  // fork/join of the clip launches of several size classes
+  cudaStream_t aux[4] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[4] = {};
   int32_t* d_status = nullptr;
   std::string err;
   // scratch owned by the context, grown on demand (never inside a capture)
@@ -127,9 +132,21 @@ struct sep_ctx {
   uint64_t use_clock = 0;
 };
 
+// One size class of bins for the clip kernel: its own block size and
+// shared-memory capacity (the largest row in the class), big rows first.
+struct sep_clip_class {
+  int32_t* d_bins = nullptr;
+  int32_t n_bins = 0;
+  int32_t cap = 0;
+  int32_t tpb = 256;
+  int32_t threshold = 0;   // rows with more entries than the previous class's threshold, up to this
+};
+
 struct sep_csr {
   sep_ctx* ctx = nullptr;
   sep::HostCsr h;
+  std::vector<sep_clip_class> plan;   // empty = one class of every bin at 256 threads
+  uint64_t plan_version = 0;
   int64_t npix = 0, nnz = 0;
   bool has_norm = false;
   int32_t* d_rowptr = nullptr;

@@ -215,3 +215,36 @@ def test_invalid_arguments_raise_before_launch():
     sep.set_params(k_clip=3.0)
     with pytest.raises(SepError):   # raw frames without a calibration
         sep.integrate_clip(torch.zeros((1, det.npix), dtype=torch.int16, device="cuda"))
+
+
+@pytest.mark.parametrize("tpb,thr", [([64], []), ([128], []), ([256], []), ([64, 256], [2048]), ([128, 128, 256], [512, 4096])])
+def test_clip_plans_keep_parity(jf_small, tpb, thr):
+    """The clip kernel's schedule (size classes, threads per block, parallel
+    branches) changes no result beyond the stated tolerances."""
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal)
+    sep.set_plan(tpb, thr)
+    assert sep.get_plan() == {"tpb": tpb, "thresholds": thr}
+    kcap = det.npix // 4
+    o, dfr = run_batch(sep, fr[:3], kcap, 20000)
+    bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+    for f in range(3):
+        sig = oracle.jf_photons(fr[f], cal[0], cal[1])
+        check_frame(det, W, sig, o, f, kcap=kcap, bounds=bnd[f])
+
+
+def test_autotune_picks_a_plan_and_caches_it(jf_small, tmp_path):
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal)
+    d = torch.from_numpy(fr.view(np.int16)).cuda()
+    cache = tmp_path / "plans.txt"
+    ms = sep.autotune(d, cache_path=cache)
+    assert ms > 0 and cache.exists()
+    plan = sep.get_plan()
+    sep2 = Separator.from_detector(det, mask=mask, calib=cal)
+    ms2 = sep2.autotune(d, cache_path=cache)   # read back, no timing
+    assert sep2.get_plan() == plan and ms2 == pytest.approx(ms, rel=1e-3)
+    o, dfr = run_batch(sep2, fr[:2], det.npix // 4, 20000)
+    sig = oracle.jf_photons(fr[0], cal[0], cal[1])
+    bnd = sep2.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+    check_frame(det, W, sig, o, 0, kcap=det.npix // 4, bounds=bnd[0])

@@ -1,0 +1,104 @@
+"""Precision study: PLAIN, KAHAN and FP64MERGE against the FP64 oracle on
+high-dynamic-range Jungfrau-shaped raw frames (background 0.01-50 photons/px,
+spots to 5e4 photons, so all three gain levels occur).
+
+Per mode: max / mean relative error of the per-bin mean and deviation over
+the bins whose clip decisions are outside the 1e-5 band, kept-pixel
+mismatches outside the band, and the peak centroid error in pixels. The
+default mode must meet the parity tolerances; the others are reported.
+Set SEP_PRECISION_REPORT=path to write the numbers as JSON, and
+SEP_PRECISION_FULL=1 to run the full-size study (256 Jungfrau-4M frames).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import BAND, Frame
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2411_09515_gb300 import (SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator,  # noqa: E402
+                                    peaks_to_numpy)
+
+MODES = {"plain": SEP_PREC_PLAIN, "kahan": SEP_PREC_KAHAN, "fp64merge": SEP_PREC_FP64MERGE}
+
+
+def study(det, n_frames, seed=21):
+    mask = det.mask()
+    cal = synth.jf_calib(det.npix, seed=seed)
+    fr, _, _ = synth.frames(det, synth.spec_jf_hdr(seed), 0, n_frames, calib=cal, mask=mask)
+    W = oracle.weights(det, mask)
+    codes = np.bincount((fr[:, mask == 0] >> 14).ravel(), minlength=4)
+    d = torch.from_numpy(fr.view(np.int16)).cuda()
+    refs = []
+    for f in range(n_frames):
+        sig = oracle.jf_photons(fr[f], cal[0], cal[1])
+        fo = Frame(W, sig, 5, 3.0, 3.0)
+        pk = oracle.peaks(det, W, sig, fo.ref["mean"], fo.ref["sigma"])
+        refs.append((sig, fo, pk))
+    report = {"frames": n_frames, "detector": det.name, "gain_level_pixels": codes.tolist()}
+    for name, prec in MODES.items():
+        sep = Separator.from_detector(det, mask=mask, calib=cal, precision=prec)
+        out = sep.process_batch(d, det.npix // 4, 50000)
+        torch.cuda.synchronize()
+        o = {k: v.cpu().numpy() for k, v in out.items()}
+        rel_mu, rel_sd, kept_bad, cen = [], [], 0, []
+        for f, (sig, fo, pk) in enumerate(refs):
+            ref = fo.ref
+            ok = (ref["band"] >= BAND) & (ref["count"] > 1)
+            scale_mu = np.maximum(np.abs(ref["mean"][ok]), 1e-7 * ref["sigma"][ok] / 1e-5)
+            rel_mu.append(np.abs(o["mean"][f][ok] - ref["mean"][ok]) / scale_mu)
+            rel_sd.append(np.abs(o["sigma"][f][ok] - ref["sigma"][ok]) / np.maximum(ref["sigma"][ok], 1e-30))
+            thr = ref["mean"] + 3.0 * ref["sigma"]
+            bop = W.bin_of_pixel
+            valid = bop >= 0
+            want = np.flatnonzero(valid & (fo.v > thr[np.where(valid, bop, 0)]))
+            got = o["idx"][f][: int(o["n_kept"][f])]
+            diff = np.setxor1d(got, want)
+            t = thr[bop[diff]]
+            kept_bad += int((np.abs(fo.v[diff] - t) > BAND * np.abs(t)).sum())
+            g = peaks_to_numpy(torch.from_numpy(o["peaks"][f]), o["n_peaks"][f])
+            common, ia, ib = np.intersect1d(g["idx"], pk["idx"], return_indices=True)
+            if common.size:
+                cen.append(np.hypot(g["y"][ia] - pk["y"][ib], g["x"][ia] - pk["x"][ib]))
+        rm, rs = np.concatenate(rel_mu), np.concatenate(rel_sd)
+        cc = np.concatenate(cen) if cen else np.zeros(1)
+        report[name] = {"mean_rel_err_max": float(rm.max()), "mean_rel_err_mean": float(rm.mean()),
+                        "sigma_rel_err_max": float(rs.max()), "sigma_rel_err_mean": float(rs.mean()),
+                        "kept_mismatch_outside_band": kept_bad, "centroid_err_px_max": float(cc.max()),
+                        "centroid_err_px_mean": float(cc.mean()), "bins_compared": int(rm.size)}
+        sep.close()
+    return report
+
+
+def _emit(report):
+    path = os.environ.get("SEP_PRECISION_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(report, f, indent=1)
+    print(json.dumps(report))
+
+
+def test_precision_modes_small():
+    det = synth.det_small_jf(split=2, nbins=300)
+    r = study(det, 6)
+    _emit(r)
+    assert r["gain_level_pixels"][1] > 0 and r["gain_level_pixels"][3] > 0   # levels 1 and 2 both occur
+    for name in ("fp64merge", "kahan"):
+        assert r[name]["mean_rel_err_max"] < 1e-5 and r[name]["sigma_rel_err_max"] < 1e-5
+        assert r[name]["kept_mismatch_outside_band"] == 0
+        assert r[name]["centroid_err_px_max"] < 1e-3
+    assert r["plain"]["mean_rel_err_mean"] < 1e-4
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("SEP_PRECISION_FULL") != "1", reason="full-size study on request")
+def test_precision_modes_jf4m_256():
+    r = study(synth.det_jf4m(), 256)
+    _emit(r)
+    assert r["fp64merge"]["mean_rel_err_max"] < 1e-5 and r["fp64merge"]["sigma_rel_err_max"] < 1e-5
