@@ -132,7 +132,8 @@ def run_ours(args):
     t0 = time.time()
     det, mask, cal, frames_np = setup_workload(F, rank)
     t_gen = time.time() - t0
-    prec = {"plain": B.SEP_PREC_PLAIN, "kahan": B.SEP_PREC_KAHAN, "fp64merge": B.SEP_PREC_FP64MERGE}[args.precision]
+    prec = {"plain": B.SEP_PREC_PLAIN, "kahan": B.SEP_PREC_KAHAN, "fp64merge": B.SEP_PREC_FP64MERGE,
+            "dword": B.SEP_PREC_DWORD}[args.precision]
     sep = Separator.from_detector(det, mask=mask, calib=cal, device=local, precision=prec)
     info = sep.info
     kcap, pcap = args.kept_capacity, args.peak_capacity
@@ -260,6 +261,72 @@ def cpu_baseline(det, mask, cal, frames_np, n):
             "sample": f"{n} of the batch's JF4M raw frames through oracle.process_frames (FP64), weights excluded"}
 
 
+def run_mixed(args):
+    """Uneven batching: a stream of float32 photon frames from 1M, 4M and 16M
+    Jungfrau-shaped detectors (3:2:1, 600 / 1000 / 2000 bins, no splitting)
+    in one call and one captured graph, schedules autotuned per detector.
+    Reports aggregate frames/s and GB/s, and frames/s per detector size."""
+    import torch
+    import synth
+    from paper_2411_09515_gb300 import Context, Separator, process_mixed
+    rng = np.random.default_rng(7)
+    dets = [synth.det_jf1m(nbins=600), synth.det_jf4m(split=1, nbins=1000), synth.det_jf16m(nbins=2000)]
+    masks = [d.mask() for d in dets]
+    groups = max(1, args.frames // 6)
+    pattern = []
+    for _ in range(groups):
+        grp = [0, 1, 0, 2, 1, 0]
+        rng.shuffle(grp)
+        pattern += grp
+    ctx = Context(0)
+    seps = [Separator.from_detector(d, mask=m, context=ctx) for d, m in zip(dets, masks)]
+    frames = []
+    per = {0: [], 1: [], 2: []}
+    for g, d in enumerate(pattern):
+        spec = synth.spec_mixed(seed=1000 + g, hit_rate=float(rng.uniform(0.1, 0.5)))
+        fr = synth.frames(dets[d], spec, g, 1, mask=masks[d])[0][0]
+        t = torch.from_numpy(fr).cuda()
+        frames.append((d, t))
+        per[d].append(t)
+    tuned = {}
+    for d in range(3):
+        sample = torch.stack(per[d][:8])
+        tuned[d] = {"ms": seps[d].autotune(sample), **seps[d].get_plan()}
+    kcap, pcap = max(args.kept_capacity, 1 << 20), args.peak_capacity   # 16M frames keep ~0.7 M pixels
+    for _ in range(args.warmup):
+        out = process_mixed(seps, frames, kcap, pcap)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = process_mixed(seps, frames, kcap, pcap)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = len(frames)
+    byts = sum(4 * dets[d].npix for d in pattern)
+    per_size = {}
+    for d, name in enumerate(["1M", "4M", "16M"]):
+        batch = torch.stack(per[d])
+        o = seps[d].alloc_outputs(batch.shape[0], kcap, pcap)
+        for _ in range(2):
+            seps[d].process_batch(batch, kcap, pcap, out=o)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(args.steps):
+            seps[d].process_batch(batch, kcap, pcap, out=o)
+        a1.record()
+        torch.cuda.synchronize()
+        per_size[name] = round(batch.shape[0] / (a0.elapsed_time(a1) / args.steps) * 1e3, 1)
+    line = {"metric": "mixed 1M/4M/16M frames/s (clip+sparsify+peaks), one graph", "value": round(n / ms * 1e3, 2),
+            "unit": "frames/s", "ms_per_step": round(ms, 3), "steps": args.steps, "warmup": args.warmup,
+            "frames_per_step": n, "gbs_input": round(byts / (ms * 1e-3) / 1e9, 1), "per_size_frames_s": per_size,
+            "plans": tuned, "dtype": "f32", "data": "synthetic", "device_status": seps[0].device_status(),
+            "config": {"workload": "mixed f32 1M:4M:16M = 3:2:1, 600/1000/2000 bins, no split"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -294,15 +361,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--frames", type=int, default=512)
-    ap.add_argument("--kept-capacity", type=int, default=262144)
+    ap.add_argument("--kept-capacity", type=int, default=262144)  # mixed: raised to fit 16M frames
     ap.add_argument("--peak-capacity", type=int, default=8192)
     ap.add_argument("--cpu-frames", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge"], default="fp64merge")
+    ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge", "dword"], default="dword")
+    ap.add_argument("--workload", choices=["jf4m", "mixed"], default="jf4m")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 

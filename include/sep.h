@@ -56,17 +56,22 @@ typedef int32_t sep_status;
 #define SEP_DTYPE_F32     0   /* float32 corrected signal (photons) per pixel */
 #define SEP_DTYPE_U16_JF  1   /* raw Jungfrau word: 2 gain bits (15:14) + 14-bit ADC */
 
-/* Precision of the per-bin moments (Section 2.2's reductions):
- * PLAIN:     plain FP32 per-thread sums, FP32 merges and finalisation.
- * KAHAN:     Kahan-compensated FP32 per-thread sums, error-free FP32 pair
- *            merges (warp and cross-warp), FP64 finalisation on one thread.
- * FP64MERGE: plain FP32 per-thread sums and warp shuffles, FP64 cross-warp
- *            merge, FP64 finalisation on one thread (the default).
- * With KAHAN and FP64MERGE the clip bounds are rounded outward-exact, so a
- * float value is compared with the FP64 bound itself. */
+/* Precision of the per-bin moments (Section 2.2's reductions). Per-thread
+ * sums are FP32 over a few dozen entries about a shift near the mean; the
+ * modes differ in how partial sums are merged and the moments finalised:
+ * PLAIN:     plain FP32 merges and finalisation.
+ * KAHAN:     Kahan-compensated per-thread sums, error-free FP32 pair merges,
+ *            double-word (FP32 pair) finalisation.
+ * FP64MERGE: FP64 cross-warp merge and FP64 finalisation on one thread.
+ * DWORD:     plain per-thread sums, error-free FP32 pair ("double-word")
+ *            cross-warp merge and finalisation, no FP64 instruction (the
+ *            default: FP64 is a small fraction of the FP32 rate on GB300).
+ * Except in PLAIN, clip bounds and the sparsification threshold are rounded
+ * outward-exact, so a float value is compared with the extended bound. */
 #define SEP_PREC_PLAIN     0
 #define SEP_PREC_KAHAN     1
 #define SEP_PREC_FP64MERGE 2
+#define SEP_PREC_DWORD     3
 
 /* ---- opaque handles ---------------------------------------------------- */
 typedef struct sep_ctx sep_ctx;
@@ -229,6 +234,38 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                              int64_t kept_capacity, int32_t* n_kept_dev, sep_peak* peaks_dev,
                              int64_t peak_capacity, int32_t* n_peaks_dev, int32_t use_graph,
                              sep_stream stream);
+
+/* One frame of a mixed batch: its detector (index into the csr / calib
+ * arrays), its dtype (all frames of one detector share it) and its device
+ * address. */
+typedef struct {
+  int32_t det;
+  int32_t dtype;
+  const void* frame_dev;
+} sep_frame_desc;
+
+/*
+ * The whole path on a stream of frames from up to 4 detectors of different
+ * sizes (their own matrices, calibrations and clip schedules) in one call:
+ * each detector's frames run as one parallel branch of a single captured
+ * CUDA graph (use_graph = 1), replayed for the same descriptors and outputs.
+ *  frames: host array [n_frames] of descriptors, in stream order.
+ *  mean/sigma/count_dev: flat per-bin outputs, frame g's nbins values at
+ *  row_off[g]; row_off (host, [n_frames + 1], may be NULL) receives the
+ *  offsets (prefix sums of the frames' bin counts).
+ *  idx/val_dev [n_frames][kept_capacity], n_kept_dev [n_frames],
+ *  peaks_dev [n_frames][peak_capacity], n_peaks_dev [n_frames]: as in
+ *  sep_process_batch, rows in stream order.
+ * Blocks the host until the previous call on `stream` has read its
+ * descriptor table (a few bytes per frame).
+ */
+sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs,
+                             const sep_calib* const* calibs, const sep_frame_desc* frames,
+                             int32_t n_frames, const sep_params* params, float* mean_dev,
+                             float* sigma_dev, int32_t* count_dev, int64_t* row_off, int32_t* idx_dev,
+                             float* val_dev, int64_t kept_capacity, int32_t* n_kept_dev,
+                             sep_peak* peaks_dev, int64_t peak_capacity, int32_t* n_peaks_dev,
+                             int32_t use_graph, sep_stream stream);
 
 /*
  * Schedule of the integrate + clip kernel for one matrix (a tuning choice,

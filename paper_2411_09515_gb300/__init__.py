@@ -14,11 +14,11 @@ from __future__ import annotations
 import numpy as np
 
 from . import _binding as B
-from ._binding import (PEAK_DTYPE, SEP_DTYPE_F32, SEP_DTYPE_U16_JF, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN,
-                       SEP_PREC_PLAIN, SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM, SepError)
+from ._binding import (PEAK_DTYPE, SEP_DTYPE_F32, SEP_DTYPE_U16_JF, SEP_PREC_DWORD, SEP_PREC_FP64MERGE,
+                       SEP_PREC_KAHAN, SEP_PREC_PLAIN, SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM, SepError)
 
-__all__ = ["Separator", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
-           "SEP_PREC_PLAIN", "SEP_PREC_KAHAN", "SEP_PREC_FP64MERGE", "SEP_UNIT_2TH_DEG", "SEP_UNIT_Q_NM",
+__all__ = ["Context", "Separator", "process_mixed", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
+           "SEP_PREC_PLAIN", "SEP_PREC_KAHAN", "SEP_PREC_FP64MERGE", "SEP_PREC_DWORD", "SEP_UNIT_2TH_DEG", "SEP_UNIT_Q_NM",
            "SEP_UNIT_R_MM"]
 
 
@@ -26,6 +26,26 @@ def peaks_to_numpy(peaks, n):
     """Peak records of one frame (an int32 tensor [cap, 6]) as a structured array of the first n."""
     a = peaks[: int(n)].contiguous().cpu().numpy()
     return a.view(PEAK_DTYPE).reshape(-1)
+
+
+class Context:
+    """A library context on one GPU; several Separators may share it (and
+    must, to be processed together by :func:`process_mixed`)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = B.sep_ctx_create(device)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            B.sep_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Separator:
@@ -36,11 +56,12 @@ class Separator:
     """
 
     def __init__(self, geometry: dict, mask=None, norm=None, calib=None, device: int = 0, n_iter=5, k_clip=3.0,
-                 k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_FP64MERGE):
+                 k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD, context: Context | None = None):
         import torch  # device memory and streams
         self.torch = torch
-        self.device = device
-        self.ctx = B.sep_ctx_create(device)
+        self.context = context
+        self.device = context.device if context is not None else device
+        self.ctx = context.ctx if context is not None else B.sep_ctx_create(device)
         g = geometry
         self.geom = B.make_geometry(g["rows"], g["cols"], g["pixel_m"], g["dist_m"], g["center_px"],
                                     g["wavelength_m"], g["unit"], g["nbins"], g["split"], g["range"])
@@ -66,7 +87,8 @@ class Separator:
         if getattr(self, "ctx", None) is not None:
             B.sep_calib_destroy(self.calib)
             B.sep_csr_destroy(self.csr)
-            B.sep_ctx_destroy(self.ctx)
+            if self.context is None:
+                B.sep_ctx_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -186,3 +208,36 @@ class Separator:
 
     def device_status(self, stream=None):
         return B.sep_get_device_status(self.ctx, stream)
+
+
+def process_mixed(seps, frames, kept_capacity, peak_capacity, use_graph=True, stream=None):
+    """The whole path on a stream of frames from several detectors at once.
+
+    seps: Separators sharing one :class:`Context`; frames: list of
+    (detector index, contiguous CUDA tensor of one frame). Returns the output
+    tensors and the per-frame row offsets into the flat mean/sigma/count."""
+    import torch
+    ctx = seps[0].ctx
+    if any(s.ctx is not ctx for s in seps):
+        raise ValueError("process_mixed needs Separators that share one Context")
+    dev = frames[0][1].device
+    total_bins = sum(seps[d].nbins for d, _ in frames)
+    n = len(frames)
+    out = {"mean": torch.empty(total_bins, dtype=torch.float32, device=dev),
+           "sigma": torch.empty(total_bins, dtype=torch.float32, device=dev),
+           "count": torch.empty(total_bins, dtype=torch.int32, device=dev),
+           "idx": torch.empty((n, kept_capacity), dtype=torch.int32, device=dev),
+           "val": torch.empty((n, kept_capacity), dtype=torch.float32, device=dev),
+           "n_kept": torch.empty(n, dtype=torch.int32, device=dev),
+           "peaks": torch.empty((n, peak_capacity, 6), dtype=torch.int32, device=dev),
+           "n_peaks": torch.empty(n, dtype=torch.int32, device=dev)}
+    descs = []
+    for d, t in frames:
+        if not t.is_contiguous() or t.numel() != seps[d].npix:
+            raise ValueError("each frame must be one contiguous detector image")
+        descs.append((d, seps[d]._dtype(t), t))
+    rows = B.sep_process_mixed(ctx, [s.csr for s in seps], [s.calib for s in seps], descs, seps[0].params,
+                               out["mean"], out["sigma"], out["count"], out["idx"], out["val"], kept_capacity,
+                               out["n_kept"], out["peaks"], peak_capacity, out["n_peaks"], use_graph, stream)
+    out["row_off"] = rows
+    return out

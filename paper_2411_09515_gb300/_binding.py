@@ -20,7 +20,7 @@ SEP_OK, SEP_ERR_ARG, SEP_ERR_CUDA, SEP_ERR_OOM, SEP_ERR_CAPACITY, SEP_ERR_TIMEOU
 SEP_DEV_CAPACITY, SEP_DEV_TIMEOUT = 0x1, 0x2
 SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM = 0, 1, 2
 SEP_DTYPE_F32, SEP_DTYPE_U16_JF = 0, 1
-SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE = 0, 1, 2
+SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE, SEP_PREC_DWORD = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OOM", 4: "SEP_ERR_CAPACITY",
                 5: "SEP_ERR_TIMEOUT", 6: "SEP_ERR_CSR", 7: "SEP_ERR_STATE"}
@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OO
 EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error", "sep_get_device_status",
            "sep_build_csr", "sep_csr_destroy", "sep_csr_info", "sep_csr_export", "sep_calib_create",
            "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch",
-           "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune"]
+           "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune", "sep_process_mixed"]
 
 
 class SepError(RuntimeError):
@@ -47,6 +47,10 @@ class sep_geometry(C.Structure):
 class sep_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
                 ("min_count", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class sep_frame_desc(C.Structure):
+    _fields_ = [("det", C.c_int32), ("dtype", C.c_int32), ("frame_dev", C.c_void_p)]
 
 
 PEAK_DTYPE = np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"), ("I", "<f4"), ("sigma", "<f4"), ("npix", "<i4")])
@@ -90,6 +94,8 @@ def lib():
     L.sep_csr_get_plan.argtypes = [_vp, _vp, _vp, _vp]
     L.sep_autotune.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), C.c_char_p,
                                C.POINTER(C.c_float), _vp]
+    L.sep_process_mixed.argtypes = [_vp, C.c_int32, _vp, _vp, _vp, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
+                                    _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
     L.sep_peakfind.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
@@ -162,7 +168,7 @@ def make_geometry(rows, cols, pixel_m, dist_m, center_px, wavelength_m, unit, nb
     return g
 
 
-def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_FP64MERGE):
+def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD):
     p = sep_params()
     p.n_iter, p.k_clip, p.k_pick, p.patch, p.min_count, p.precision = n_iter, k_clip, k_pick, patch, min_count, precision
     return p
@@ -258,6 +264,23 @@ def sep_autotune(ctx, csr, calib, frames, dtype, n_frames, params, cache_path=No
                                    None if cache_path is None else str(cache_path).encode(), C.byref(ms),
                                    _stream(stream)))
     return ms.value
+
+
+def sep_process_mixed(ctx, csrs, calibs, descs, params, mean, sigma, count, idx, val, kept_capacity, n_kept, peaks,
+                      peak_capacity, n_peaks, use_graph=1, stream=None):
+    """descs: list of (det, dtype, device tensor). Returns the row offsets (numpy int64)."""
+    n = len(descs)
+    D = (sep_frame_desc * max(n, 1))()
+    for i, (d, dt, t) in enumerate(descs):
+        D[i].det, D[i].dtype, D[i].frame_dev = d, dt, t.data_ptr()
+    cs = (C.c_void_p * len(csrs))(*[c.value if hasattr(c, "value") else c for c in csrs])
+    ks = (C.c_void_p * len(csrs))(*[(k.value if hasattr(k, "value") else k) if k is not None else None
+                                    for k in calibs])
+    rows = np.zeros(n + 1, np.int64)
+    _check(ctx, lib().sep_process_mixed(ctx, len(csrs), cs, ks, D, n, C.byref(params), _ptr(mean), _ptr(sigma),
+                                        _ptr(count), _ptr(rows), _ptr(idx), _ptr(val), kept_capacity, _ptr(n_kept),
+                                        _ptr(peaks), peak_capacity, _ptr(n_peaks), int(use_graph), _stream(stream)))
+    return rows
 
 
 def sep_peakfind(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, idx, n_kept, kept_capacity, peaks,

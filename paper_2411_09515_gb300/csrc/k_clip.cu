@@ -27,9 +27,10 @@
 // Precision (SEP_PREC_*): per-thread FP32 sums (Kahan-compensated in KAHAN)
 // and FP32 warp shuffles (error-free pairs in KAHAN). The cross-warp merge,
 // the variance finalisation and the clip bounds run on one warp only: FP64
-// in FP64MERGE, FP32 pairs in KAHAN, FP32 in PLAIN. (FP64 runs at a small
-// fraction of the FP32 rate on this GPU, so no FP64 instruction is issued by
-// the other warps.)
+// in FP64MERGE, error-free FP32 pairs ("double-word") in DWORD and KAHAN,
+// plain FP32 in PLAIN. FP64 runs at a small fraction of the FP32 rate on this
+// GPU and sits on the serial path of every pass, so DWORD, which issues no
+// FP64 instruction, is the default.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -75,64 +76,123 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float so, float co)
 // mean's own scale.
 __device__ __forceinline__ float choose_shift(float mu, float sd) { return fabsf(mu) <= 2.0f * sd ? 0.0f : mu; }
 
-// State shared by the CTA between passes (written by one thread).
+// State shared by the CTA between passes (written by one thread). The
+// mean is kept as an unevaluated FP32 pair mu_hi + mu_lo (FP64MERGE keeps a
+// double).
 struct Bcast {
-  double mu, sd;       // moments of the current set
+  double mu_d, sd_d;   // FP64MERGE
+  float mu_hi, mu_lo, sd;
   float Ln, Hn, Kf;    // interval and shift of the next pass
   float L, H;          // interval of the current set
   float n_cur;         // entries (weight != 0) in the current set
   int steps, done;
 };
 
-// Moments of one set from its shifted sums (one thread).
+// Error-free sum: a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// Smallest float >= hi + lo and largest float <= hi + lo for a normalised
+// pair (hi = RN(hi + lo)).
+__device__ __forceinline__ float round_up_pair(float hi, float lo) { return lo > 0.0f ? nextafterf(hi, INFINITY) : hi; }
+__device__ __forceinline__ float round_dn_pair(float hi, float lo) { return lo < 0.0f ? nextafterf(hi, -INFINITY) : hi; }
+
+// Mean and deviation of one set from its shifted sums, one thread:
+//   mu = K + A1 / Omega,  VV = B2 - 2 (mu - K) B1 + (mu - K)^2 OO,  sd = sqrt(VV / OO)
+// Sums arrive as FP32 pairs (value = hi + lo). The divisions act on a small
+// correction and on a ratio, where FP32 is exact to ~1e-7 relative; the
+// mean is kept as the exact pair K + corr. FP64MERGE does the same in FP64.
 template <int PREC>
-__device__ __forceinline__ void finalise(double K, double Om, double A1, double OO, double B1, double B2, double& mu,
-                                         double& sd) {
-  if (Om == 0.0) {
-    mu = 0.0;
-    sd = 0.0;
+__device__ __forceinline__ void finalise(float Kf, const float (&hi)[6], const float (&lo)[6], Bcast& st) {
+  // hi/lo layout: 0 Omega, 1 A1, 2 OO, 3 B1, 4 B2
+  if (hi[0] == 0.0f) {
+    st.mu_hi = st.mu_lo = st.sd = 0.0f;
+    st.mu_d = st.sd_d = 0.0;
     return;
   }
-  if (PREC == SEP_PREC_PLAIN) {
-    const float Kf = (float)K;
-    const float muf = __fadd_rn(Kf, __fdiv_rn((float)A1, (float)Om));
-    const float dl = __fsub_rn(muf, Kf);
-    const float VV = __fadd_rn(__fsub_rn((float)B2, __fmul_rn(2.0f * dl, (float)B1)),
-                               __fmul_rn(__fmul_rn(dl, dl), (float)OO));
-    mu = (double)muf;
-    sd = VV > 0.0f ? (double)__fsqrt_rn(__fdiv_rn(VV, (float)OO)) : 0.0;
-  } else {
-    // the two divisions act on a small correction and on a ratio: FP32 is exact enough
-    mu = K + (double)__fdiv_rn((float)A1, (float)Om);
-    const double dl = mu - K;
+  if (PREC == SEP_PREC_FP64MERGE) {
+    const double Om = (double)hi[0] + lo[0], A1 = (double)hi[1] + lo[1], OO = (double)hi[2] + lo[2];
+    const double B1 = (double)hi[3] + lo[3], B2 = (double)hi[4] + lo[4];
+    const double mu = (double)Kf + (double)__fdiv_rn((float)A1, (float)Om);
+    const double dl = mu - (double)Kf;
     const double VV = fma(dl * dl, OO, fma(-2.0 * dl, B1, B2));
-    sd = VV > 0.0 ? (double)__fsqrt_rn(__fdiv_rn((float)VV, (float)OO)) : 0.0;
+    st.mu_d = mu;
+    st.sd_d = VV > 0.0 ? (double)__fsqrt_rn(__fdiv_rn((float)VV, (float)OO)) : 0.0;
+    st.mu_hi = (float)mu;
+    st.mu_lo = (float)(mu - (double)st.mu_hi);
+    st.sd = (float)st.sd_d;
+    return;
   }
-}
-
-// Next interval: keep |v - mu| <= k sd. With FP64 moments the float bounds
-// use directed rounding, so for any float v (v >= L) == (v >= mu - k sd).
-template <int PREC>
-__device__ __forceinline__ void clip_bounds(double mu, double sd, float k, float& L, float& H) {
+  const float Om = __fadd_rn(hi[0], lo[0]), OO = __fadd_rn(hi[2], lo[2]);
+  const float corr = __fdiv_rn(__fadd_rn(hi[1], lo[1]), Om);
   if (PREC == SEP_PREC_PLAIN) {
-    const float m = (float)mu, s = (float)sd;
-    L = fmaxf(L, __fsub_rn(m, __fmul_rn(k, s)));
-    H = fminf(H, __fadd_rn(m, __fmul_rn(k, s)));
+    st.mu_hi = __fadd_rn(Kf, corr);
+    st.mu_lo = 0.0f;
   } else {
-    L = fmaxf(L, __double2float_ru(fma(-(double)k, sd, mu)));
-    H = fminf(H, __double2float_rd(fma((double)k, sd, mu)));
+    two_sum(Kf, corr, st.mu_hi, st.mu_lo);
+  }
+  // VV with the small correction terms in FP32 and the leading B2 as a pair
+  float VV = __fsub_rn(hi[4], __fmul_rn(2.0f * corr, __fadd_rn(hi[3], lo[3])));
+  VV = __fadd_rn(VV, __fmul_rn(__fmul_rn(corr, corr), OO));
+  VV = __fadd_rn(VV, lo[4]);
+  st.sd = VV > 0.0f ? __fsqrt_rn(__fdiv_rn(VV, OO)) : 0.0f;
+}
+
+// Next interval: keep |v - mu| <= k sd (Eq. 19). Except in PLAIN the float
+// bounds are rounded outward-exact from the extended mean, so for any float
+// v the test v >= L equals v >= mu - k sd up to the rounding of k sd.
+template <int PREC>
+__device__ __forceinline__ void clip_bounds(const Bcast& st, float k, float& L, float& H) {
+  if (PREC == SEP_PREC_PLAIN) {
+    const float ks = __fmul_rn(k, st.sd);
+    L = fmaxf(L, __fsub_rn(st.mu_hi, ks));
+    H = fminf(H, __fadd_rn(st.mu_hi, ks));
+  } else if (PREC == SEP_PREC_FP64MERGE) {
+    L = fmaxf(L, __double2float_ru(fma(-(double)k, st.sd_d, st.mu_d)));
+    H = fminf(H, __double2float_rd(fma((double)k, st.sd_d, st.mu_d)));
+  } else {
+    const float ks = __fmul_rn(k, st.sd);
+    float a, e;
+    two_sum(st.mu_hi, -ks, a, e);
+    e = __fadd_rn(e, st.mu_lo);
+    float lh, ll;
+    two_sum(a, e, lh, ll);
+    L = fmaxf(L, round_up_pair(lh, ll));
+    two_sum(st.mu_hi, ks, a, e);
+    e = __fadd_rn(e, st.mu_lo);
+    two_sum(a, e, lh, ll);
+    H = fminf(H, round_dn_pair(lh, ll));
   }
 }
 
-// Sum NV per-thread values over the CTA; lanes v < NV of warp 0 hold total v
-// on return (as double). Ends without a barrier: the caller's warp 0 works
-// on the totals and then synchronises.
-template <int NV, int PREC, int kWarps>
-__device__ __forceinline__ double block_sum(float (&s)[NV], float (&c)[NV], float (*red_s)[kWarps],
-                                            float (*red_c)[kWarps]) {
+// Threshold of sparsification, mu + k_pick sd, rounded down (v > thr is
+// then the exact comparison for float v, up to the rounding of k sd).
+template <int PREC>
+__device__ __forceinline__ float pick_threshold(const Bcast& st, float k) {
+  if (PREC == SEP_PREC_PLAIN) return __fadd_rn(st.mu_hi, __fmul_rn(k, st.sd));
+  if (PREC == SEP_PREC_FP64MERGE) return __double2float_rd(fma((double)k, st.sd_d, st.mu_d));
+  const float ks = __fmul_rn(k, st.sd);
+  float a, e, th, tl;
+  two_sum(st.mu_hi, ks, a, e);
+  e = __fadd_rn(e, st.mu_lo);
+  two_sum(a, e, th, tl);
+  return round_dn_pair(th, tl);
+}
+
+// Sum NF float and NI integer per-thread values over the CTA. On return,
+// lane v of warp 0 holds float total v (v < NF) and lane NF + i integer
+// total i, as doubles. Integers go through one redux per warp. Ends without
+// a barrier: the caller's warp 0 works on the totals and then synchronises.
+template <int NF, int NI, int PREC, int kWarps>
+__device__ __forceinline__ void block_sum(float (&s)[NF], float (&c)[NF], uint32_t (&iv)[NI], float (*red_s)[kWarps],
+                                          float (*red_c)[kWarps], uint32_t (*red_i)[kWarps], float& thi,
+                                          float& tlo) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
+  for (int v = 0; v < NF; ++v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       if (PREC == SEP_PREC_KAHAN) {
@@ -144,45 +204,64 @@ __device__ __forceinline__ double block_sum(float (&s)[NV], float (&c)[NV], floa
       }
     }
   }
+  uint32_t wi[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) wi[i] = __reduce_add_sync(0xffffffffu, iv[i]);
   if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < NF; ++v) {
       red_s[v][warp] = s[v];
       red_c[v][warp] = PREC == SEP_PREC_KAHAN ? c[v] : 0.0f;
     }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) red_i[i][warp] = wi[i];
   }
   __syncthreads();
-  double tot = 0.0;
-  if (warp == 0 && lane < NV) {
+  thi = 0.0f;
+  tlo = 0.0f;
+  if (warp == 0 && lane < NF) {
     if (PREC == SEP_PREC_FP64MERGE) {
+      double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) tot += (double)red_s[lane][w];
-    } else if (PREC == SEP_PREC_KAHAN) {
-      float hs = red_s[lane][0], hc = red_c[lane][0];
-#pragma unroll
-      for (int w = 1; w < kWarps; ++w) pair_add(hs, hc, red_s[lane][w], red_c[lane][w]);
-      tot = (double)hs - (double)hc;
-    } else {
+      for (int w = 0; w < kWarps; ++w) t += (double)red_s[lane][w];
+      thi = (float)t;
+      tlo = (float)(t - (double)thi);
+    } else if (PREC == SEP_PREC_PLAIN) {
       float x = red_s[lane][0];
 #pragma unroll
       for (int w = 1; w < kWarps; ++w) x = __fadd_rn(x, red_s[lane][w]);
-      tot = (double)x;
+      thi = x;
+    } else {   // error-free pairs (value = hs - hc)
+      float hs = red_s[lane][0], hc = red_c[lane][0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) pair_add(hs, hc, red_s[lane][w], red_c[lane][w]);
+      two_sum(hs, -hc, thi, tlo);
     }
+  } else if (warp == 0 && lane < NF + NI) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) x += red_i[lane - NF][w];
+    thi = __uint_as_float(x);   // integer totals travel as raw bits (packed counts exceed 2^24)
   }
-  return tot;
 }
 
 template <int DT, int MODE, int PREC, int kThreads>
 __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
   constexpr int kWarps = kThreads / 32;
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
-  // MODE_UNIT: one class of weight 1; sums (count, S1, S2).
-  // MODE_CLASS / MODE_ENTRY: sums (count, Omega, A1, OO, B1, B2).
-  constexpr int NV = MODE == MODE_UNIT ? 3 : 6;
+  // Per pass, float sums and integer counts:
+  //   MODE_UNIT:  (S1, S2) + count
+  //   MODE_CLASS: (A1, B1, B2) + class counts packed 16 + 16 bits in two words
+  //   MODE_ENTRY: (Omega, A1, OO, B1, B2) + count
+  // (a row holds fewer than 2^16 entries: its values must fit shared memory)
+  constexpr int NF = MODE == MODE_UNIT ? 2 : (MODE == MODE_CLASS ? 3 : 5);
+  constexpr int NI = MODE == MODE_CLASS ? 2 : 1;
+  constexpr int NV = NF > 3 ? NF : 3;   // the first pass reduces 3 floats
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* vals = reinterpret_cast<float*>(smem_raw);
   float* wts = vals + a.cap;   // MODE_ENTRY only: per-entry weight
   __shared__ float red_s[NV][kWarps], red_c[NV][kWarps];
+  __shared__ uint32_t red_i[NI][kWarps];
   __shared__ Bcast st;
 
   const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
@@ -206,12 +285,24 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
   }
 
   for (int f = f0; f < f1; ++f) {
-    const void* frame = frame_ptr<DT>(a.frames, f, a.npix);
+    const void* frame = a.fptr ? (const void*)a.fptr[f] : frame_ptr<DT>(a.frames, f, a.npix);
     // ------------- gather + correct; rough sums giving the first shift -------------
     float s0[NV], c0[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) s0[v] = c0[v] = 0.0f;
     {
+      // Stage the row's packed entries into the value slots (16-byte
+      // cp.async copies); each thread later reads only the slots it staged,
+      // so its own wait_group is the only synchronisation needed. The
+      // gathers then depend on a shared-memory read, not on a global load.
+      {
+        const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
+        for (int q = tid; q < nq; q += kThreads)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
+                       : "memory");
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+      }
+      const uint4* ents = reinterpret_cast<const uint4*>(vals);
       float om = 0.0f, vv = 0.0f, v2 = 0.0f;
       // two vectors of 4 entries per step, every load issued before any use
       for (int qa = tid; qa < nq; qa += 2 * kThreads) {
@@ -222,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const bool ok = qs[h] < nq;
-          const uint4 u = ok ? __ldg(ent4 + qs[h]) : make_uint4(kPad, kPad, kPad, kPad);
+          const uint4 u = ok ? ents[qs[h]] : make_uint4(kPad, kPad, kPad, kPad);
           uu[h][0] = u.x; uu[h][1] = u.y; uu[h][2] = u.z; uu[h][3] = u.w;
           if (DT == SEP_DTYPE_U16_JF && ok) {
             const float4* cal4 = reinterpret_cast<const float4*>(a.cal0 + r0);
@@ -292,16 +383,18 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
       s0[2] = v2;
     }
     {
-      const double t = block_sum<NV, SEP_PREC_PLAIN, kWarps>(s0, c0, red_s, red_c);
+      uint32_t none[1] = {0u};
+      float thi, tlo;
+      block_sum<NV, 1, SEP_PREC_PLAIN, kWarps>(s0, c0, none, red_s, red_c, red_i, thi, tlo);
       // lanes 0, 1, 2 of warp 0 hold Omega, V, sum w v^2
-      const double Om = __shfl_sync(0xffffffffu, t, 0);
-      const double V = __shfl_sync(0xffffffffu, t, 1);
-      const double V2 = __shfl_sync(0xffffffffu, t, 2);
+      const float Om = __shfl_sync(0xffffffffu, thi, 0);
+      const float V = __shfl_sync(0xffffffffu, thi, 1);
+      const float V2 = __shfl_sync(0xffffffffu, thi, 2);
       if (tid == 0) {
         float K = 0.0f;
-        if (Om > 0.0) {
-          const float m = __fdiv_rn((float)V, (float)Om);
-          const float var = __fsub_rn(__fdiv_rn((float)V2, (float)Om), m * m);
+        if (Om > 0.0f) {
+          const float m = __fdiv_rn(V, Om);
+          const float var = __fsub_rn(__fdiv_rn(V2, Om), m * m);
           K = choose_shift(m, var > 0.0f ? sqrtf(var) : 0.0f);
         }
         st.Kf = K;
@@ -312,8 +405,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         st.n_cur = -1.0f;
         st.steps = -1;
         st.done = 0;
-        st.mu = 0.0;
-        st.sd = 0.0;
+        st.mu_hi = st.mu_lo = st.sd = 0.0f;
+        st.mu_d = st.sd_d = 0.0;
       }
       __syncthreads();   // values and state visible to all
     }
@@ -321,16 +414,19 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
     for (;;) {
       // ------------- one pass: shifted sums over entries in [Ln, Hn] -------------
       const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
-      float ss[NV], cc[NV];
+      float ss[NF], cc[NF];
+      uint32_t ci[NI];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ss[v] = cc[v] = 0.0f;
+      for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) ci[i] = 0u;
       if (MODE == MODE_CLASS) {
         int lo = 0;
 #pragma unroll
         for (int cls = 0; cls < 4; ++cls) {
           const int hi = ge[cls];
           const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
-          float cnt = 0.0f;
+          uint32_t cnt = 0;
           Acc<KAHAN> a1, a2;
           for (int q = (lo >> 2) + tid; q < (hi >> 2); q += kThreads) {
             const float4 v4 = vals4[q];
@@ -339,31 +435,28 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
             for (int j = 0; j < 4; ++j) {
               if (xs[j] >= Ln && xs[j] <= Hn) {
                 const float d = __fsub_rn(xs[j], Kf);
-                cnt += 1.0f;
+                ++cnt;
                 a1.add(d);
                 a2.add(__fmul_rn(d, d));
               }
             }
           }
-          // weights k/4 times counts below 2^22 are exact in FP32
           const float s1 = a1.val(), s2 = a2.val();
-          ss[0] += cnt;
-          ss[1] += w * cnt;
-          ss[3] += w2 * cnt;
+          ci[cls >> 1] += cnt << (16 * (cls & 1));
           if (KAHAN) {
-            Acc<true> t2, t4, t5;
-            t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w, s1)); ss[2] = t2.s; cc[2] = t2.c;
-            t4.s = ss[4]; t4.c = cc[4]; t4.add(__fmul_rn(w2, s1)); ss[4] = t4.s; cc[4] = t4.c;
-            t5.s = ss[5]; t5.c = cc[5]; t5.add(__fmul_rn(w2, s2)); ss[5] = t5.s; cc[5] = t5.c;
+            Acc<true> t0, t1, t2;
+            t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
+            t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
+            t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
           } else {
-            ss[2] = fmaf(w, s1, ss[2]);
-            ss[4] = fmaf(w2, s1, ss[4]);
-            ss[5] = fmaf(w2, s2, ss[5]);
+            ss[0] = fmaf(w, s1, ss[0]);
+            ss[1] = fmaf(w2, s1, ss[1]);
+            ss[2] = fmaf(w2, s2, ss[2]);
           }
           lo = hi;
         }
       } else if (MODE == MODE_UNIT) {
-        float cnt = 0.0f;
+        uint32_t cnt = 0;
         Acc<KAHAN> a1, a2;
         for (int q = tid; q < (ge[0] >> 2); q += kThreads) {
           const float4 v4 = vals4[q];
@@ -372,15 +465,16 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
           for (int j = 0; j < 4; ++j) {
             if (xs[j] >= Ln && xs[j] <= Hn) {
               const float d = __fsub_rn(xs[j], Kf);
-              cnt += 1.0f;
+              ++cnt;
               a1.add(d);
               a2.add(__fmul_rn(d, d));
             }
           }
         }
-        ss[0] = cnt; ss[1] = a1.s; cc[1] = a1.c; ss[2] = a2.s; cc[2] = a2.c;
+        ci[0] = cnt;
+        ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
       } else {
-        float cnt = 0.0f;
+        uint32_t cnt = 0;
         Acc<KAHAN> om, a1, oo, b1, b2;
         for (int q = tid; q < (ge[3] >> 2); q += kThreads) {
           const float4 v4 = vals4[q];
@@ -392,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
               const float d = __fsub_rn(xs[j], Kf);
               const float w2 = __fmul_rn(w, w);
               const float w2d = __fmul_rn(w2, d);
-              cnt += 1.0f;
+              ++cnt;
               om.add(w);
               a1.add(__fmul_rn(w, d));
               oo.add(w2);
@@ -401,39 +495,61 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
             }
           }
         }
-        ss[0] = cnt;
-        ss[1] = om.s; cc[1] = om.c; ss[2] = a1.s; cc[2] = a1.c; ss[3] = oo.s; cc[3] = oo.c;
-        ss[4] = b1.s; cc[4] = b1.c; ss[5] = b2.s; cc[5] = b2.c;
+        ci[0] = cnt;
+        ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
+        ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
       }
-      const double tot = block_sum<NV, PREC, kWarps>(ss, cc, red_s, red_c);
+      float thi, tlo;
+      block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
       if (warp == 0) {
-        double t[NV];
+        float th[NF + NI], tl[NF + NI];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) t[v] = __shfl_sync(0xffffffffu, tot, v);
+        for (int v = 0; v < NF + NI; ++v) {
+          th[v] = __shfl_sync(0xffffffffu, thi, v);
+          tl[v] = __shfl_sync(0xffffffffu, tlo, v);
+        }
         if (lane == 0) {
+          // sums of the measured set: 0 Omega, 1 A1, 2 OO, 3 B1, 4 B2 (pairs) and its size
+          float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+          float n_set;
+          if (MODE == MODE_CLASS) {
+            // class counts (exact integers); their weighted sums are exact in FP32
+            const uint32_t p01 = __float_as_uint(th[3]), p23 = __float_as_uint(th[4]);
+            const float n0 = (float)(p01 & 0xffffu), n1 = (float)(p01 >> 16);
+            const float n2 = (float)(p23 & 0xffffu), n3 = (float)(p23 >> 16);
+            n_set = n0 + n1 + n2 + n3;
+            h[0] = n0 + 0.75f * n1 + 0.5f * n2 + 0.25f * n3;
+            h[2] = n0 + 0.5625f * n1 + 0.25f * n2 + 0.0625f * n3;
+            h[1] = th[0]; l[1] = tl[0];
+            h[3] = th[1]; l[3] = tl[1];
+            h[4] = th[2]; l[4] = tl[2];
+          } else if (MODE == MODE_UNIT) {
+            n_set = (float)__float_as_uint(th[2]);
+            h[0] = h[2] = n_set;
+            h[1] = h[3] = th[0]; l[1] = l[3] = tl[0];
+            h[4] = th[1]; l[4] = tl[1];
+          } else {
+            n_set = (float)__float_as_uint(th[5]);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) { h[v] = th[v]; l[v] = tl[v]; }
+          }
           // the pass measured S' = S ∩ [Ln, Hn]; S' == S means nothing was discarded
-          if (st.steps >= 0 && (float)t[0] == st.n_cur) {
+          if (st.steps >= 0 && n_set == st.n_cur) {
             st.done = 1;
           } else {
-            st.n_cur = (float)t[0];
+            st.n_cur = n_set;
             st.L = Ln;
             st.H = Hn;
-            double mu, sd;
-            if (MODE == MODE_UNIT)
-              finalise<PREC>((double)Kf, t[0], t[1], t[0], t[1], t[2], mu, sd);
-            else
-              finalise<PREC>((double)Kf, t[1], t[2], t[3], t[4], t[5], mu, sd);
-            st.mu = mu;
-            st.sd = sd;
+            finalise<PREC>(Kf, h, l, st);
             st.steps += 1;
             if (st.steps >= a.n_iter) {
               st.done = 1;
             } else {   // next set: reject |v - mu| > k sd (Eq. 19), cumulatively
               float L2 = Ln, H2 = Hn;
-              clip_bounds<PREC>(mu, sd, a.k_clip, L2, H2);
+              clip_bounds<PREC>(st, a.k_clip, L2, H2);
               st.Ln = L2;
               st.Hn = H2;
-              st.Kf = choose_shift((float)mu, (float)sd);
+              st.Kf = choose_shift(st.mu_hi, st.sd);
             }
           }
         }
@@ -441,11 +557,10 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
       __syncthreads();
       if (st.done) break;
     }
-    const double mu = st.mu, sd = st.sd;
-    const int64_t o = (int64_t)f * a.nbins + b;
+    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (tid == 0) {
-      a.mean[o] = (float)mu;
-      a.sigma[o] = (float)sd;
+      a.mean[o] = st.mu_hi;
+      a.sigma[o] = st.sd;
       a.count[o] = (int32_t)st.n_cur;
       if (a.bounds) {
         a.bounds[2 * o] = st.L;
@@ -456,9 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
     // ---------------- sparsification mark (Section 3) ----------------
     if (a.bitmap) {
       __shared__ float thr_s;
-      if (tid == 0)
-        thr_s = PREC == SEP_PREC_PLAIN ? __fadd_rn((float)mu, __fmul_rn(a.k_pick, (float)sd))
-                                       : __double2float_rd(fma((double)a.k_pick, sd, mu));
+      if (tid == 0) thr_s = pick_threshold<PREC>(st, a.k_pick);
       __syncthreads();
       const float thr = thr_s;
       uint32_t* bm = a.bitmap + (int64_t)f * a.words;
@@ -510,7 +623,8 @@ cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int m
   switch (prec) {
     case SEP_PREC_PLAIN: return launch_b<DT, MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
     case SEP_PREC_KAHAN: return launch_b<DT, MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);
-    default: return launch_b<DT, MODE, SEP_PREC_FP64MERGE>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_FP64MERGE: return launch_b<DT, MODE, SEP_PREC_FP64MERGE>(a, n_ctas, tpb, mode, s);
+    default: return launch_b<DT, MODE, SEP_PREC_DWORD>(a, n_ctas, tpb, mode, s);
   }
 }
 

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
     if (threadIdx.x == 0) {
       base_s = before;
       if (tile == 0) {
-        n_kept[f] = (int32_t)all;
+        n_kept[p.fidx ? p.fidx[f] : f] = (int32_t)all;
         if (all > cap) atomicOr(status, SEP_DEV_CAPACITY);
       }
     }
@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
   const int64_t base = base_s;
   if (base >= cap) return;
   const uint32_t* bm = bitmap + f * words;
-  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
+  const void* frame = p.fptr ? (const void*)p.fptr[f] : frame_ptr<DT>(p.frames, f, p.npix);
+  const int64_t g = p.fidx ? p.fidx[f] : f;   // output row of this frame
   const int64_t w0 = (int64_t)tile * kTileWords + (int64_t)threadIdx.x * kWordsPerThread;
   uint32_t wv[kWordsPerThread];
   if (w0 + kWordsPerThread <= words) {
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
       const int bit = __ffs(m) - 1;
       m &= m - 1u;
       const int64_t i = (w0 + j) * 32 + bit;
-      idx[f * cap + pos] = (int32_t)i;
-      val[f * cap + pos] = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
+      idx[g * cap + pos] = (int32_t)i;
+      val[g * cap + pos] = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
       ++pos;
     }
   }
@@ -207,14 +208,15 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_flags(PixArgs p, const ui
                                                              int32_t* chunk_cnt, int32_t n_chunks) {
   const int64_t f = blockIdx.y;
   const uint32_t* bm = bitmap + f * words;
-  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
-  int64_t n = n_kept[f];
+  const void* frame = p.fptr ? (const void*)p.fptr[f] : frame_ptr<DT>(p.frames, f, p.npix);
+  const int64_t g = p.fidx ? p.fidx[f] : f;
+  int64_t n = n_kept[g];
   if (n > kcap) n = kcap;
   const int h = patch >> 1;
   for (int64_t ch = blockIdx.x; ch * kPeakChunk < n; ch += gridDim.x) {
     const int64_t k = ch * kPeakChunk + threadIdx.x;
     bool peak = false;
-    const int64_t i = k < n ? idx[f * kcap + k] : -1;
+    const int64_t i = k < n ? idx[g * kcap + k] : -1;
     if (i >= 0 && i < p.npix && __ldg(p.bop + i) >= 0) {
       int nk;
       const float vi = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
@@ -239,7 +241,8 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
                                                     int32_t* status) {
   __shared__ int sh[32];
   const int64_t f = blockIdx.x;
-  int64_t n = n_kept[f];
+  const int64_t g = p.fidx ? p.fidx[f] : f;
+  int64_t n = n_kept[g];
   if (n > kcap) n = kcap;
   const int nch = (int)((n + kPeakChunk - 1) / kPeakChunk);
   // chunk counts become chunk offsets, in place (a count <= kcap < 2^31)
@@ -255,13 +258,14 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    n_peaks[f] = (int32_t)total;
+    n_peaks[g] = (int32_t)total;
     if (total > pcap) atomicOr(status, SEP_DEV_CAPACITY);
   }
   const uint32_t* bm = bitmap + f * words;
-  const void* frame = frame_ptr<DT>(p.frames, f, p.npix);
-  const float* mu = mean + (int64_t)f * nbins;
-  const float* sd = sigma + (int64_t)f * nbins;
+  const void* frame = p.fptr ? (const void*)p.fptr[f] : frame_ptr<DT>(p.frames, f, p.npix);
+  const int64_t row = p.orow ? p.orow[f] : f * (int64_t)nbins;
+  const float* mu = mean + row;
+  const float* sd = sigma + row;
   const int h = patch >> 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t* fl = flags + f * ((int64_t)n_chunks * 8);
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
       if ((m >> lane) & 1u) {
         const int64_t pos = rank + __popc(m & ((1u << lane) - 1u));
         const int64_t k = (int64_t)c * kPeakChunk + wd * 32 + lane;
-        const int64_t i = idx[f * kcap + k];
+        const int64_t i = idx[g * kcap + k];
         if (pos < pcap) {
           const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
           const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
           rec.x = sx / I;
           rec.sigma = sqrtf(s2);
           rec.npix = nk;
-          peaks[f * pcap + pos] = rec;
+          peaks[g * pcap + pos] = rec;
         }
       }
       rank += __popc(m);

@@ -85,7 +85,7 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
   if (!(p->k_pick >= 0.0f) || !isfinite(p->k_pick)) return fail(ctx, SEP_ERR_ARG, "k_pick must be finite and >= 0");
   if (p->patch < 1 || p->patch > 15 || (p->patch & 1) == 0) return fail(ctx, SEP_ERR_ARG, "patch must be odd in [1, 15]");
   if (p->min_count < 1) return fail(ctx, SEP_ERR_ARG, "min_count must be >= 1");
-  if (p->precision < SEP_PREC_PLAIN || p->precision > SEP_PREC_FP64MERGE) return fail(ctx, SEP_ERR_ARG, "unknown precision");
+  if (p->precision < SEP_PREC_PLAIN || p->precision > SEP_PREC_DWORD) return fail(ctx, SEP_ERR_ARG, "unknown precision");
   for (int i = 0; i < 4; ++i)
     if (p->reserved[i] != 0) return fail(ctx, SEP_ERR_ARG, "reserved params must be 0");
   return SEP_OK;
@@ -224,7 +224,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
 // caller's stream, several as parallel branches (fork / join through events,
 // which a stream capture records as graph edges).
 cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int32_t dtype, int32_t precision,
-                         int mode, cudaStream_t s) {
+                         int mode, cudaStream_t s, bool allow_fork = true) {
   const bool split = csr->h.split > 1;
   if (csr->plan.empty()) {
     a.bin_list = nullptr;
@@ -232,7 +232,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
     return sep::launch_integrate_clip(a, csr->h.nbins, 256, dtype, split, csr->has_norm, precision, mode, s);
   }
   const int nc = (int)csr->plan.size();
-  if (nc == 1 || mode == 1) {
+  if (nc == 1 || mode == 1 || !allow_fork) {
     for (const auto& k : csr->plan) {
       a.bin_list = k.d_bins;
       a.cap = k.cap;
@@ -299,6 +299,8 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
+  if (ctx->d_desc) cudaFree(ctx->d_desc);
+  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   for (int i = 1; i < 4; ++i) {
     if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
     if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
@@ -738,6 +740,193 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
       fclose(fp);
     }
   }
+  return SEP_OK;
+}
+
+
+sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, const sep_calib* const* calibs,
+                             const sep_frame_desc* frames, int32_t n_frames, const sep_params* params,
+                             float* mean_dev, float* sigma_dev, int32_t* count_dev, int64_t* row_off,
+                             int32_t* idx_dev, float* val_dev, int64_t kept_capacity, int32_t* n_kept_dev,
+                             sep_peak* peaks_dev, int64_t peak_capacity, int32_t* n_peaks_dev, int32_t use_graph,
+                             sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (n_det < 1 || n_det > 4 || !csrs) return fail(ctx, SEP_ERR_ARG, "1 to 4 detectors");
+  if (n_frames < 0 || (n_frames > 0 && !frames)) return fail(ctx, SEP_ERR_ARG, "bad frame list");
+  if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
+  sep_status st = check_params(ctx, params);
+  if (st != SEP_OK) return st;
+  if (n_frames > 0 && (!mean_dev || !sigma_dev || !count_dev || !n_kept_dev || !n_peaks_dev ||
+                       (kept_capacity > 0 && (!idx_dev || !val_dev)) || (peak_capacity > 0 && !peaks_dev)))
+    return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  for (int d = 0; d < n_det; ++d) {
+    if (!csrs[d] || csrs[d]->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr missing or from another context");
+    if ((st = check_bin_fits(ctx, csrs[d])) != SEP_OK) return st;
+  }
+  std::vector<std::vector<int32_t>> members(n_det);
+  std::vector<int64_t> rows((size_t)n_frames + 1, 0);
+  for (int32_t g = 0; g < n_frames; ++g) {
+    const sep_frame_desc& fd = frames[g];
+    if (fd.det < 0 || fd.det >= n_det || !fd.frame_dev) return fail(ctx, SEP_ERR_ARG, "bad frame descriptor");
+    if (fd.dtype == SEP_DTYPE_U16_JF) {
+      const sep_calib* c = calibs ? calibs[fd.det] : nullptr;
+      if (!c || c->ctx != ctx || c->npix != csrs[fd.det]->npix)
+        return fail(ctx, SEP_ERR_ARG, "raw frames need their detector's calibration");
+    } else if (fd.dtype != SEP_DTYPE_F32) {
+      return fail(ctx, SEP_ERR_ARG, "unknown dtype");
+    }
+    if (g > 0 && fd.det == frames[g - 1].det && fd.dtype != frames[g - 1].dtype) {
+      // frames of one detector share a dtype (one kernel variant per detector)
+    }
+    members[fd.det].push_back(g);
+    rows[g + 1] = rows[g] + csrs[fd.det]->h.nbins;
+  }
+  for (int d = 0; d < n_det; ++d)
+    for (int32_t g : members[d])
+      if (frames[g].dtype != frames[members[d][0]].dtype)
+        return fail(ctx, SEP_ERR_ARG, "frames of one detector must share a dtype");
+  if (row_off) memcpy(row_off, rows.data(), rows.size() * sizeof(int64_t));
+  if (n_frames == 0) return SEP_OK;
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // descriptor table (device): per detector fptr[m], orow[m], fidx[m]
+  std::vector<int64_t> desc;
+  std::vector<size_t> off_fptr(n_det), off_orow(n_det), off_fidx(n_det);
+  int64_t bm_total = 0, aux_total = 0;
+  std::vector<int64_t> bm_off(n_det), aux_off(n_det), words(n_det);
+  for (int d = 0; d < n_det; ++d) {
+    const int64_t m = (int64_t)members[d].size();
+    off_fptr[d] = desc.size();
+    for (int32_t g : members[d]) desc.push_back((int64_t)(uintptr_t)frames[g].frame_dev);
+    off_orow[d] = desc.size();
+    for (int32_t g : members[d]) desc.push_back(rows[g]);
+    off_fidx[d] = desc.size();
+    for (size_t i = 0; i < members[d].size(); i += 2)
+      desc.push_back((int64_t)(uint32_t)members[d][i] |
+                     (i + 1 < members[d].size() ? (int64_t)members[d][i + 1] << 32 : 0));
+    words[d] = bitmap_words(csrs[d]->npix);
+    bm_off[d] = bm_total;
+    bm_total += words[d] * m;
+    aux_off[d] = aux_total;
+    aux_total += sep::consumer_scratch_words((int32_t)m, words[d], kept_capacity);
+  }
+  if ((st = ensure_scratch(ctx, bm_total, 0, aux_total)) != SEP_OK) return st;
+  if (desc.size() > ctx->desc_len) {
+    if (ctx->d_desc) cudaFree(ctx->d_desc);
+    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+    ctx->d_desc = nullptr;
+    ctx->h_desc = nullptr;
+    ctx->desc_len = 0;
+    if (cudaMalloc((void**)&ctx->d_desc, desc.size() * 8) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_desc, desc.size() * 8) != cudaSuccess)
+      return fail(ctx, SEP_ERR_OOM, "descriptor table allocation failed");
+    ctx->desc_len = desc.size();
+  }
+  // the previous call's copy may still be reading the staging buffer
+  SEP_CUDA(ctx, cudaStreamSynchronize(s));
+  memcpy(ctx->h_desc, desc.data(), desc.size() * 8);
+  SEP_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc.size() * 8, cudaMemcpyHostToDevice, s));
+
+  auto enqueue = [&](int mode) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (mode != 1) e = cudaEventRecord(ctx->ev_fork, s);
+    for (int d = 0; d < n_det && e == cudaSuccess; ++d) {
+      const int32_t m = (int32_t)members[d].size();
+      if (m == 0) continue;
+      const sep_csr* csr = csrs[d];
+      const int32_t dtype = frames[members[d][0]].dtype;
+      const sep_calib* calib = calibs ? calibs[d] : nullptr;
+      cudaStream_t sd = d == 0 ? s : ctx->aux[d];
+      if (d > 0 && mode != 1) e = cudaStreamWaitEvent(sd, ctx->ev_fork, 0);
+      uint32_t* bm = ctx->d_bitmap + bm_off[d];
+      int32_t* aux = ctx->d_aux + aux_off[d];
+      const uint64_t* fptr = reinterpret_cast<const uint64_t*>(ctx->d_desc + off_fptr[d]);
+      const int64_t* orow = ctx->d_desc + off_orow[d];
+      const int32_t* fidx = reinterpret_cast<const int32_t*>(ctx->d_desc + off_fidx[d]);
+      sep::ClipArgs ca = clip_args(ctx, csr, calib, nullptr, dtype, m, params, mean_dev, sigma_dev, count_dev, nullptr,
+                                   nullptr, bm, words[d]);
+      ca.fptr = fptr;
+      ca.orow = orow;
+      if (mode == 1) {
+        e = enqueue_clip(ctx, csr, ca, dtype, params->precision, 1, sd, false);
+        continue;
+      }
+      sep::PixArgs pa = pix_args(csr, calib, nullptr, dtype);
+      pa.fptr = fptr;
+      pa.fidx = fidx;
+      pa.orow = orow;
+      if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
+      if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, dtype, params->precision, mode, sd, false);
+      if (e == cudaSuccess)
+        e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,
+                                sd);
+      if (e == cudaSuccess)
+        e = sep::launch_peaks(pa, m, csr->h.nbins, mean_dev, sigma_dev, bm, words[d], idx_dev, n_kept_dev,
+                              kept_capacity, params->patch, params->min_count, peaks_dev, peak_capacity, n_peaks_dev,
+                              aux, ctx->d_status, sd);
+      if (e == cudaSuccess && d > 0) e = cudaEventRecord(ctx->ev_join[d], sd);
+    }
+    for (int d = 1; d < n_det && e == cudaSuccess && mode != 1; ++d)
+      if (!members[d].empty()) e = cudaStreamWaitEvent(s, ctx->ev_join[d], 0);
+    return e;
+  };
+
+  if (!use_graph || s == nullptr) {
+    cudaError_t e = enqueue(0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "process_mixed launch");
+    return SEP_OK;
+  }
+  std::vector<uint64_t> key = {0x6d69786564ull, (uint64_t)n_frames, (uint64_t)(uintptr_t)mean_dev,
+                               (uint64_t)(uintptr_t)sigma_dev, (uint64_t)(uintptr_t)count_dev,
+                               (uint64_t)(uintptr_t)idx_dev, (uint64_t)(uintptr_t)val_dev, (uint64_t)kept_capacity,
+                               (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev, (uint64_t)peak_capacity,
+                               (uint64_t)(uintptr_t)n_peaks_dev, (uint64_t)(uintptr_t)ctx->d_bitmap,
+                               (uint64_t)(uintptr_t)ctx->d_aux, (uint64_t)(uintptr_t)ctx->d_desc,
+                               (uint64_t)(uintptr_t)s};
+  for (int d = 0; d < n_det; ++d) {
+    key.push_back((uint64_t)(uintptr_t)csrs[d]);
+    key.push_back(csrs[d]->plan_version);
+    key.push_back((uint64_t)(uintptr_t)(calibs ? calibs[d] : nullptr));
+  }
+  for (int32_t g = 0; g < n_frames; ++g) key.push_back(((uint64_t)frames[g].det << 8) | (uint64_t)frames[g].dtype);
+  for (int64_t v : desc) key.push_back((uint64_t)v);
+  {
+    uint32_t pw[sizeof(sep_params) / 4];
+    memcpy(pw, params, sizeof(sep_params));
+    for (uint32_t w : pw) key.push_back(w);
+  }
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (ctx->graphs.size() >= 16) {
+      auto lru = ctx->graphs.begin();
+      for (auto j = ctx->graphs.begin(); j != ctx->graphs.end(); ++j)
+        if (j->second.last_use < lru->second.last_use) lru = j;
+      cudaGraphExecDestroy(lru->second.exec);
+      cudaGraphDestroy(lru->second.graph);
+      ctx->graphs.erase(lru);
+    }
+    cudaError_t e = enqueue(1);   // kernel attributes, outside the capture
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute");
+    sep_graph_entry g;
+    SEP_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    e = enqueue(2);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e != cudaSuccess ? e : e2, "process_mixed capture");
+    }
+    g.graph = graph;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    it = ctx->graphs.emplace(key, g).first;
+  }
+  it->second.last_use = ++ctx->use_clock;
+  SEP_CUDA(ctx, cudaGraphLaunch(it->second.exec, s));
   return SEP_OK;
 }
 

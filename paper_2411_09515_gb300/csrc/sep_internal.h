@@ -66,6 +66,10 @@ struct ClipArgs {
   int32_t* iters;          // optional [F][B]
   uint32_t* bitmap;        // optional kept-pixel map [F][words]
   int64_t words;           // bitmap words per frame
+  // mixed batches: per launch frame, its address and the first output row
+  // (in bins) of its profile; null = contiguous frames, rows f * nbins
+  const uint64_t* fptr = nullptr;
+  const int64_t* orow = nullptr;
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
@@ -76,6 +80,11 @@ struct PixArgs {           // what the consumers need to recompute a pixel value
   const float* gain;
   const float* norm;       // may be null
   const int32_t* bop;      // [npix], -1 masked
+  // mixed batches: per launch frame, its address, its index among the
+  // call's frames (rows of the kept / peak outputs) and its profile row
+  const uint64_t* fptr = nullptr;
+  const int32_t* fidx = nullptr;
+  const int64_t* orow = nullptr;
 };
 
 // mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
@@ -127,6 +136,9 @@ struct sep_ctx {
   size_t thr_len = 0;
   int32_t* d_aux = nullptr;    // consumer scratch (tile counts, flag bits)
   size_t aux_len = 0;
+  int64_t* d_desc = nullptr;   // mixed batches: per-frame descriptor table
+  int64_t* h_desc = nullptr;   // its pinned staging copy
+  size_t desc_len = 0;
   // captured batches, keyed by every launch argument
   std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
   uint64_t use_clock = 0;

@@ -13,8 +13,8 @@ from parity import Frame, check_clip, check_kept, check_peaks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2411_09515_gb300 import (SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator,  # noqa: E402
-                                    peaks_to_numpy)
+from paper_2411_09515_gb300 import (SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN,  # noqa: E402
+                                    Separator, peaks_to_numpy)
 
 
 def run_batch(sep, frames_np, kcap, pcap, use_graph=True):
@@ -102,7 +102,7 @@ def jf_small():
     return det, mask, cal, fr, W
 
 
-@pytest.mark.parametrize("precision", [SEP_PREC_FP64MERGE, SEP_PREC_KAHAN])
+@pytest.mark.parametrize("precision", [SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN])
 def test_jungfrau_raw_split_parity(jf_small, precision):
     det, mask, cal, fr, W = jf_small
     sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)

@@ -1,4 +1,4 @@
-"""Precision study: PLAIN, KAHAN and FP64MERGE against the FP64 oracle on
+"""Precision study: PLAIN, KAHAN, FP64MERGE and DWORD against the FP64 oracle on
 high-dynamic-range Jungfrau-shaped raw frames (background 0.01-50 photons/px,
 spots to 5e4 photons, so all three gain levels occur).
 
@@ -22,10 +22,10 @@ from parity import BAND, Frame
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2411_09515_gb300 import (SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator,  # noqa: E402
-                                    peaks_to_numpy)
+from paper_2411_09515_gb300 import (SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN,  # noqa: E402
+                                    Separator, peaks_to_numpy)
 
-MODES = {"plain": SEP_PREC_PLAIN, "kahan": SEP_PREC_KAHAN, "fp64merge": SEP_PREC_FP64MERGE}
+MODES = {"plain": SEP_PREC_PLAIN, "kahan": SEP_PREC_KAHAN, "fp64merge": SEP_PREC_FP64MERGE, "dword": SEP_PREC_DWORD}
 
 
 def study(det, n_frames, seed=21):
@@ -89,7 +89,7 @@ def test_precision_modes_small():
     r = study(det, 6)
     _emit(r)
     assert r["gain_level_pixels"][1] > 0 and r["gain_level_pixels"][3] > 0   # levels 1 and 2 both occur
-    for name in ("fp64merge", "kahan"):
+    for name in ("dword", "fp64merge", "kahan"):
         assert r[name]["mean_rel_err_max"] < 1e-5 and r[name]["sigma_rel_err_max"] < 1e-5
         assert r[name]["kept_mismatch_outside_band"] == 0
         assert r[name]["centroid_err_px_max"] < 1e-3
@@ -101,4 +101,5 @@ def test_precision_modes_small():
 def test_precision_modes_jf4m_256():
     r = study(synth.det_jf4m(), 256)
     _emit(r)
-    assert r["fp64merge"]["mean_rel_err_max"] < 1e-5 and r["fp64merge"]["sigma_rel_err_max"] < 1e-5
+    for name in ("dword", "fp64merge"):
+        assert r[name]["mean_rel_err_max"] < 1e-5 and r[name]["sigma_rel_err_max"] < 1e-5
