@@ -77,6 +77,7 @@ typedef int32_t sep_status;
 typedef struct sep_ctx sep_ctx;
 typedef struct sep_csr sep_csr;
 typedef struct sep_calib sep_calib;
+typedef struct sep_model sep_model;
 typedef struct CUstream_st* sep_stream; /* identical to cudaStream_t */
 
 /* ---- plain structs ----------------------------------------------------- */
@@ -107,7 +108,12 @@ typedef struct {
   int32_t patch;             /* peak patch side, odd, 1 .. 15 (Section 4) */
   int32_t min_count;         /* minimum kept pixels in the patch, >= 1 */
   int32_t precision;         /* SEP_PREC_* */
-  int32_t reserved[4];       /* must be 0 */
+  int32_t surrogate;         /* 0: plain clip loop. n in 1 .. 8: start from the
+                                prediction of the model attached to the CSR
+                                (sep_csr_attach_model) and verify it in at most n
+                                passes, else run the plain loop for that bin;
+                                needs precision SEP_PREC_DWORD */
+  int32_t reserved[3];       /* must be 0 */
 } sep_params;
 
 /* One peak (Section 4). y, x: centroid in pixel units (row, column axes,
@@ -291,6 +297,94 @@ sep_status sep_csr_get_plan(const sep_csr* csr, int32_t* n_classes, int32_t* thr
 sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                         int32_t dtype, int32_t n_frames, const sep_params* params, const char* cache_path,
                         float* best_ms, sep_stream stream);
+
+/* ---- learned surrogate of the clip iteration ------------------------------ */
+/*
+ * A small network (no counterpart in the paper) predicts a bin's clipped mean
+ * and deviation from its first-pass statistics, so the clip loop can start
+ * from the prediction and stop once verified; the plain loop remains the
+ * fallback. Network: SEP_MLP_IN features -> 64 -> GELU -> 64 -> GELU -> 2,
+ * GELU exact (x Phi(x)), weights stored BF16 for every forward / backward,
+ * FP32 master copy and FP32 accumulation. Parameter layout (floats):
+ * W1 [64][20], b1 [64], W2 [64][64], b2 [64], W3 [2][64], b3 [2].
+ * Normalisation block: feature mean [20], feature deviation [20], target
+ * mean [2], target deviation [2] (used only by the clip kernel's inference;
+ * sep_mlp_* and sep_surrogate_train work on already normalised data).
+ */
+#define SEP_MLP_IN 20
+#define SEP_MLP_HIDDEN 64
+#define SEP_MLP_OUT 2
+#define SEP_MLP_PARAMS 5634
+#define SEP_MLP_NORM 44
+
+typedef struct {
+  int32_t epochs;   /* passes over the samples, >= 1 */
+  int32_t batch;    /* samples per Adam step, >= 64 */
+  float lr;         /* Adam learning rate, > 0 */
+  int32_t pad;
+  uint64_t seed;    /* visiting order */
+} sep_train_cfg;
+
+/* New model with He-uniform weights from `seed`, zero biases, identity normalisation. */
+sep_status sep_model_create(sep_ctx* ctx, uint64_t seed, sep_model** out);
+void sep_model_destroy(sep_model* model);
+/* Copy the parameters out to get_host and / or in from set_host (either may be NULL), [SEP_MLP_PARAMS]. */
+sep_status sep_model_params(sep_model* model, float* get_host, const float* set_host);
+/* Same for the normalisation block [SEP_MLP_NORM]; deviations must be > 0. */
+sep_status sep_model_norm(sep_model* model, float* get_host, const float* set_host);
+/* y_dev [n][2] = network(x_dev [n][20]) on device memory. */
+sep_status sep_mlp_forward(sep_model* model, const float* x_dev, int64_t n, float* y_dev, sep_stream stream);
+/* Loss L = mean over n samples of the summed squared error against t_dev [n][2]
+ * into *loss_dev, and dL/dparams into grad_dev [SEP_MLP_PARAMS] (device). */
+sep_status sep_mlp_loss_grad(sep_model* model, const float* x_dev, const float* t_dev, int64_t n,
+                             float* grad_dev, float* loss_dev, sep_stream stream);
+/* Adam (0.9, 0.999, 1e-8) over n samples in a pseudo-random order; the
+ * last epoch's mean loss goes to *final_loss (may be NULL). Synchronises. */
+sep_status sep_surrogate_train(sep_model* model, const float* x_dev, const float* t_dev, int64_t n,
+                               const sep_train_cfg* cfg, float* final_loss, sep_stream stream);
+/* Attach a model to a CSR (NULL detaches). The CSR keeps the pointer, not a
+ * copy: the model must outlive its use, and later training of the model is
+ * seen by later launches. Calls with params->surrogate > 0 then start each
+ * bin from the model's prediction: with the first-pass mean m1 and deviation
+ * s1 of the bin, mu^ = m1 + s1 y0, sd^ = s1 exp(y1) (y de-normalised by the
+ * target block), candidate set I = {|v - mu^| <= k sd^}; one pass measures I
+ * and accepts it iff I is a fixed point of the clip map of Eq. 19, i.e.
+ * {|v - mu_I| <= k sd_I} == I; otherwise the next candidate is that set, up
+ * to params->surrogate passes, then the plain loop from the full set. A bin
+ * settled by the surrogate reports 0 iterations (iters_dev). */
+sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
+
+/* Plain clip (params->surrogate must be 0) that also records, per frame and
+ * bin, the surrogate's input features feat_dev [n_frames][nbins][SEP_MLP_IN]
+ * and its training targets target_dev [n_frames][nbins][2] =
+ * ((mu - m1) / s1, log(sd / s1)) of the clipped result (NaN where the bin has
+ * fewer than 2 entries in the final set or a zero deviation). Features:
+ * 0 log(n) / 8 (n entries of weight != 0), 1 Omega / n, 2 clamp(m1 / s1, -20,
+ * 20) / 4, 3 fraction with z = (v - m1) / s1 > 4, 4 .. 19 the quantiles
+ * (j + 1/2) / 16 of z from a 64-bin histogram over [-4, 12). */
+sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
+                                int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
+                                float* sigma_dev, int32_t* count_dev, float* feat_dev, float* target_dev,
+                                sep_stream stream);
+
+/* Training set from recorded rows: keeps the rows whose features and targets
+ * are finite (order preserved), computes the normalisation block over them
+ * (mean and population deviation of each feature and target; a deviation
+ * below 1e-6 becomes 1) into norm_host [SEP_MLP_NORM], and writes the kept
+ * rows normalised to x_dev [n_valid][20], t_dev [n_valid][2] (room for n
+ * rows each). Synchronises the stream. */
+sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const float* target_dev, int64_t n,
+                                 float* x_dev, float* t_dev, float* norm_host, int64_t* n_valid, sep_stream stream);
+
+/* Counters of bins settled by the surrogate and bins that fell back to the
+ * plain loop, summed over every call since the last reset. Synchronises. */
+sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
+                               sep_stream stream);
+
+/* Checkpoint: one JSON header line, then float32 parameters, normalisation,
+ * Adam moments. */
+sep_status sep_model_save(const sep_model* model, const char* path);
+sep_status sep_model_load(sep_ctx* ctx, const char* path, sep_model** out);
 
 /*
  * sep_sparsify with no allocation during the call (the paper has no

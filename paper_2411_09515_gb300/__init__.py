@@ -17,7 +17,7 @@ from . import _binding as B
 from ._binding import (PEAK_DTYPE, SEP_DTYPE_F32, SEP_DTYPE_U16_JF, SEP_PREC_DWORD, SEP_PREC_FP64MERGE,
                        SEP_PREC_KAHAN, SEP_PREC_PLAIN, SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM, SepError)
 
-__all__ = ["Context", "Separator", "process_mixed", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
+__all__ = ["Context", "Separator", "Surrogate", "process_mixed", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
            "SEP_PREC_PLAIN", "SEP_PREC_KAHAN", "SEP_PREC_FP64MERGE", "SEP_PREC_DWORD", "SEP_UNIT_2TH_DEG", "SEP_UNIT_Q_NM",
            "SEP_UNIT_R_MM"]
 
@@ -75,6 +75,7 @@ class Separator:
             self.calib = B.sep_calib_create(self.ctx, self.csr, calib[0], calib[1])
         self.params = B.make_params(n_iter, k_clip, k_pick, patch, min_count, precision)
         self._outs = {}
+        self.surrogate = None
 
     @classmethod
     def from_detector(cls, det, mask=None, **kw):
@@ -113,6 +114,35 @@ class Separator:
     def set_params(self, **kw):
         for k, v in kw.items():
             setattr(self.params, k, v)
+
+    # ---- learned surrogate of the clip loop ----
+    def attach_surrogate(self, model: "Surrogate | None", passes: int = 1):
+        """Start every bin's clip from the model's prediction, verified in at
+        most ``passes`` passes (plain loop where that fails); None detaches."""
+        B.sep_csr_attach_model(self.ctx, self.csr, model.model if model is not None else None)
+        self.surrogate = model
+        self.params.surrogate = passes if model is not None else 0
+
+    def record(self, frames, stream=None):
+        """Plain clip that also returns the surrogate's features [F][B][20]
+        and training targets [F][B][2] per bin."""
+        t = self.torch
+        F = self._check_frames(frames)
+        dev = frames.device
+        mean = t.empty((F, self.nbins), dtype=t.float32, device=dev)
+        sigma = t.empty_like(mean)
+        count = t.empty((F, self.nbins), dtype=t.int32, device=dev)
+        feat = t.empty((F, self.nbins, B.SEP_MLP_IN), dtype=t.float32, device=dev)
+        target = t.empty((F, self.nbins, B.SEP_MLP_OUT), dtype=t.float32, device=dev)
+        p = B.make_params(self.params.n_iter, self.params.k_clip, self.params.k_pick, self.params.patch,
+                          self.params.min_count, SEP_PREC_DWORD)
+        B.sep_surrogate_record(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, p, mean, sigma, count,
+                               feat, target, stream)
+        return {"mean": mean, "sigma": sigma, "count": count, "feat": feat, "target": target}
+
+    def surrogate_stats(self, reset=False, stream=None):
+        """(bins settled by the surrogate, bins that fell back) since the last reset."""
+        return B.sep_surrogate_stats(self.ctx, reset, stream)
 
     # ------------------------------------------------------------------
     def _dtype(self, frames):
@@ -208,6 +238,66 @@ class Separator:
 
     def device_status(self, stream=None):
         return B.sep_get_device_status(self.ctx, stream)
+
+
+class Surrogate:
+    """The clip surrogate's network (20 -> 64 -> 64 -> 2, GELU), trained on
+    the GPU by the library's own forward / backward / Adam kernels."""
+
+    def __init__(self, context, seed=0, path=None):
+        self.ctx = context.ctx if isinstance(context, Context) else context
+        self._context = context
+        self.model = B.sep_model_load(self.ctx, path) if path else B.sep_model_create(self.ctx, seed)
+
+    def close(self):
+        if getattr(self, "model", None) is not None:
+            B.sep_model_destroy(self.model)
+            self.model = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, set_host=None):
+        return B.sep_model_params(self.ctx, self.model, set_host)
+
+    def norm(self, set_host=None):
+        return B.sep_model_norm(self.ctx, self.model, set_host)
+
+    def save(self, path):
+        B.sep_model_save(self.ctx, self.model, path)
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty((x.shape[0], B.SEP_MLP_OUT), dtype=torch.float32, device=x.device)
+        B.sep_mlp_forward(self.ctx, self.model, x, x.shape[0], y, stream)
+        return y
+
+    def loss_grad(self, x, t, stream=None):
+        import torch
+        g = torch.empty(B.SEP_MLP_PARAMS, dtype=torch.float32, device=x.device)
+        l = torch.empty(1, dtype=torch.float32, device=x.device)
+        B.sep_mlp_loss_grad(self.ctx, self.model, x, t, x.shape[0], g, l, stream)
+        return l, g
+
+    def fit(self, feat, target, epochs=4, batch=4096, lr=2e-3, seed=0, stream=None):
+        """Train on recorded rows (feat [n][20], target [n][2], device):
+        keeps the finite rows, sets the normalisation, runs Adam. Returns
+        (last epoch's mean loss, rows used)."""
+        import torch
+        f = feat.reshape(-1, B.SEP_MLP_IN).contiguous()
+        t = target.reshape(-1, B.SEP_MLP_OUT).contiguous()
+        n = f.shape[0]
+        x = torch.empty_like(f)
+        y = torch.empty_like(t)
+        norm, nv = B.sep_surrogate_prepare(self.ctx, f, t, n, x, y, stream)
+        if nv == 0:
+            raise ValueError("no usable training rows")
+        self.norm(norm)
+        loss = B.sep_surrogate_train(self.ctx, self.model, x, y, nv, epochs, batch, lr, seed, stream)
+        return loss, nv
 
 
 def process_mixed(seps, frames, kept_capacity, peak_capacity, use_graph=True, stream=None):

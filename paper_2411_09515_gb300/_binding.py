@@ -29,7 +29,12 @@ STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OO
 EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error", "sep_get_device_status",
            "sep_build_csr", "sep_csr_destroy", "sep_csr_info", "sep_csr_export", "sep_calib_create",
            "sep_calib_destroy", "sep_integrate_clip", "sep_sparsify", "sep_peakfind", "sep_process_batch",
-           "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune", "sep_process_mixed"]
+           "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune", "sep_process_mixed",
+           "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
+           "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
+           "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats"]
+
+SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 
 
 class SepError(RuntimeError):
@@ -46,7 +51,13 @@ class sep_geometry(C.Structure):
 
 class sep_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
-                ("min_count", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("min_count", C.c_int32), ("precision", C.c_int32), ("surrogate", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+class sep_train_cfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("pad", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class sep_frame_desc(C.Structure):
@@ -100,9 +111,25 @@ def lib():
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
                                     _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
+    L.sep_model_create.argtypes = [_vp, C.c_uint64, C.POINTER(_vp)]
+    L.sep_model_destroy.argtypes = [_vp]
+    L.sep_model_destroy.restype = None
+    L.sep_model_params.argtypes = [_vp, _vp, _vp]
+    L.sep_model_norm.argtypes = [_vp, _vp, _vp]
+    L.sep_mlp_forward.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+    L.sep_mlp_loss_grad.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp]
+    L.sep_surrogate_train.argtypes = [_vp, _vp, _vp, C.c_int64, C.POINTER(sep_train_cfg), C.POINTER(C.c_float), _vp]
+    L.sep_model_save.argtypes = [_vp, C.c_char_p]
+    L.sep_model_load.argtypes = [_vp, C.c_char_p, C.POINTER(_vp)]
+    L.sep_csr_attach_model.argtypes = [_vp, _vp]
+    L.sep_surrogate_record.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp,
+                                       _vp, _vp, _vp, _vp]
+    L.sep_surrogate_prepare.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_int64), _vp]
+    L.sep_surrogate_stats.argtypes = [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int32, _vp]
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("sep_version", "sep_last_error", "sep_ctx_destroy", "sep_csr_destroy", "sep_calib_destroy"):
+        if name not in ("sep_version", "sep_last_error", "sep_ctx_destroy", "sep_csr_destroy", "sep_calib_destroy",
+                        "sep_model_destroy"):
             f.restype = C.c_int32
     _lib = L
     return L
@@ -168,9 +195,10 @@ def make_geometry(rows, cols, pixel_m, dist_m, center_px, wavelength_m, unit, nb
     return g
 
 
-def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD):
+def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD, surrogate=0):
     p = sep_params()
     p.n_iter, p.k_clip, p.k_pick, p.patch, p.min_count, p.precision = n_iter, k_clip, k_pick, patch, min_count, precision
+    p.surrogate = surrogate
     return p
 
 
@@ -295,3 +323,82 @@ def sep_process_batch(ctx, csr, calib, frames, dtype, n_frames, params, mean, si
     _check(ctx, lib().sep_process_batch(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
                                         _ptr(sigma), _ptr(count), _ptr(idx), _ptr(val), kept_capacity, _ptr(n_kept),
                                         _ptr(peaks), peak_capacity, _ptr(n_peaks), int(use_graph), _stream(stream)))
+
+
+# ---- surrogate ----
+
+def sep_model_create(ctx, seed=0):
+    h = _vp()
+    _check(ctx, lib().sep_model_create(ctx, seed, C.byref(h)))
+    return h
+
+
+def sep_model_destroy(model):
+    lib().sep_model_destroy(model)
+
+
+def sep_model_params(ctx, model, set_host=None):
+    """Returns the parameters (float32 [5634]); sets them first if set_host is given."""
+    out = np.zeros(SEP_MLP_PARAMS, np.float32)
+    src = None if set_host is None else np.ascontiguousarray(set_host, np.float32)
+    _check(ctx, lib().sep_model_params(model, _ptr(out), _ptr(src)))
+    return out
+
+
+def sep_model_norm(ctx, model, set_host=None):
+    out = np.zeros(SEP_MLP_NORM, np.float32)
+    src = None if set_host is None else np.ascontiguousarray(set_host, np.float32)
+    _check(ctx, lib().sep_model_norm(model, _ptr(out), _ptr(src)))
+    return out
+
+
+def sep_mlp_forward(ctx, model, x, n, y, stream=None):
+    _check(ctx, lib().sep_mlp_forward(model, _ptr(x), n, _ptr(y), _stream(stream)))
+
+
+def sep_mlp_loss_grad(ctx, model, x, t, n, grad, loss, stream=None):
+    _check(ctx, lib().sep_mlp_loss_grad(model, _ptr(x), _ptr(t), n, _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def sep_surrogate_train(ctx, model, x, t, n, epochs=4, batch=4096, lr=2e-3, seed=0, stream=None):
+    cfg = sep_train_cfg()
+    cfg.epochs, cfg.batch, cfg.lr, cfg.seed = epochs, batch, lr, seed
+    loss = C.c_float(0.0)
+    _check(ctx, lib().sep_surrogate_train(model, _ptr(x), _ptr(t), n, C.byref(cfg), C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def sep_model_save(ctx, model, path):
+    _check(ctx, lib().sep_model_save(model, os.fsencode(path)))
+
+
+def sep_model_load(ctx, path):
+    h = _vp()
+    _check(ctx, lib().sep_model_load(ctx, os.fsencode(path), C.byref(h)))
+    return h
+
+
+def sep_csr_attach_model(ctx, csr, model):
+    _check(ctx, lib().sep_csr_attach_model(csr, model))
+
+
+def sep_surrogate_record(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, count, feat, target,
+                         stream=None):
+    _check(ctx, lib().sep_surrogate_record(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params),
+                                           _ptr(mean), _ptr(sigma), _ptr(count), _ptr(feat), _ptr(target),
+                                           _stream(stream)))
+
+
+def sep_surrogate_prepare(ctx, feat, target, n, x, t, stream=None):
+    """Returns (normalisation block float32 [44], number of kept rows)."""
+    norm = np.zeros(SEP_MLP_NORM, np.float32)
+    nv = C.c_int64(0)
+    _check(ctx, lib().sep_surrogate_prepare(ctx, _ptr(feat), _ptr(target), n, _ptr(x), _ptr(t), _ptr(norm),
+                                            C.byref(nv), _stream(stream)))
+    return norm, nv.value
+
+
+def sep_surrogate_stats(ctx, reset=False, stream=None):
+    a, b = C.c_uint64(0), C.c_uint64(0)
+    _check(ctx, lib().sep_surrogate_stats(ctx, C.byref(a), C.byref(b), int(reset), _stream(stream)))
+    return a.value, b.value

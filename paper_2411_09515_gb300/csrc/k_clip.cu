@@ -37,6 +37,7 @@
 
 #include "sep_device.cuh"
 #include "sep_internal.h"
+#include "sep_mlp.cuh"
 
 namespace sep {
 namespace {
@@ -245,24 +246,198 @@ __device__ __forceinline__ void block_sum(float (&s)[NF], float (&c)[NF], uint32
   }
 }
 
-template <int DT, int MODE, int PREC, int kThreads>
-__global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
-  constexpr int kWarps = kThreads / 32;
-  constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
-  // Per pass, float sums and integer counts:
+template <int MODE>
+struct Sums {
+  // per pass, float sums and integer counts:
   //   MODE_UNIT:  (S1, S2) + count
   //   MODE_CLASS: (A1, B1, B2) + class counts packed 16 + 16 bits in two words
   //   MODE_ENTRY: (Omega, A1, OO, B1, B2) + count
   // (a row holds fewer than 2^16 entries: its values must fit shared memory)
-  constexpr int NF = MODE == MODE_UNIT ? 2 : (MODE == MODE_CLASS ? 3 : 5);
-  constexpr int NI = MODE == MODE_CLASS ? 2 : 1;
-  constexpr int NV = NF > 3 ? NF : 3;   // the first pass reduces 3 floats
+  static constexpr int NF = MODE == MODE_UNIT ? 2 : (MODE == MODE_CLASS ? 3 : 5);
+  static constexpr int NI = MODE == MODE_CLASS ? 2 : 1;
+};
+
+// Extremes around an interval [Ln, Hn] (over the entries of weight != 0):
+// x[0] = max below Ln, x[1] = min inside, x[2] = max inside, x[3] = min above Hn.
+struct Ext {
+  float x[4] = {-INFINITY, INFINITY, -INFINITY, INFINITY};
+  __device__ __forceinline__ void add(float v, float Ln, float Hn) {
+    if (v < Ln) x[0] = fmaxf(x[0], v);
+    else if (v > Hn) x[3] = fminf(x[3], v);
+    else if (v == v) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
+  }
+};
+
+// One pass: shifted sums about Kf over the entries of weight != 0 whose value
+// lies in [Ln, Hn], and (EXT) the extremes around the interval.
+template <int MODE, bool KAHAN, bool EXT, int kThreads>
+__device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts, const int (&ge)[4], float Ln,
+                                          float Hn, float Kf, Ext& ex, float (&ss)[Sums<MODE>::NF],
+                                          float (&cc)[Sums<MODE>::NF], uint32_t (&ci)[Sums<MODE>::NI]) {
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) ci[i] = 0u;
+  if (MODE == MODE_CLASS) {
+    int lo = 0;
+#pragma unroll
+    for (int cls = 0; cls < 4; ++cls) {
+      const int hi = ge[cls];
+      const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
+      uint32_t cnt = 0;
+      Acc<KAHAN> a1, a2;
+      for (int q = (lo >> 2) + tid; q < (hi >> 2); q += kThreads) {
+        const float4 v4 = vals4[q];
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (EXT) ex.add(xs[j], Ln, Hn);
+          if (xs[j] >= Ln && xs[j] <= Hn) {
+            const float d = __fsub_rn(xs[j], Kf);
+            ++cnt;
+            a1.add(d);
+            a2.add(__fmul_rn(d, d));
+          }
+        }
+      }
+      const float s1 = a1.val(), s2 = a2.val();
+      ci[cls >> 1] += cnt << (16 * (cls & 1));
+      if (KAHAN) {
+        Acc<true> t0, t1, t2;
+        t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
+        t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
+        t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
+      } else {
+        ss[0] = fmaf(w, s1, ss[0]);
+        ss[1] = fmaf(w2, s1, ss[1]);
+        ss[2] = fmaf(w2, s2, ss[2]);
+      }
+      lo = hi;
+    }
+  } else if (MODE == MODE_UNIT) {
+    uint32_t cnt = 0;
+    Acc<KAHAN> a1, a2;
+    for (int q = tid; q < (ge[0] >> 2); q += kThreads) {
+      const float4 v4 = vals4[q];
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (EXT) ex.add(xs[j], Ln, Hn);
+        if (xs[j] >= Ln && xs[j] <= Hn) {
+          const float d = __fsub_rn(xs[j], Kf);
+          ++cnt;
+          a1.add(d);
+          a2.add(__fmul_rn(d, d));
+        }
+      }
+    }
+    ci[0] = cnt;
+    ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
+  } else {
+    uint32_t cnt = 0;
+    Acc<KAHAN> om, a1, oo, b1, b2;
+    for (int q = tid; q < (ge[3] >> 2); q += kThreads) {
+      const float4 v4 = vals4[q];
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = wts[4 * q + j];
+        if (EXT && w != 0.0f) ex.add(xs[j], Ln, Hn);
+        if (w != 0.0f && xs[j] >= Ln && xs[j] <= Hn) {
+          const float d = __fsub_rn(xs[j], Kf);
+          const float w2 = __fmul_rn(w, w);
+          const float w2d = __fmul_rn(w2, d);
+          ++cnt;
+          om.add(w);
+          a1.add(__fmul_rn(w, d));
+          oo.add(w2);
+          b1.add(w2d);
+          b2.add(__fmul_rn(w2d, d));
+        }
+      }
+    }
+    ci[0] = cnt;
+    ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
+    ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
+  }
+}
+
+// Warp reduction of the extremes, one row per warp in red_x (read after the
+// barrier inside the following block_sum).
+template <int kWarps>
+__device__ __forceinline__ void warp_ext(Ext& ex, float (*red_x)[kWarps]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ex.x[0] = fmaxf(ex.x[0], __shfl_xor_sync(0xffffffffu, ex.x[0], o));
+    ex.x[1] = fminf(ex.x[1], __shfl_xor_sync(0xffffffffu, ex.x[1], o));
+    ex.x[2] = fmaxf(ex.x[2], __shfl_xor_sync(0xffffffffu, ex.x[2], o));
+    ex.x[3] = fminf(ex.x[3], __shfl_xor_sync(0xffffffffu, ex.x[3], o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) red_x[v][threadIdx.x >> 5] = ex.x[v];
+  }
+}
+
+// Lane 0 of warp 0: a pass's totals as (count, Omega, A1, OO, B1, B2) pairs.
+template <int MODE>
+__device__ __forceinline__ void unpack_totals(const float* th, const float* tl, float& n_set, float (&h)[6],
+                                              float (&l)[6]) {
+#pragma unroll
+  for (int v = 0; v < 6; ++v) h[v] = l[v] = 0.0f;
+  if (MODE == MODE_CLASS) {
+    // class counts are exact integers; their weighted sums are exact in FP32
+    const uint32_t p01 = __float_as_uint(th[3]), p23 = __float_as_uint(th[4]);
+    const float n0 = (float)(p01 & 0xffffu), n1 = (float)(p01 >> 16);
+    const float n2 = (float)(p23 & 0xffffu), n3 = (float)(p23 >> 16);
+    n_set = n0 + n1 + n2 + n3;
+    h[0] = n0 + 0.75f * n1 + 0.5f * n2 + 0.25f * n3;
+    h[2] = n0 + 0.5625f * n1 + 0.25f * n2 + 0.0625f * n3;
+    h[1] = th[0]; l[1] = tl[0];
+    h[3] = th[1]; l[3] = tl[1];
+    h[4] = th[2]; l[4] = tl[2];
+  } else if (MODE == MODE_UNIT) {
+    n_set = (float)__float_as_uint(th[2]);
+    h[0] = h[2] = n_set;
+    h[1] = h[3] = th[0]; l[1] = l[3] = tl[0];
+    h[4] = th[1]; l[4] = tl[1];
+  } else {
+    n_set = (float)__float_as_uint(th[5]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { h[v] = th[v]; l[v] = tl[v]; }
+  }
+}
+
+// Surrogate scratch in shared memory (per CTA).
+struct SurrShared {
+  uint32_t hist[64];     // z-histogram of the first-pass set, bins of 0.25 over [-4, 12)
+  float feat[kIn];       // the 20 features
+  float xn[kIn];         // normalised features
+  float h1[kH], h2[kH];  // hidden activations
+  float m1, s1, om, n;   // first-pass weighted mean, deviation, weight and count
+  int accepted;
+};
+
+// The surrogate variants hold the network's temporaries on top of the pass
+// state: cap their registers so that 1024 threads stay resident per SM.
+template <int DT, int MODE, int PREC, int kThreads, int SURR>
+__global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integrate_clip(ClipArgs a) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+  constexpr int NV = NF > 4 ? NF : 4;   // the gather reduces 4 floats
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* vals = reinterpret_cast<float*>(smem_raw);
   float* wts = vals + a.cap;   // MODE_ENTRY only: per-entry weight
   __shared__ float red_s[NV][kWarps], red_c[NV][kWarps];
   __shared__ uint32_t red_i[NI][kWarps];
   __shared__ Bcast st;
+  __shared__ SurrShared sv;
+  __shared__ float red_x[4][kWarps];
+  (void)sv;
+  (void)red_x;
 
   const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
   const int f0 = blockIdx.y * a.frames_per_cta;
@@ -286,6 +461,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
 
   for (int f = f0; f < f1; ++f) {
     const void* frame = a.fptr ? (const void*)a.fptr[f] : frame_ptr<DT>(a.frames, f, a.npix);
+    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
+    if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
     // ------------- gather + correct; rough sums giving the first shift -------------
     float s0[NV], c0[NV];
 #pragma unroll
@@ -303,7 +480,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       }
       const uint4* ents = reinterpret_cast<const uint4*>(vals);
-      float om = 0.0f, vv = 0.0f, v2 = 0.0f;
+      float om = 0.0f, vv = 0.0f, v2 = 0.0f, cn = 0.0f;
       // two vectors of 4 entries per step, every load issued before any use
       for (int qa = tid; qa < nq; qa += 2 * kThreads) {
         const int qs[2] = {qa, qa + kThreads};
@@ -360,7 +537,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
             if (MODE == MODE_ENTRY) x[j] = __fdiv_rn(x[j], __ldg(a.norm + col));
           }
           vals4[qs[h]] = make_float4(x[0], x[1], x[2], x[3]);
-          // rough sums (plain FP32): they only choose the first shift
+          // rough sums (plain FP32): the first shift, and the surrogate's first-pass statistics
           const int e0 = qs[h] << 2;
           if (e0 < ge[3]) {
             float w = 1.0f;
@@ -370,6 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
               if (MODE == MODE_ENTRY) w = wts[e0 + j];
               if (x[j] == x[j] && w != 0.0f) {
                 om += w;
+                cn += 1.0f;
                 const float wx = w * x[j];
                 vv += wx;
                 v2 = fmaf(wx, x[j], v2);
@@ -381,21 +559,24 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
       s0[0] = om;
       s0[1] = vv;
       s0[2] = v2;
+      s0[3] = cn;
     }
     {
       uint32_t none[1] = {0u};
       float thi, tlo;
       block_sum<NV, 1, SEP_PREC_PLAIN, kWarps>(s0, c0, none, red_s, red_c, red_i, thi, tlo);
-      // lanes 0, 1, 2 of warp 0 hold Omega, V, sum w v^2
+      // lanes 0..3 of warp 0 hold Omega, V, sum w v^2, count
       const float Om = __shfl_sync(0xffffffffu, thi, 0);
       const float V = __shfl_sync(0xffffffffu, thi, 1);
       const float V2 = __shfl_sync(0xffffffffu, thi, 2);
+      const float Cn = __shfl_sync(0xffffffffu, thi, 3);
       if (tid == 0) {
-        float K = 0.0f;
+        float K = 0.0f, m = 0.0f, sdev = 0.0f;
         if (Om > 0.0f) {
-          const float m = __fdiv_rn(V, Om);
+          m = __fdiv_rn(V, Om);
           const float var = __fsub_rn(__fdiv_rn(V2, Om), m * m);
-          K = choose_shift(m, var > 0.0f ? sqrtf(var) : 0.0f);
+          sdev = var > 0.0f ? sqrtf(var) : 0.0f;
+          K = choose_shift(m, sdev);
         }
         st.Kf = K;
         st.Ln = -FLT_MAX;
@@ -407,98 +588,187 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         st.done = 0;
         st.mu_hi = st.mu_lo = st.sd = 0.0f;
         st.mu_d = st.sd_d = 0.0;
+        if (SURR != 0) {
+          sv.m1 = m;
+          sv.s1 = sdev;
+          sv.om = Om;
+          sv.n = Cn;
+          sv.accepted = 0;
+        }
       }
       __syncthreads();   // values and state visible to all
     }
 
-    for (;;) {
-      // ------------- one pass: shifted sums over entries in [Ln, Hn] -------------
+    if (SURR != 0) {
+      // ------------- surrogate features: first-pass statistics + z quantiles -------------
+      const float m1 = sv.m1, inv = sv.s1 > 0.0f ? 1.0f / sv.s1 : 0.0f;
+      const int zend = MODE == MODE_UNIT ? ge[0] : ge[3];
+      for (int q = tid; q < (zend >> 2); q += kThreads) {
+        const float4 v4 = vals4[q];
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (!(xs[j] == xs[j])) continue;
+          if (MODE == MODE_ENTRY && wts[4 * q + j] == 0.0f) continue;
+          const float zb = fminf(fmaxf(__fmul_rn(__fsub_rn(xs[j], m1), inv) * 4.0f + 16.0f, 0.0f), 63.0f);
+          atomicAdd(&sv.hist[(int)zb], 1u);
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float tot = 0.0f;
+#pragma unroll 4
+        for (int hb = 0; hb < 64; ++hb) tot += (float)sv.hist[hb];
+        if (lane < 16) {
+          // quantile (lane + 1/2) / 16 of z, linear inside its histogram bin
+          const float target = ((float)lane + 0.5f) * (1.0f / 16.0f) * tot;
+          float cum = 0.0f, zq = 12.0f;
+#pragma unroll 1
+          for (int hb = 0; hb < 64; ++hb) {
+            const float c = (float)sv.hist[hb];
+            if (c > 0.0f && cum + c >= target) {
+              zq = -4.0f + 0.25f * ((float)hb + (target - cum) / c);
+              break;
+            }
+            cum += c;
+          }
+          sv.feat[4 + lane] = tot > 0.0f ? zq : 0.0f;
+        } else if (lane == 16) {
+          float hi_tail = 0.0f;
+#pragma unroll 4
+          for (int hb = 32; hb < 64; ++hb) hi_tail += (float)sv.hist[hb];
+          const float nn = sv.n > 0.0f ? sv.n : 1.0f;
+          sv.feat[0] = logf(nn) * 0.125f;
+          sv.feat[1] = sv.om / nn;
+          sv.feat[2] = sv.s1 > 0.0f ? fminf(fmaxf(sv.m1 / sv.s1, -20.0f), 20.0f) * 0.25f : 0.0f;
+          sv.feat[3] = tot > 0.0f ? hi_tail / tot : 0.0f;
+        }
+        if (SURR == 2) {
+          __syncwarp();
+          if (lane < kIn) sv.xn[lane] = (sv.feat[lane] - a.mlp_norm[lane]) / a.mlp_norm[kIn + lane];
+        }
+      }
+      __syncthreads();
+    }
+
+    if (SURR == 2) {
+      // ------------- predict (fused inference) -------------
+      const __nv_bfloat16* W = a.mlp_w;
+      for (int j = tid; j < kH; j += kThreads) {
+        float acc = __bfloat162float(W[kB1 + j]);
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) acc = fmaf(__bfloat162float(W[kW1 + j * kIn + k]), sv.xn[k], acc);
+        sv.h1[j] = gelu_f(acc);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < 4 * kH; idx += kThreads) {
+        const int j = idx >> 2, part = idx & 3;
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 16 * part; k < 16 * part + 16; ++k) acc = fmaf(__bfloat162float(W[kW2 + j * kH + k]), sv.h1[k], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0) sv.h2[j] = gelu_f(acc + __bfloat162float(W[kB2 + j]));
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float y0 = __bfloat162float(W[kW3 + lane]) * sv.h2[lane] + __bfloat162float(W[kW3 + lane + 32]) * sv.h2[lane + 32];
+        float y1 = __bfloat162float(W[kW3 + kH + lane]) * sv.h2[lane] +
+                   __bfloat162float(W[kW3 + kH + lane + 32]) * sv.h2[lane + 32];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          y0 += __shfl_xor_sync(0xffffffffu, y0, off);
+          y1 += __shfl_xor_sync(0xffffffffu, y1, off);
+        }
+        if (lane == 0) {
+          const float* nm = a.mlp_norm;
+          const float u0 = (y0 + __bfloat162float(W[kB3])) * nm[2 * kIn + 2] + nm[2 * kIn];
+          const float u1 = (y1 + __bfloat162float(W[kB3 + 1])) * nm[2 * kIn + 3] + nm[2 * kIn + 1];
+          const float mh = sv.m1 + sv.s1 * u0, sh = sv.s1 * expf(fminf(u1, 20.0f));
+          // candidate set I0 = {|v - mh| <= k sh}
+          st.Ln = mh - a.k_clip * sh;
+          st.Hn = mh + a.k_clip * sh;
+          st.Kf = choose_shift(mh, sh);
+          sv.accepted = 0;
+        }
+      }
+      __syncthreads();
+      // ------------- verify: one pass per candidate -------------
+      // Measure I = {v in [Ln, Hn]}: its moments give the next interval
+      // [L', H'] = mu_I -+ k sd_I (Eq. 19), and the extremes around [Ln, Hn]
+      // decide whether {v in [L', H']} == I without another pass: I is a fixed
+      // point of the clip map iff no entry lies between the two intervals.
+      for (int r = 0; r <= a.surr_refine; ++r) {
+        const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
+        float ss[NF], cc[NF];
+        uint32_t ci[NI];
+        Ext ex;
+        pass_sums<MODE, KAHAN, true, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
+        warp_ext<kWarps>(ex, red_x);
+        float thi, tlo;
+        block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
+        if (warp == 0) {
+          float th[NF + NI], tl[NF + NI];
+#pragma unroll
+          for (int v = 0; v < NF + NI; ++v) {
+            th[v] = __shfl_sync(0xffffffffu, thi, v);
+            tl[v] = __shfl_sync(0xffffffffu, tlo, v);
+          }
+          if (lane == 0) {
+            float n_set, h[6], l[6];
+            unpack_totals<MODE>(th, tl, n_set, h, l);
+            float e0 = -INFINITY, e1 = INFINITY, e2 = -INFINITY, e3 = INFINITY;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+              e0 = fmaxf(e0, red_x[0][w]);
+              e1 = fminf(e1, red_x[1][w]);
+              e2 = fmaxf(e2, red_x[2][w]);
+              e3 = fminf(e3, red_x[3][w]);
+            }
+            st.n_cur = n_set;
+            st.L = Ln;
+            st.H = Hn;
+            finalise<PREC>(Kf, h, l, st);
+            float L2 = -FLT_MAX, H2 = FLT_MAX;
+            clip_bounds<PREC>(st, a.k_clip, L2, H2);
+            if (n_set >= 2.0f && e0 < L2 && L2 <= e1 && e2 <= H2 && H2 < e3) {
+              sv.accepted = 1;
+            } else {
+              st.Ln = L2;
+              st.Hn = H2;
+              st.Kf = choose_shift(st.mu_hi, st.sd);
+            }
+          }
+        }
+        __syncthreads();
+        if (sv.accepted) break;
+      }
+      if (tid == 0) {
+        if (sv.accepted) {
+          st.steps = 0;   // marks a bin settled by the surrogate
+          st.done = 1;
+        } else {          // fall back to the plain iteration from the full set
+          st.Ln = -FLT_MAX;
+          st.Hn = FLT_MAX;
+          st.L = -FLT_MAX;
+          st.H = FLT_MAX;
+          st.Kf = choose_shift(sv.m1, sv.s1);
+          st.n_cur = -1.0f;
+          st.steps = -1;
+          st.done = 0;
+        }
+        if (a.surr_stats) atomicAdd(a.surr_stats + (sv.accepted ? 0 : 1), 1ull);
+      }
+      __syncthreads();
+    }
+
+    // ------------- the plain clip loop (Eq. 19, cumulative) -------------
+    while (!st.done) {
       const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
       float ss[NF], cc[NF];
       uint32_t ci[NI];
-#pragma unroll
-      for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
-#pragma unroll
-      for (int i = 0; i < NI; ++i) ci[i] = 0u;
-      if (MODE == MODE_CLASS) {
-        int lo = 0;
-#pragma unroll
-        for (int cls = 0; cls < 4; ++cls) {
-          const int hi = ge[cls];
-          const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
-          uint32_t cnt = 0;
-          Acc<KAHAN> a1, a2;
-          for (int q = (lo >> 2) + tid; q < (hi >> 2); q += kThreads) {
-            const float4 v4 = vals4[q];
-            const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (xs[j] >= Ln && xs[j] <= Hn) {
-                const float d = __fsub_rn(xs[j], Kf);
-                ++cnt;
-                a1.add(d);
-                a2.add(__fmul_rn(d, d));
-              }
-            }
-          }
-          const float s1 = a1.val(), s2 = a2.val();
-          ci[cls >> 1] += cnt << (16 * (cls & 1));
-          if (KAHAN) {
-            Acc<true> t0, t1, t2;
-            t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
-            t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
-            t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
-          } else {
-            ss[0] = fmaf(w, s1, ss[0]);
-            ss[1] = fmaf(w2, s1, ss[1]);
-            ss[2] = fmaf(w2, s2, ss[2]);
-          }
-          lo = hi;
-        }
-      } else if (MODE == MODE_UNIT) {
-        uint32_t cnt = 0;
-        Acc<KAHAN> a1, a2;
-        for (int q = tid; q < (ge[0] >> 2); q += kThreads) {
-          const float4 v4 = vals4[q];
-          const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (xs[j] >= Ln && xs[j] <= Hn) {
-              const float d = __fsub_rn(xs[j], Kf);
-              ++cnt;
-              a1.add(d);
-              a2.add(__fmul_rn(d, d));
-            }
-          }
-        }
-        ci[0] = cnt;
-        ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
-      } else {
-        uint32_t cnt = 0;
-        Acc<KAHAN> om, a1, oo, b1, b2;
-        for (int q = tid; q < (ge[3] >> 2); q += kThreads) {
-          const float4 v4 = vals4[q];
-          const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float w = wts[4 * q + j];
-            if (w != 0.0f && xs[j] >= Ln && xs[j] <= Hn) {
-              const float d = __fsub_rn(xs[j], Kf);
-              const float w2 = __fmul_rn(w, w);
-              const float w2d = __fmul_rn(w2, d);
-              ++cnt;
-              om.add(w);
-              a1.add(__fmul_rn(w, d));
-              oo.add(w2);
-              b1.add(w2d);
-              b2.add(__fmul_rn(w2d, d));
-            }
-          }
-        }
-        ci[0] = cnt;
-        ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
-        ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
-      }
+      Ext ex;
+      pass_sums<MODE, KAHAN, false, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
       float thi, tlo;
       block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
       if (warp == 0) {
@@ -509,30 +779,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
           tl[v] = __shfl_sync(0xffffffffu, tlo, v);
         }
         if (lane == 0) {
-          // sums of the measured set: 0 Omega, 1 A1, 2 OO, 3 B1, 4 B2 (pairs) and its size
-          float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
-          float n_set;
-          if (MODE == MODE_CLASS) {
-            // class counts (exact integers); their weighted sums are exact in FP32
-            const uint32_t p01 = __float_as_uint(th[3]), p23 = __float_as_uint(th[4]);
-            const float n0 = (float)(p01 & 0xffffu), n1 = (float)(p01 >> 16);
-            const float n2 = (float)(p23 & 0xffffu), n3 = (float)(p23 >> 16);
-            n_set = n0 + n1 + n2 + n3;
-            h[0] = n0 + 0.75f * n1 + 0.5f * n2 + 0.25f * n3;
-            h[2] = n0 + 0.5625f * n1 + 0.25f * n2 + 0.0625f * n3;
-            h[1] = th[0]; l[1] = tl[0];
-            h[3] = th[1]; l[3] = tl[1];
-            h[4] = th[2]; l[4] = tl[2];
-          } else if (MODE == MODE_UNIT) {
-            n_set = (float)__float_as_uint(th[2]);
-            h[0] = h[2] = n_set;
-            h[1] = h[3] = th[0]; l[1] = l[3] = tl[0];
-            h[4] = th[1]; l[4] = tl[1];
-          } else {
-            n_set = (float)__float_as_uint(th[5]);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) { h[v] = th[v]; l[v] = tl[v]; }
-          }
+          float n_set, h[6], l[6];
+          unpack_totals<MODE>(th, tl, n_set, h, l);
           // the pass measured S' = S ∩ [Ln, Hn]; S' == S means nothing was discarded
           if (st.steps >= 0 && n_set == st.n_cur) {
             st.done = 1;
@@ -555,9 +803,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         }
       }
       __syncthreads();
-      if (st.done) break;
     }
-    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (tid == 0) {
       a.mean[o] = st.mu_hi;
       a.sigma[o] = st.sd;
@@ -567,6 +813,13 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
         a.bounds[2 * o + 1] = st.H;
       }
       if (a.iters) a.iters[o] = st.steps;
+      if (SURR == 1) {
+        // training record: features and the plain result as normalised targets
+        for (int k = 0; k < kIn; ++k) a.rec_feat[o * kIn + k] = sv.feat[k];
+        const bool ok = sv.s1 > 0.0f && st.sd > 0.0f && st.n_cur >= 2.0f;
+        a.rec_target[o * 2] = ok ? (st.mu_hi - sv.m1) / sv.s1 : __int_as_float(0x7fc00000);
+        a.rec_target[o * 2 + 1] = ok ? logf(st.sd / sv.s1) : __int_as_float(0x7fc00000);
+      }
     }
     // ---------------- sparsification mark (Section 3) ----------------
     if (a.bitmap) {
@@ -596,10 +849,10 @@ __global__ void __launch_bounds__(kThreads) k_integrate_clip(ClipArgs a) {
 
 // mode 0: set the shared-memory attribute and launch; 1: attribute only
 // (done eagerly before a stream capture); 2: launch only.
-template <int DT, int MODE, int PREC, int TPB>
+template <int DT, int MODE, int PREC, int TPB, int SURR>
 cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
   const size_t smem = clip_smem_bytes(a.cap, MODE == MODE_ENTRY);
-  auto k = k_integrate_clip<DT, MODE, PREC, TPB>;
+  auto k = k_integrate_clip<DT, MODE, PREC, TPB, SURR>;
   if (mode != 2) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess || mode == 1) return e;
@@ -609,22 +862,25 @@ cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int DT, int MODE, int PREC>
+template <int DT, int MODE, int PREC, int SURR>
 cudaError_t launch_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
   switch (tpb) {
-    case 64: return launch_t<DT, MODE, PREC, 64>(a, n_ctas, mode, s);
-    case 128: return launch_t<DT, MODE, PREC, 128>(a, n_ctas, mode, s);
-    default: return launch_t<DT, MODE, PREC, 256>(a, n_ctas, mode, s);
+    case 64: return launch_t<DT, MODE, PREC, 64, SURR>(a, n_ctas, mode, s);
+    case 128: return launch_t<DT, MODE, PREC, 128, SURR>(a, n_ctas, mode, s);
+    default: return launch_t<DT, MODE, PREC, 256, SURR>(a, n_ctas, mode, s);
   }
 }
 
 template <int DT, int MODE>
 cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
+  // the surrogate modes exist for the default precision only
+  if (a.rec_feat) return launch_b<DT, MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
+  if (a.mlp_w) return launch_b<DT, MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
   switch (prec) {
-    case SEP_PREC_PLAIN: return launch_b<DT, MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_KAHAN: return launch_b<DT, MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_FP64MERGE: return launch_b<DT, MODE, SEP_PREC_FP64MERGE>(a, n_ctas, tpb, mode, s);
-    default: return launch_b<DT, MODE, SEP_PREC_DWORD>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_PLAIN: return launch_b<DT, MODE, SEP_PREC_PLAIN, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_KAHAN: return launch_b<DT, MODE, SEP_PREC_KAHAN, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_FP64MERGE: return launch_b<DT, MODE, SEP_PREC_FP64MERGE, 0>(a, n_ctas, tpb, mode, s);
+    default: return launch_b<DT, MODE, SEP_PREC_DWORD, 0>(a, n_ctas, tpb, mode, s);
   }
 }
 

@@ -86,7 +86,10 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
   if (p->patch < 1 || p->patch > 15 || (p->patch & 1) == 0) return fail(ctx, SEP_ERR_ARG, "patch must be odd in [1, 15]");
   if (p->min_count < 1) return fail(ctx, SEP_ERR_ARG, "min_count must be >= 1");
   if (p->precision < SEP_PREC_PLAIN || p->precision > SEP_PREC_DWORD) return fail(ctx, SEP_ERR_ARG, "unknown precision");
-  for (int i = 0; i < 4; ++i)
+  if (p->surrogate < 0 || p->surrogate > 8) return fail(ctx, SEP_ERR_ARG, "surrogate must be in [0, 8]");
+  if (p->surrogate > 0 && p->precision != SEP_PREC_DWORD)
+    return fail(ctx, SEP_ERR_ARG, "the surrogate runs in precision SEP_PREC_DWORD only");
+  for (int i = 0; i < 3; ++i)
     if (p->reserved[i] != 0) return fail(ctx, SEP_ERR_ARG, "reserved params must be 0");
   return SEP_OK;
 }
@@ -107,6 +110,8 @@ sep_status check_common(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   }
   sep_status st = check_params(ctx, params);
   if (st != SEP_OK) return st;
+  if (params->surrogate > 0 && !csr->model) return fail(ctx, SEP_ERR_STATE, "surrogate requested but no model attached");
+  if (params->surrogate > 0 && csr->model->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "model belongs to another context");
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
   return SEP_OK;
 }
@@ -216,6 +221,12 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   a.iters = iters;
   a.bitmap = bitmap;
   a.words = words;
+  if (pr->surrogate > 0 && csr->model) {
+    a.mlp_w = csr->model->d_wbf;
+    a.mlp_norm = csr->model->d_norm;
+    a.surr_stats = ctx->d_surr;
+    a.surr_refine = pr->surrogate - 1;
+  }
   return a;
 }
 
@@ -276,11 +287,14 @@ sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_surr, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_surr, 0, 2 * sizeof(unsigned long long));
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_surr) cudaFree(c->d_surr);
     delete c;
     return SEP_ERR_CUDA;
   }
@@ -296,6 +310,7 @@ void sep_ctx_destroy(sep_ctx* ctx) {
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_surr) cudaFree(ctx->d_surr);
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
@@ -479,6 +494,48 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
   return SEP_OK;
 }
 
+sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
+                                int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
+                                float* sigma_dev, int32_t* count_dev, float* feat_dev, float* target_dev,
+                                sep_stream stream) {
+  sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
+  if (st != SEP_OK) return st;
+  if (params->surrogate != 0) return fail(ctx, SEP_ERR_ARG, "recording runs the plain loop: surrogate must be 0");
+  if (params->precision != SEP_PREC_DWORD) return fail(ctx, SEP_ERR_ARG, "recording runs in SEP_PREC_DWORD only");
+  if (n_frames > 0 && (!mean_dev || !sigma_dev || !count_dev || !feat_dev || !target_dev))
+    return fail(ctx, SEP_ERR_ARG, "NULL output");
+  if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
+  if (n_frames == 0) return SEP_OK;
+  sep::ClipArgs a = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
+                              nullptr, nullptr, nullptr, 0);
+  a.rec_feat = feat_dev;
+  a.rec_target = target_dev;
+  cudaError_t e = enqueue_clip(ctx, csr, a, dtype, params->precision, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate_record launch");
+  return SEP_OK;
+}
+
+sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
+                               sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  unsigned long long v[2] = {0, 0};
+  cudaStream_t s = (cudaStream_t)stream;
+  SEP_CUDA(ctx, cudaMemcpyAsync(v, ctx->d_surr, sizeof v, cudaMemcpyDeviceToHost, s));
+  if (reset) SEP_CUDA(ctx, cudaMemsetAsync(ctx->d_surr, 0, sizeof v, s));
+  SEP_CUDA(ctx, cudaStreamSynchronize(s));
+  if (accepted) *accepted = v[0];
+  if (fell_back) *fell_back = v[1];
+  return SEP_OK;
+}
+
+sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model) {
+  if (!csr) return SEP_ERR_ARG;
+  if (model && model->ctx != csr->ctx) return fail(csr->ctx, SEP_ERR_STATE, "model belongs to another context");
+  csr->model = model;
+  return SEP_OK;
+}
+
 sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                         int32_t dtype, int32_t n_frames, const sep_params* params, const float* mean_dev,
                         const float* sigma_dev, int32_t* idx_dev, float* val_dev, int64_t capacity,
@@ -583,7 +640,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev,
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
                                (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
-                               (uint64_t)(uintptr_t)s, csr->plan_version};
+                               (uint64_t)(uintptr_t)s, csr->plan_version, (uint64_t)(uintptr_t)csr->model};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));
@@ -762,6 +819,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
   for (int d = 0; d < n_det; ++d) {
     if (!csrs[d] || csrs[d]->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr missing or from another context");
     if ((st = check_bin_fits(ctx, csrs[d])) != SEP_OK) return st;
+    if (params->surrogate > 0 && (!csrs[d]->model || csrs[d]->model->ctx != ctx))
+      return fail(ctx, SEP_ERR_STATE, "surrogate requested but a detector has no model of this context");
   }
   std::vector<std::vector<int32_t>> members(n_det);
   std::vector<int64_t> rows((size_t)n_frames + 1, 0);

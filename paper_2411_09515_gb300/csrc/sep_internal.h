@@ -1,6 +1,7 @@
 // Internal declarations of libsep (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,13 @@ struct ClipArgs {
   // (in bins) of its profile; null = contiguous frames, rows f * nbins
   const uint64_t* fptr = nullptr;
   const int64_t* orow = nullptr;
+  // surrogate: record features + targets (training data), or predict + verify
+  float* rec_feat = nullptr;           // [rows][20]
+  float* rec_target = nullptr;         // [rows][2]
+  const __nv_bfloat16* mlp_w = nullptr;
+  const float* mlp_norm = nullptr;
+  unsigned long long* surr_stats = nullptr;   // [2]: bins settled by the surrogate, bins that fell back
+  int32_t surr_refine = 0;             // verification passes after the first
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
@@ -139,6 +147,7 @@ struct sep_ctx {
   int64_t* d_desc = nullptr;   // mixed batches: per-frame descriptor table
   int64_t* h_desc = nullptr;   // its pinned staging copy
   size_t desc_len = 0;
+  unsigned long long* d_surr = nullptr;   // surrogate counters: settled, fell back
   // captured batches, keyed by every launch argument
   std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
   uint64_t use_clock = 0;
@@ -167,6 +176,20 @@ struct sep_csr {
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
+  const sep_model* model = nullptr;   // surrogate attached by sep_csr_attach_model
+};
+
+struct sep_model {
+  sep_ctx* ctx = nullptr;
+  float* d_params = nullptr;      // FP32 master parameters
+  __nv_bfloat16* d_wbf = nullptr; // BF16 copy read by every forward / backward
+  float* d_m = nullptr;           // Adam moments
+  float* d_v = nullptr;
+  float* d_grad = nullptr;
+  float* d_loss = nullptr;
+  float* d_norm = nullptr;        // feature / target normalisation (device copy)
+  float norm[SEP_MLP_NORM] = {};
+  int64_t step = 0;
 };
 
 struct sep_calib {
