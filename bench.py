@@ -141,6 +141,14 @@ def run_ours(args):
     dev = host.to(f"cuda:{local}", non_blocking=False)
     out = sep.alloc_outputs(F, kcap, pcap)
     stream = torch.cuda.current_stream()
+    tune_ms = None
+    if not args.no_autotune:
+        # the library's autotuner picks the clip schedule on a sample of the batch
+        tune_ms = sep.autotune(dev[: min(F, 128)], stream=stream)
+    plan = sep.get_plan()
+    # launches of our kernels per step: one clip launch per size class of
+    # the schedule, two for the compaction, two for the peaks
+    launches_per_step = max(len(plan["tpb"]), 1) + 4
 
     def step():
         sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)
@@ -210,6 +218,11 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # the learned surrogate against the plain loop on the same batch
+    sur = None
+    if args.surrogate_train_frames > 0:
+        sur = surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args)
+
     # oracle on the host cores, rank 0 at N = 1 only
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -228,7 +241,8 @@ def run_ours(args):
             "data": "synthetic (seeded Jungfrau-4M-shaped raw frames; no dataset)",
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "nnz": info["nnz"], "max_row": info["max_row"],
                        "l2": "inputs larger than L2 (4.58 GB/batch), no flush", "parallelism": f"replicas x{world}",
-                       "kept_capacity": kcap, "peak_capacity": pcap, "precision": args.precision},
+                       "kept_capacity": kcap, "peak_capacity": pcap, "precision": args.precision,
+                       "clip_schedule": plan, "autotune_sample_ms": tune_ms},
             "roofline": {"bound": "hbm", "kernel": "k_integrate_clip", "achieved": round(achieved, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": None,
@@ -236,9 +250,10 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg},
             "e2e": {"value": round(F * args.steps * world / (e2e_ms * 1e-3), 2), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "surrogate": sur,
             "device_status": status,
             "mean_kept_per_frame": float(n_kept.mean()), "mean_peaks_per_frame": float(n_peaks.mean()),
             "setup_s": round(t_gen, 1),
@@ -246,6 +261,64 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
+    """Train the clip surrogate on frames of another seed range (recorded by
+    the plain clip on the GPU, trained by the library's kernels), then time
+    the whole path with it against the plain path on the bench batch."""
+    import torch
+    import synth
+    from paper_2411_09515_gb300 import Surrogate
+    F = dev.shape[0]
+    spec = synth.spec_jf_serial(7777)
+    t0 = time.time()
+    feats, tgts = [], []
+    for i in range(0, args.surrogate_train_frames, 64):
+        n = min(64, args.surrogate_train_frames - i)
+        tr, _, _ = synth.frames(det, spec, 1_000_000 + i, n, calib=cal, mask=mask)
+        r = sep.record(torch.from_numpy(tr.view(np.int16)).cuda(dev.device), stream=stream)
+        feats.append(r["feat"])
+        tgts.append(r["target"])
+    model = Surrogate(sep.ctx, seed=1)
+    loss, rows = model.fit(torch.cat(feats), torch.cat(tgts), epochs=24, batch=1024, lr=2e-3, stream=stream)
+    t_train = time.time() - t0
+    del feats, tgts
+
+    def timed(steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    sep.attach_surrogate(None)
+    timed(2)
+    plain_ms = timed(args.steps)
+    plain = {k: out[k].clone() for k in ("idx", "n_kept", "count")}
+    res = {"train_frames": args.surrogate_train_frames, "train_rows": rows, "train_loss": round(loss, 5),
+           "train_s": round(t_train, 1), "plain_fps": round(F / (plain_ms * 1e-3), 2)}
+    for passes in (1, 2):
+        sep.attach_surrogate(model, passes=passes)
+        timed(2)
+        sep.surrogate_stats(reset=True, stream=stream)
+        ms = timed(args.steps)
+        acc, fb = sep.surrogate_stats(reset=True, stream=stream)
+        same = 0
+        for f in range(F):
+            n = int(plain["n_kept"][f])
+            if int(out["n_kept"][f]) == n and torch.equal(out["idx"][f, :n], plain["idx"][f, :n]):
+                same += 1
+        res[f"passes{passes}"] = {
+            "fps": round(F / (ms * 1e-3), 2), "settled_frac": round(acc / max(acc + fb, 1), 4),
+            "bins_same_count_frac": round(float((out["count"] == plain["count"]).float().mean().item()), 4),
+            "frames_identical_kept": round(same / F, 4)}
+    sep.attach_surrogate(None)
+    model.close()
+    return res
 
 
 def cpu_baseline(det, mask, cal, frames_np, n):
@@ -365,6 +438,8 @@ def main():
     ap.add_argument("--peak-capacity", type=int, default=8192)
     ap.add_argument("--cpu-frames", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--surrogate-train-frames", type=int, default=256)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge", "dword"], default="dword")
     ap.add_argument("--workload", choices=["jf4m", "mixed"], default="jf4m")

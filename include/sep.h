@@ -350,15 +350,18 @@ sep_status sep_surrogate_train(sep_model* model, const float* x_dev, const float
  * target block), candidate set I = {|v - mu^| <= k sd^}; one pass measures I
  * and accepts it iff I is a fixed point of the clip map of Eq. 19, i.e.
  * {|v - mu_I| <= k sd_I} == I; otherwise the next candidate is that set, up
- * to params->surrogate passes, then the plain loop from the full set. A bin
- * settled by the surrogate reports 0 iterations (iters_dev). */
+ * to params->surrogate passes, then the plain loop (bit-identical to a call
+ * without the surrogate). A bin settled by the surrogate reports -1
+ * iterations (iters_dev); bins that the first pass settles alone skip the
+ * surrogate. */
 sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
 
 /* Plain clip (params->surrogate must be 0) that also records, per frame and
  * bin, the surrogate's input features feat_dev [n_frames][nbins][SEP_MLP_IN]
  * and its training targets target_dev [n_frames][nbins][2] =
  * ((mu - m1) / s1, log(sd / s1)) of the clipped result (NaN where the bin has
- * fewer than 2 entries in the final set or a zero deviation). Features:
+ * fewer than 2 entries in the final set or a zero deviation); m1 and s1 are
+ * the mean and deviation (Eqs. 12-13) of the full set. Features:
  * 0 log(n) / 8 (n entries of weight != 0), 1 Omega / n, 2 clamp(m1 / s1, -20,
  * 20) / 4, 3 fraction with z = (v - m1) / s1 > 4, 4 .. 19 the quantiles
  * (j + 1/2) / 16 of z from a 64-bin histogram over [-4, 12). */
@@ -376,8 +379,9 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
 sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const float* target_dev, int64_t n,
                                  float* x_dev, float* t_dev, float* norm_host, int64_t* n_valid, sep_stream stream);
 
-/* Counters of bins settled by the surrogate and bins that fell back to the
- * plain loop, summed over every call since the last reset. Synchronises. */
+/* Of the bins the surrogate ran on: how many it settled and how many fell
+ * back to the plain loop, summed over every call since the last reset.
+ * Synchronises. */
 sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
                                sep_stream stream);
 

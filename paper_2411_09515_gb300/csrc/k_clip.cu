@@ -257,22 +257,28 @@ struct Sums {
   static constexpr int NI = MODE == MODE_CLASS ? 2 : 1;
 };
 
-// Extremes around an interval [Ln, Hn] (over the entries of weight != 0):
+// Extremes around an interval [Ln, Hn] over the entries of weight != 0:
 // x[0] = max below Ln, x[1] = min inside, x[2] = max inside, x[3] = min above Hn.
+// EXT 1 tracks the two inside the interval only, EXT 2 all four.
+template <int EXT>
 struct Ext {
   float x[4] = {-INFINITY, INFINITY, -INFINITY, INFINITY};
   __device__ __forceinline__ void add(float v, float Ln, float Hn) {
-    if (v < Ln) x[0] = fmaxf(x[0], v);
-    else if (v > Hn) x[3] = fminf(x[3], v);
-    else if (v == v) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
+    if (EXT == 1) {
+      if (v >= Ln && v <= Hn) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
+    } else if (EXT == 2) {
+      if (v < Ln) x[0] = fmaxf(x[0], v);
+      else if (v > Hn) x[3] = fminf(x[3], v);
+      else if (v == v) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
+    }
   }
 };
 
 // One pass: shifted sums about Kf over the entries of weight != 0 whose value
-// lies in [Ln, Hn], and (EXT) the extremes around the interval.
-template <int MODE, bool KAHAN, bool EXT, int kThreads>
+// lies in [Ln, Hn], and the extremes around the interval (Ext).
+template <int MODE, bool KAHAN, int EXT, int kThreads>
 __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts, const int (&ge)[4], float Ln,
-                                          float Hn, float Kf, Ext& ex, float (&ss)[Sums<MODE>::NF],
+                                          float Hn, float Kf, Ext<EXT>& ex, float (&ss)[Sums<MODE>::NF],
                                           float (&cc)[Sums<MODE>::NF], uint32_t (&ci)[Sums<MODE>::NI]) {
   constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
   const int tid = threadIdx.x;
@@ -366,19 +372,68 @@ __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts,
 
 // Warp reduction of the extremes, one row per warp in red_x (read after the
 // barrier inside the following block_sum).
-template <int kWarps>
-__device__ __forceinline__ void warp_ext(Ext& ex, float (*red_x)[kWarps]) {
+template <int EXT, int kWarps>
+__device__ __forceinline__ void warp_ext(Ext<EXT>& ex, float (*red_x)[kWarps]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ex.x[0] = fmaxf(ex.x[0], __shfl_xor_sync(0xffffffffu, ex.x[0], o));
+    if (EXT == 2) ex.x[0] = fmaxf(ex.x[0], __shfl_xor_sync(0xffffffffu, ex.x[0], o));
     ex.x[1] = fminf(ex.x[1], __shfl_xor_sync(0xffffffffu, ex.x[1], o));
     ex.x[2] = fmaxf(ex.x[2], __shfl_xor_sync(0xffffffffu, ex.x[2], o));
-    ex.x[3] = fminf(ex.x[3], __shfl_xor_sync(0xffffffffu, ex.x[3], o));
+    if (EXT == 2) ex.x[3] = fminf(ex.x[3], __shfl_xor_sync(0xffffffffu, ex.x[3], o));
   }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) red_x[v][threadIdx.x >> 5] = ex.x[v];
   }
+}
+
+// Lane 0 of warp 0: the extremes over the CTA.
+template <int kWarps>
+__device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)[4]) {
+  e[0] = -INFINITY; e[1] = INFINITY; e[2] = -INFINITY; e[3] = INFINITY;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    e[0] = fmaxf(e[0], red_x[0][w]);
+    e[1] = fminf(e[1], red_x[1][w]);
+    e[2] = fmaxf(e[2], red_x[2][w]);
+    e[3] = fminf(e[3], red_x[3][w]);
+  }
+}
+
+// One step of the clip loop (lane 0 of warp 0) after a pass measured the set
+// S' = S ∩ [Ln, Hn] (count n_set, sums h/l about Kf, smallest and largest
+// member e_lo, e_hi). S' == S means nothing was discarded: the loop ends
+// with the moments of S. Otherwise S' becomes the set, its moments are
+// evaluated and the next interval is the intersection with
+// [mu - k sd, mu + k sd] (Eq. 19, cumulative); when every member of S' lies
+// inside it, the next pass would discard nothing and the loop ends here.
+// (have_moments: st already holds the moments of S'.)
+template <int PREC>
+__device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&h)[6], const float (&l)[6],
+                                          float e_lo, float e_hi, float Kf, float Ln, float Hn, int n_iter,
+                                          float k, bool have_moments = false) {
+  if (st.steps >= 0 && n_set == st.n_cur) {
+    st.done = 1;
+    return;
+  }
+  st.n_cur = n_set;
+  st.L = Ln;
+  st.H = Hn;
+  if (!have_moments) finalise<PREC>(Kf, h, l, st);
+  st.steps += 1;
+  if (st.steps >= n_iter) {
+    st.done = 1;
+    return;
+  }
+  float L2 = Ln, H2 = Hn;
+  clip_bounds<PREC>(st, k, L2, H2);
+  if (e_lo >= L2 && e_hi <= H2) {
+    st.done = 1;
+    return;
+  }
+  st.Ln = L2;
+  st.Hn = H2;
+  st.Kf = choose_shift(st.mu_hi, st.sd);
 }
 
 // Lane 0 of warp 0: a pass's totals as (count, Omega, A1, OO, B1, B2) pairs.
@@ -420,24 +475,109 @@ struct SurrShared {
   int accepted;
 };
 
-// The surrogate variants hold the network's temporaries on top of the pass
-// state: cap their registers so that 1024 threads stay resident per SM.
+// Per-thread sums of the first pass (the full set, shift 0), accumulated
+// while the values are gathered, in the order and layout of pass_sums.
+template <int MODE, bool KAHAN>
+struct FirstPass {
+  static constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+  float ss[NF], cc[NF];
+  uint32_t ci[NI];
+  Ext<1> ex;
+  int cur = 0;            // MODE_CLASS: class of the entries being accumulated
+  uint32_t cnt = 0;
+  Acc<KAHAN> a1, a2;      // MODE_CLASS / MODE_UNIT
+  Acc<KAHAN> om, oo, b1;  // MODE_ENTRY (a1 = sum w d, a2 = sum w^2 d^2)
+  __device__ __forceinline__ FirstPass() {
+#pragma unroll
+    for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) ci[i] = 0u;
+  }
+  // add the current class (weight w = 1 - cur / 4) to the totals
+  __device__ __forceinline__ void flush_class() {
+    const float w = 1.0f - 0.25f * (float)cur, w2 = w * w;
+    const float s1 = a1.val(), s2 = a2.val();
+    if (cur >> 1) ci[1] += cnt << (16 * (cur & 1));
+    else ci[0] += cnt << (16 * (cur & 1));
+    if (KAHAN) {
+      Acc<true> t0, t1, t2;
+      t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
+      t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
+      t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
+    } else {
+      ss[0] = fmaf(w, s1, ss[0]);
+      ss[1] = fmaf(w2, s1, ss[1]);
+      ss[2] = fmaf(w2, s2, ss[2]);
+    }
+    cnt = 0;
+    a1 = Acc<KAHAN>();
+    a2 = Acc<KAHAN>();
+  }
+  // the value of entry e (each thread's entries ascend)
+  __device__ __forceinline__ void add1(float v, int e, const int (&ge)[4], const float* wts) {
+    if (MODE == MODE_CLASS) {
+      while (cur < 4 && e >= ge[cur]) {
+        flush_class();
+        ++cur;
+      }
+      if (cur >= 4) return;   // weight-0 carriers
+    } else if (MODE == MODE_UNIT) {
+      if (e >= ge[0]) return;
+    }
+    if (MODE == MODE_ENTRY) {
+      const float w = wts[e];
+      if (w != 0.0f && v >= -FLT_MAX && v <= FLT_MAX) {
+        const float w2 = __fmul_rn(w, w);
+        const float w2d = __fmul_rn(w2, v);
+        ++cnt;
+        om.add(w);
+        a1.add(__fmul_rn(w, v));
+        oo.add(w2);
+        b1.add(w2d);
+        a2.add(__fmul_rn(w2d, v));
+        ex.add(v, -FLT_MAX, FLT_MAX);
+      }
+    } else if (v >= -FLT_MAX && v <= FLT_MAX) {
+      ++cnt;
+      a1.add(v);
+      a2.add(__fmul_rn(v, v));
+      ex.add(v, -FLT_MAX, FLT_MAX);
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    if (MODE == MODE_CLASS) {
+      while (cur < 4) {
+        flush_class();
+        ++cur;
+      }
+    } else if (MODE == MODE_UNIT) {
+      ci[0] = cnt;
+      ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
+    } else {
+      ci[0] = cnt;
+      ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
+      ss[3] = b1.s; cc[3] = b1.c; ss[4] = a2.s; cc[4] = a2.c;
+    }
+  }
+};
+
+// Registers are capped so that 1024 threads stay resident per SM (the
+// serial step of one CTA overlaps the passes of the others).
 template <int DT, int MODE, int PREC, int kThreads, int SURR>
-__global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integrate_clip(ClipArgs a) {
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(ClipArgs a) {
   constexpr int kWarps = kThreads / 32;
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
   constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
-  constexpr int NV = NF > 4 ? NF : 4;   // the gather reduces 4 floats
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* vals = reinterpret_cast<float*>(smem_raw);
   float* wts = vals + a.cap;   // MODE_ENTRY only: per-entry weight
-  __shared__ float red_s[NV][kWarps], red_c[NV][kWarps];
+  __shared__ float red_s[NF][kWarps], red_c[NF][kWarps];
   __shared__ uint32_t red_i[NI][kWarps];
-  __shared__ Bcast st;
-  __shared__ SurrShared sv;
   __shared__ float red_x[4][kWarps];
+  __shared__ Bcast st, st0;   // st0: the state after the first pass (surrogate fallback)
+  __shared__ SurrShared sv;
   (void)sv;
-  (void)red_x;
+  (void)st0;
 
   const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
   const int f0 = blockIdx.y * a.frames_per_cta;
@@ -463,15 +603,15 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
     const void* frame = a.fptr ? (const void*)a.fptr[f] : frame_ptr<DT>(a.frames, f, a.npix);
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
-    // ------------- gather + correct; rough sums giving the first shift -------------
-    float s0[NV], c0[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) s0[v] = c0[v] = 0.0f;
+    // ------------- gather + correct, with the first pass (full set, shift 0) -------------
+    FirstPass<MODE, KAHAN> fp;
     {
       // Stage the row's packed entries into the value slots (16-byte
-      // cp.async copies); each thread later reads only the slots it staged,
-      // so its own wait_group is the only synchronisation needed. The
-      // gathers then depend on a shared-memory read, not on a global load.
+      // cp.async copies), then gather with consecutive threads on
+      // consecutive entries: entries ascend in pixel index along the
+      // ring's arcs, so a warp's loads of raw words fall on few sectors.
+      // Slot e is read (entry) and then written (value) by the same thread
+      // only, so one barrier after the staging suffices.
       {
         const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
         for (int q = tid; q < nq; q += kThreads)
@@ -479,127 +619,105 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
                        : "memory");
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       }
-      const uint4* ents = reinterpret_cast<const uint4*>(vals);
-      float om = 0.0f, vv = 0.0f, v2 = 0.0f, cn = 0.0f;
-      // two vectors of 4 entries per step, every load issued before any use
-      for (int qa = tid; qa < nq; qa += 2 * kThreads) {
-        const int qs[2] = {qa, qa + kThreads};
-        uint32_t uu[2][4];
-        float pp[2][4], gg[2][4];
-        uint32_t rw[2][4];
+      __syncthreads();
+      const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
+      constexpr int U = 8;   // entries per thread in flight
+      for (int e0 = tid; e0 < n; e0 += U * kThreads) {
+        uint32_t uu[U], rw[U];
+        float pp[U], gg[U];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const bool ok = qs[h] < nq;
-          const uint4 u = ok ? ents[qs[h]] : make_uint4(kPad, kPad, kPad, kPad);
-          uu[h][0] = u.x; uu[h][1] = u.y; uu[h][2] = u.z; uu[h][3] = u.w;
-          if (DT == SEP_DTYPE_U16_JF && ok) {
-            const float4* cal4 = reinterpret_cast<const float4*>(a.cal0 + r0);
-            const float4 ca = __ldg(cal4 + 2 * qs[h]), cb = __ldg(cal4 + 2 * qs[h] + 1);
-            pp[h][0] = ca.x; gg[h][0] = ca.y; pp[h][1] = ca.z; gg[h][1] = ca.w;
-            pp[h][2] = cb.x; gg[h][2] = cb.y; pp[h][3] = cb.z; gg[h][3] = cb.w;
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) { pp[h][j] = 0.0f; gg[h][j] = 1.0f; }
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * kThreads;
+          uu[k] = e < n ? ents[e] : kPad;
+          pp[k] = 0.0f;
+          gg[k] = 1.0f;
+          if (DT == SEP_DTYPE_U16_JF && !(uu[k] & kPad)) {
+            const float2 c = __ldg(a.cal0 + r0 + e);
+            pp[k] = c.x;
+            gg[k] = c.y;
           }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int k = 0; k < U; ++k) {
+          const int64_t col = uu[k] & kColMask;
+          if (uu[k] & kPad) rw[k] = 0u;
+          else if (DT == SEP_DTYPE_U16_JF) rw[k] = __ldg(reinterpret_cast<const uint16_t*>(frame) + col);
+          else rw[k] = __float_as_uint(__ldg(reinterpret_cast<const float*>(frame) + col));
+        }
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int64_t col = uu[h][j] & kColMask;
-            if (uu[h][j] & kPad) rw[h][j] = 0u;
-            else if (DT == SEP_DTYPE_U16_JF) rw[h][j] = __ldg(reinterpret_cast<const uint16_t*>(frame) + col);
-            else rw[h][j] = __float_as_uint(__ldg(reinterpret_cast<const float*>(frame) + col));
-          }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (qs[h] >= nq) continue;
-          float x[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (uu[h][j] & kPad) {
-              x[j] = __int_as_float(0x7fc00000);   // NaN: outside every interval
-              continue;
-            }
-            const int64_t col = uu[h][j] & kColMask;
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * kThreads;
+          if (e >= n) break;
+          float x;
+          if (uu[k] & kPad) {
+            x = __int_as_float(0x7fc00000);   // NaN: outside every interval
+          } else {
+            const int64_t col = uu[k] & kColMask;
             if (DT == SEP_DTYPE_U16_JF) {
-              const uint32_t raw = rw[h][j], code = raw >> 14;
-              float ped = pp[h][j], gain = gg[h][j];
+              const uint32_t raw = rw[k], code = raw >> 14;
+              float ped = pp[k], gain = gg[k];
               if (code != 0) {   // gain levels 1 and 2 are rare: read the pixel-ordered planes
                 const int64_t lvl = code == 1 ? 1 : 2;
                 ped = __ldg(a.ped + lvl * a.npix + col);
                 gain = __ldg(a.gain + lvl * a.npix + col);
               }
-              x[j] = __fdiv_rn(__fsub_rn((float)(raw & 0x3FFFu), ped), gain);
+              x = __fdiv_rn(__fsub_rn((float)(raw & 0x3FFFu), ped), gain);
             } else {
-              x[j] = __uint_as_float(rw[h][j]);
+              x = __uint_as_float(rw[k]);
             }
-            if (MODE == MODE_ENTRY) x[j] = __fdiv_rn(x[j], __ldg(a.norm + col));
+            if (MODE == MODE_ENTRY) x = __fdiv_rn(x, __ldg(a.norm + col));
           }
-          vals4[qs[h]] = make_float4(x[0], x[1], x[2], x[3]);
-          // rough sums (plain FP32): the first shift, and the surrogate's first-pass statistics
-          const int e0 = qs[h] << 2;
-          if (e0 < ge[3]) {
-            float w = 1.0f;
-            if (MODE == MODE_CLASS) w = e0 < ge[0] ? 1.0f : (e0 < ge[1] ? 0.75f : (e0 < ge[2] ? 0.5f : 0.25f));
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (MODE == MODE_ENTRY) w = wts[e0 + j];
-              if (x[j] == x[j] && w != 0.0f) {
-                om += w;
-                cn += 1.0f;
-                const float wx = w * x[j];
-                vv += wx;
-                v2 = fmaf(wx, x[j], v2);
-              }
-            }
-          }
+          vals[e] = x;
+          fp.add1(x, e, ge, wts);
         }
       }
-      s0[0] = om;
-      s0[1] = vv;
-      s0[2] = v2;
-      s0[3] = cn;
+      fp.finish();
     }
     {
-      uint32_t none[1] = {0u};
+      warp_ext<1, kWarps>(fp.ex, red_x);
       float thi, tlo;
-      block_sum<NV, 1, SEP_PREC_PLAIN, kWarps>(s0, c0, none, red_s, red_c, red_i, thi, tlo);
-      // lanes 0..3 of warp 0 hold Omega, V, sum w v^2, count
-      const float Om = __shfl_sync(0xffffffffu, thi, 0);
-      const float V = __shfl_sync(0xffffffffu, thi, 1);
-      const float V2 = __shfl_sync(0xffffffffu, thi, 2);
-      const float Cn = __shfl_sync(0xffffffffu, thi, 3);
-      if (tid == 0) {
-        float K = 0.0f, m = 0.0f, sdev = 0.0f;
-        if (Om > 0.0f) {
-          m = __fdiv_rn(V, Om);
-          const float var = __fsub_rn(__fdiv_rn(V2, Om), m * m);
-          sdev = var > 0.0f ? sqrtf(var) : 0.0f;
-          K = choose_shift(m, sdev);
+      block_sum<NF, NI, PREC, kWarps>(fp.ss, fp.cc, fp.ci, red_s, red_c, red_i, thi, tlo);
+      if (warp == 0) {
+        float th[NF + NI], tl[NF + NI];
+#pragma unroll
+        for (int v = 0; v < NF + NI; ++v) {
+          th[v] = __shfl_sync(0xffffffffu, thi, v);
+          tl[v] = __shfl_sync(0xffffffffu, tlo, v);
         }
-        st.Kf = K;
-        st.Ln = -FLT_MAX;
-        st.Hn = FLT_MAX;
-        st.L = -FLT_MAX;
-        st.H = FLT_MAX;
-        st.n_cur = -1.0f;
-        st.steps = -1;
-        st.done = 0;
-        st.mu_hi = st.mu_lo = st.sd = 0.0f;
-        st.mu_d = st.sd_d = 0.0;
-        if (SURR != 0) {
-          sv.m1 = m;
-          sv.s1 = sdev;
-          sv.om = Om;
-          sv.n = Cn;
-          sv.accepted = 0;
+        if (lane == 0) {
+          float n_set, h[6], l[6], e[4];
+          unpack_totals<MODE>(th, tl, n_set, h, l);
+          cta_ext<kWarps>(red_x, e);
+          st.Ln = -FLT_MAX;
+          st.Hn = FLT_MAX;
+          st.L = -FLT_MAX;
+          st.H = FLT_MAX;
+          st.n_cur = -1.0f;
+          st.steps = -1;
+          st.done = 0;
+          // moments of the full set about 0
+          finalise<PREC>(0.0f, h, l, st);
+          if (SURR != 0) {
+            sv.m1 = st.mu_hi;
+            sv.s1 = st.sd;
+            sv.om = __fadd_rn(h[0], l[0]);
+            sv.n = n_set;
+            sv.accepted = 0;
+          }
+          if (choose_shift(st.mu_hi, st.sd) == 0.0f) {
+            // the shift 0 suits this set: the gather was the first pass
+            clip_step<PREC>(st, n_set, h, l, e[1], e[2], 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true);
+          } else {
+            // cancellation about 0 is too large: the first pass runs again about the mean
+            st.Kf = st.mu_hi;
+          }
+          if (SURR == 2) st0 = st;
         }
       }
       __syncthreads();   // values and state visible to all
     }
 
-    if (SURR != 0) {
+    if (SURR == 1 || (SURR == 2 && !st.done)) {
       // ------------- surrogate features: first-pass statistics + z quantiles -------------
       const float m1 = sv.m1, inv = sv.s1 > 0.0f ? 1.0f / sv.s1 : 0.0f;
       const int zend = MODE == MODE_UNIT ? ge[0] : ge[3];
@@ -608,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
         const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (!(xs[j] == xs[j])) continue;
+          if (!(xs[j] >= -FLT_MAX && xs[j] <= FLT_MAX)) continue;
           if (MODE == MODE_ENTRY && wts[4 * q + j] == 0.0f) continue;
           const float zb = fminf(fmaxf(__fmul_rn(__fsub_rn(xs[j], m1), inv) * 4.0f + 16.0f, 0.0f), 63.0f);
           atomicAdd(&sv.hist[(int)zb], 1u);
@@ -651,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
       __syncthreads();
     }
 
-    if (SURR == 2) {
+    if (SURR == 2 && !st.done) {
       // ------------- predict (fused inference) -------------
       const __nv_bfloat16* W = a.mlp_w;
       for (int j = tid; j < kH; j += kThreads) {
@@ -689,7 +807,6 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
           st.Ln = mh - a.k_clip * sh;
           st.Hn = mh + a.k_clip * sh;
           st.Kf = choose_shift(mh, sh);
-          sv.accepted = 0;
         }
       }
       __syncthreads();
@@ -698,13 +815,13 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
       // [L', H'] = mu_I -+ k sd_I (Eq. 19), and the extremes around [Ln, Hn]
       // decide whether {v in [L', H']} == I without another pass: I is a fixed
       // point of the clip map iff no entry lies between the two intervals.
-      for (int r = 0; r <= a.surr_refine; ++r) {
+      for (int r = 0; r < a.surr_passes; ++r) {
         const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
         float ss[NF], cc[NF];
         uint32_t ci[NI];
-        Ext ex;
-        pass_sums<MODE, KAHAN, true, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
-        warp_ext<kWarps>(ex, red_x);
+        Ext<2> ex;
+        pass_sums<MODE, KAHAN, 2, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
+        warp_ext<2, kWarps>(ex, red_x);
         float thi, tlo;
         block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
         if (warp == 0) {
@@ -715,23 +832,16 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
             tl[v] = __shfl_sync(0xffffffffu, tlo, v);
           }
           if (lane == 0) {
-            float n_set, h[6], l[6];
+            float n_set, h[6], l[6], e[4];
             unpack_totals<MODE>(th, tl, n_set, h, l);
-            float e0 = -INFINITY, e1 = INFINITY, e2 = -INFINITY, e3 = INFINITY;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-              e0 = fmaxf(e0, red_x[0][w]);
-              e1 = fminf(e1, red_x[1][w]);
-              e2 = fmaxf(e2, red_x[2][w]);
-              e3 = fminf(e3, red_x[3][w]);
-            }
+            cta_ext<kWarps>(red_x, e);
             st.n_cur = n_set;
             st.L = Ln;
             st.H = Hn;
             finalise<PREC>(Kf, h, l, st);
             float L2 = -FLT_MAX, H2 = FLT_MAX;
             clip_bounds<PREC>(st, a.k_clip, L2, H2);
-            if (n_set >= 2.0f && e0 < L2 && L2 <= e1 && e2 <= H2 && H2 < e3) {
+            if (n_set >= 2.0f && e[0] < L2 && L2 <= e[1] && e[2] <= H2 && H2 < e[3]) {
               sv.accepted = 1;
             } else {
               st.Ln = L2;
@@ -745,17 +855,10 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
       }
       if (tid == 0) {
         if (sv.accepted) {
-          st.steps = 0;   // marks a bin settled by the surrogate
+          st.steps = -1;   // marks a bin settled by the surrogate
           st.done = 1;
-        } else {          // fall back to the plain iteration from the full set
-          st.Ln = -FLT_MAX;
-          st.Hn = FLT_MAX;
-          st.L = -FLT_MAX;
-          st.H = FLT_MAX;
-          st.Kf = choose_shift(sv.m1, sv.s1);
-          st.n_cur = -1.0f;
-          st.steps = -1;
-          st.done = 0;
+        } else {
+          st = st0;        // the plain loop from its state after the first pass
         }
         if (a.surr_stats) atomicAdd(a.surr_stats + (sv.accepted ? 0 : 1), 1ull);
       }
@@ -767,8 +870,9 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
       const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
       float ss[NF], cc[NF];
       uint32_t ci[NI];
-      Ext ex;
-      pass_sums<MODE, KAHAN, false, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
+      Ext<1> ex;
+      pass_sums<MODE, KAHAN, 1, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
+      warp_ext<1, kWarps>(ex, red_x);
       float thi, tlo;
       block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
       if (warp == 0) {
@@ -779,27 +883,10 @@ __global__ void __launch_bounds__(kThreads, SURR ? 1024 / kThreads : 1) k_integr
           tl[v] = __shfl_sync(0xffffffffu, tlo, v);
         }
         if (lane == 0) {
-          float n_set, h[6], l[6];
+          float n_set, h[6], l[6], e[4];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          // the pass measured S' = S ∩ [Ln, Hn]; S' == S means nothing was discarded
-          if (st.steps >= 0 && n_set == st.n_cur) {
-            st.done = 1;
-          } else {
-            st.n_cur = n_set;
-            st.L = Ln;
-            st.H = Hn;
-            finalise<PREC>(Kf, h, l, st);
-            st.steps += 1;
-            if (st.steps >= a.n_iter) {
-              st.done = 1;
-            } else {   // next set: reject |v - mu| > k sd (Eq. 19), cumulatively
-              float L2 = Ln, H2 = Hn;
-              clip_bounds<PREC>(st, a.k_clip, L2, H2);
-              st.Ln = L2;
-              st.Hn = H2;
-              st.Kf = choose_shift(st.mu_hi, st.sd);
-            }
-          }
+          cta_ext<kWarps>(red_x, e);
+          clip_step<PREC>(st, n_set, h, l, e[1], e[2], Kf, Ln, Hn, a.n_iter, a.k_clip);
         }
       }
       __syncthreads();

@@ -225,7 +225,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
     a.mlp_w = csr->model->d_wbf;
     a.mlp_norm = csr->model->d_norm;
     a.surr_stats = ctx->d_surr;
-    a.surr_refine = pr->surrogate - 1;
+    a.surr_passes = pr->surrogate;
   }
   return a;
 }

@@ -77,7 +77,7 @@ struct ClipArgs {
   const __nv_bfloat16* mlp_w = nullptr;
   const float* mlp_norm = nullptr;
   unsigned long long* surr_stats = nullptr;   // [2]: bins settled by the surrogate, bins that fell back
-  int32_t surr_refine = 0;             // verification passes after the first
+  int32_t surr_passes = 1;             // verification passes before the plain fallback
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
