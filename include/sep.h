@@ -146,8 +146,9 @@ sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* statu
  *  norm_host: rows*cols floats, the normalisation of Eq. 1 (denominator);
  *             may be NULL (= 1 everywhere). Must be > 0 on valid pixels.
  * Rows of the matrix are bins. Within a row, entries are grouped by
- * coefficient (largest first, then weight-0 entries), columns ascending in
- * a group, each group padded to a multiple of 4 entries. Every valid
+ * coefficient (largest first, then weight-0 entries), each group padded to
+ * a multiple of 4 entries and ordered by staging position (see
+ * sep_csr_staging). Every valid
  * pixel also gets its centre bin (the bin its threshold is taken from in
  * sparsification, Section 3); where that bin has no coefficient of the
  * pixel, an entry of weight 0 is added for it.
@@ -162,6 +163,13 @@ void sep_csr_destroy(sep_csr* csr);
 /* Sizes: pixels, bins, nonzeros, largest row; range[2] as used. Any out pointer may be NULL. */
 sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64_t* nnz,
                         int32_t* max_row, double* range);
+/* Staging order: every pixel with at least one matrix entry has a staging
+ * position (its corrected value is written there once per frame and the
+ * integration reads it from there). Pixels are grouped by tiles of 8 rows x
+ * 128 columns (tiles in row-major order); inside a tile, by centre bin, then
+ * pixel index. perm_inv [npos] receives the pixel of each position (may be
+ * NULL); *npos the number of positions. */
+sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos);
 /* Host copies for inspection (any pointer may be NULL):
  * rowptr [nbins+1], col [nnz] (-1 for padding), coef [nnz] (c_{i,r}; 0 for
  * padding and centre-only entries),

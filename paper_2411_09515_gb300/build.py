@@ -19,7 +19,7 @@ LIB = os.path.join(OUT, "libsep.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["k_clip.cu", "k_consumers.cu", "k_mlp.cu", "sep_api.cu", "sep_model.cu", "sep_noalloc.cu"]
+CU_SOURCES = ["k_clip.cu", "k_consumers.cu", "k_mlp.cu", "k_stage.cu", "sep_api.cu", "sep_model.cu", "sep_noalloc.cu"]
 CPP_SOURCES = ["sep_csr.cpp"]
 
 

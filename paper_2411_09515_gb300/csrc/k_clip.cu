@@ -1,25 +1,30 @@
-// Fused detector correction + CSR azimuthal integration + sigma-clipping.
+// Integration + sigma-clipping over staged pixel values.
 //
 // One CTA (64, 128 or 256 threads: a tuning choice per size class of bins)
 // owns one radial bin (a row of the integration matrix) and walks a group of
-// frames. Per frame it gathers the bin's pixels
-// once from the frame, corrects them (Section 1.2), and keeps the values in
-// shared memory; every clipping pass (Eq. 19, Section 2.4) then runs on chip.
+// frames. Per frame it gathers the bin's values from the frame's staged copy
+// (k_stage.cu: corrected pixels, Section 1.2, in an order where each bin
+// reads short contiguous runs) and keeps them in shared memory; every
+// clipping pass (Eq. 19, Section 2.4) then runs on chip.
 //
-// Moments (Eqs. 8-13) are accumulated about a shift K (the previous mean):
-// with d = v - K, per set S
+// Moments (Eqs. 8-13) are accumulated about a shift K: with d = v - K, per
+// set S
 //   Omega = sum w, A1 = sum w d, OO = sum w^2, B1 = sum w^2 d, B2 = sum w^2 d^2,
 //   mu = K + A1 / Omega,  VV = B2 - 2 (mu - K) B1 + (mu - K)^2 OO  (Eq. 11),
 //   sigma = sqrt(VV / OO)  (Eq. 13),
 // which is exact algebra; with K close to mu the correction terms are small,
-// so one pass per moment evaluation suffices (the gather pass supplies the
-// first shift).
+// so one pass per moment evaluation suffices. The gather itself accumulates
+// the sums of the full set about 0, which serve as the first pass whenever
+// that shift is adequate (|mu| <= 2 sigma).
 //
 // Rejection is cumulative and symmetric about the current mean, so the set
 // after t steps is every entry whose value lies in an interval [L_t, H_t]:
-// no per-entry flag is kept. Row entries are grouped by coefficient class
-// (a group shares one weight), so per-entry work is unweighted and the
-// class weight is applied once per thread per pass.
+// no per-entry flag is kept. Each pass also finds the smallest and largest
+// member of the set it measured; when both lie inside the next interval, the
+// next pass could discard nothing and the loop ends without it. Row entries
+// are grouped by coefficient class (a group shares one weight), so per-entry
+// work is unweighted and the class weight is applied once per thread per
+// pass.
 //
 // After the last evaluation, the bin's centre entries above mu + k_pick sigma
 // set their pixel's bit in the frame's kept-pixel bitmap (Section 3).
@@ -563,7 +568,7 @@ struct FirstPass {
 
 // Registers are capped so that 1024 threads stay resident per SM (the
 // serial step of one CTA overlaps the passes of the others).
-template <int DT, int MODE, int PREC, int kThreads, int SURR>
+template <int MODE, int PREC, int kThreads, int SURR>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(ClipArgs a) {
   constexpr int kWarps = kThreads / 32;
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
@@ -600,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
   }
 
   for (int f = f0; f < f1; ++f) {
-    const void* frame = a.fptr ? (const void*)a.fptr[f] : frame_ptr<DT>(a.frames, f, a.npix);
+    const float* vf = a.stage + (int64_t)f * a.npos;   // this frame's staged values
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
     // ------------- gather + correct, with the first pass (full set, shift 0) -------------
@@ -608,8 +613,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
     {
       // Stage the row's packed entries into the value slots (16-byte
       // cp.async copies), then gather with consecutive threads on
-      // consecutive entries: entries ascend in pixel index along the
-      // ring's arcs, so a warp's loads of raw words fall on few sectors.
+      // consecutive entries: inside a coefficient group the entries ascend
+      // in staging position, so a warp's loads fall on short contiguous runs.
       // Slot e is read (entry) and then written (value) by the same thread
       // only, so one barrier after the staging suffices.
       {
@@ -623,52 +628,20 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
       const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
       constexpr int U = 8;   // entries per thread in flight
       for (int e0 = tid; e0 < n; e0 += U * kThreads) {
-        uint32_t uu[U], rw[U];
-        float pp[U], gg[U];
+        float xv[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
           const int e = e0 + k * kThreads;
-          uu[k] = e < n ? ents[e] : kPad;
-          pp[k] = 0.0f;
-          gg[k] = 1.0f;
-          if (DT == SEP_DTYPE_U16_JF && !(uu[k] & kPad)) {
-            const float2 c = __ldg(a.cal0 + r0 + e);
-            pp[k] = c.x;
-            gg[k] = c.y;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int64_t col = uu[k] & kColMask;
-          if (uu[k] & kPad) rw[k] = 0u;
-          else if (DT == SEP_DTYPE_U16_JF) rw[k] = __ldg(reinterpret_cast<const uint16_t*>(frame) + col);
-          else rw[k] = __float_as_uint(__ldg(reinterpret_cast<const float*>(frame) + col));
+          const uint32_t u = e < n ? ents[e] : kPad;
+          // padding: NaN lies outside every interval
+          xv[k] = (u & kPad) ? __int_as_float(0x7fc00000) : __ldg(vf + (u & kColMask));
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
           const int e = e0 + k * kThreads;
           if (e >= n) break;
-          float x;
-          if (uu[k] & kPad) {
-            x = __int_as_float(0x7fc00000);   // NaN: outside every interval
-          } else {
-            const int64_t col = uu[k] & kColMask;
-            if (DT == SEP_DTYPE_U16_JF) {
-              const uint32_t raw = rw[k], code = raw >> 14;
-              float ped = pp[k], gain = gg[k];
-              if (code != 0) {   // gain levels 1 and 2 are rare: read the pixel-ordered planes
-                const int64_t lvl = code == 1 ? 1 : 2;
-                ped = __ldg(a.ped + lvl * a.npix + col);
-                gain = __ldg(a.gain + lvl * a.npix + col);
-              }
-              x = __fdiv_rn(__fsub_rn((float)(raw & 0x3FFFu), ped), gain);
-            } else {
-              x = __uint_as_float(rw[k]);
-            }
-            if (MODE == MODE_ENTRY) x = __fdiv_rn(x, __ldg(a.norm + col));
-          }
-          vals[e] = x;
-          fp.add1(x, e, ge, wts);
+          vals[e] = xv[k];
+          fp.add1(xv[k], e, ge, wts);
         }
       }
       fp.finish();
@@ -923,7 +896,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           if (xs[j] > thr) {   // NaN padding never passes
             const uint32_t u = __ldg(a.ent + r0 + 4 * q + j);
             if (MODE == MODE_UNIT || (u & kCentre)) {
-              const uint32_t col = u & kColMask;
+              const uint32_t col = (uint32_t)__ldg(a.perm_inv + (u & kColMask));
               atomicOr(bm + (col >> 5), 1u << (col & 31u));
             }
           }
@@ -936,10 +909,10 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
 
 // mode 0: set the shared-memory attribute and launch; 1: attribute only
 // (done eagerly before a stream capture); 2: launch only.
-template <int DT, int MODE, int PREC, int TPB, int SURR>
+template <int MODE, int PREC, int TPB, int SURR>
 cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
   const size_t smem = clip_smem_bytes(a.cap, MODE == MODE_ENTRY);
-  auto k = k_integrate_clip<DT, MODE, PREC, TPB, SURR>;
+  auto k = k_integrate_clip<MODE, PREC, TPB, SURR>;
   if (mode != 2) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess || mode == 1) return e;
@@ -949,34 +922,26 @@ cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int DT, int MODE, int PREC, int SURR>
+template <int MODE, int PREC, int SURR>
 cudaError_t launch_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
   switch (tpb) {
-    case 64: return launch_t<DT, MODE, PREC, 64, SURR>(a, n_ctas, mode, s);
-    case 128: return launch_t<DT, MODE, PREC, 128, SURR>(a, n_ctas, mode, s);
-    default: return launch_t<DT, MODE, PREC, 256, SURR>(a, n_ctas, mode, s);
+    case 64: return launch_t<MODE, PREC, 64, SURR>(a, n_ctas, mode, s);
+    case 128: return launch_t<MODE, PREC, 128, SURR>(a, n_ctas, mode, s);
+    default: return launch_t<MODE, PREC, 256, SURR>(a, n_ctas, mode, s);
   }
 }
 
-template <int DT, int MODE>
+template <int MODE>
 cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
   // the surrogate modes exist for the default precision only
-  if (a.rec_feat) return launch_b<DT, MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
-  if (a.mlp_w) return launch_b<DT, MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
+  if (a.rec_feat) return launch_b<MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
+  if (a.mlp_w) return launch_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
   switch (prec) {
-    case SEP_PREC_PLAIN: return launch_b<DT, MODE, SEP_PREC_PLAIN, 0>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_KAHAN: return launch_b<DT, MODE, SEP_PREC_KAHAN, 0>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_FP64MERGE: return launch_b<DT, MODE, SEP_PREC_FP64MERGE, 0>(a, n_ctas, tpb, mode, s);
-    default: return launch_b<DT, MODE, SEP_PREC_DWORD, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_PLAIN: return launch_b<MODE, SEP_PREC_PLAIN, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_KAHAN: return launch_b<MODE, SEP_PREC_KAHAN, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_FP64MERGE: return launch_b<MODE, SEP_PREC_FP64MERGE, 0>(a, n_ctas, tpb, mode, s);
+    default: return launch_b<MODE, SEP_PREC_DWORD, 0>(a, n_ctas, tpb, mode, s);
   }
-}
-
-template <int DT>
-cudaError_t launch_d(const ClipArgs& a, int n_ctas, int tpb, bool split, bool norm, int32_t prec, int mode,
-                     cudaStream_t s) {
-  if (norm) return launch_p<DT, MODE_ENTRY>(a, n_ctas, tpb, prec, mode, s);
-  return split ? launch_p<DT, MODE_CLASS>(a, n_ctas, tpb, prec, mode, s)
-               : launch_p<DT, MODE_UNIT>(a, n_ctas, tpb, prec, mode, s);
 }
 
 }  // namespace
@@ -986,11 +951,12 @@ size_t clip_smem_bytes(int32_t cap, bool weighted) {
   return (smem + 15) & ~(size_t)15;
 }
 
-cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, int32_t dtype, bool split, bool has_norm,
+cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, bool split, bool has_norm,
                                   int32_t precision, int mode, cudaStream_t s) {
   if (a.n_frames <= 0 || n_ctas <= 0) return cudaSuccess;
-  if (dtype == SEP_DTYPE_U16_JF) return launch_d<SEP_DTYPE_U16_JF>(a, n_ctas, tpb, split, has_norm, precision, mode, s);
-  return launch_d<SEP_DTYPE_F32>(a, n_ctas, tpb, split, has_norm, precision, mode, s);
+  if (has_norm) return launch_p<MODE_ENTRY>(a, n_ctas, tpb, precision, mode, s);
+  return split ? launch_p<MODE_CLASS>(a, n_ctas, tpb, precision, mode, s)
+               : launch_p<MODE_UNIT>(a, n_ctas, tpb, precision, mode, s);
 }
 
 }  // namespace sep

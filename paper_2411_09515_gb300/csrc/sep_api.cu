@@ -78,6 +78,19 @@ sep_status ensure_scratch(sep_ctx* ctx, int64_t bitmap_total, int64_t thr_total,
   return SEP_OK;
 }
 
+// Staged values of a batch: floats [total] (grown on demand, never inside a capture).
+sep_status ensure_stage(sep_ctx* ctx, int64_t total) {
+  if ((size_t)total > ctx->stage_len) {
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_len = 0;
+    cudaError_t e = cudaMalloc((void**)&ctx->d_stage, (size_t)total * 4);
+    if (e != cudaSuccess) return fail(ctx, SEP_ERR_OOM, "staging buffer allocation failed");
+    ctx->stage_len = (size_t)total;
+  }
+  return SEP_OK;
+}
+
 sep_status check_params(sep_ctx* ctx, const sep_params* p) {
   if (!p) return fail(ctx, SEP_ERR_ARG, "params is NULL");
   if (p->n_iter < 0 || p->n_iter > 1000) return fail(ctx, SEP_ERR_ARG, "n_iter out of range [0, 1000]");
@@ -193,24 +206,22 @@ int frames_per_cta(const sep_ctx* ctx, int32_t n_frames, int32_t nbins) {
   return (int)std::min<int64_t>(std::max<int64_t>(fpc, 1), 8);
 }
 
-sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames, int32_t dtype,
-                        int32_t n_frames, const sep_params* pr, float* mean, float* sigma, int32_t* count,
-                        float* bounds, int32_t* iters, uint32_t* bitmap, int64_t words) {
+sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, int32_t n_frames, const sep_params* pr,
+                        float* mean, float* sigma, int32_t* count, float* bounds, int32_t* iters, uint32_t* bitmap,
+                        int64_t words) {
   sep::ClipArgs a;
+  a.bin_list = nullptr;
   a.rowptr = csr->d_rowptr;
   a.grp = csr->d_grp;
-  a.cal0 = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_cal0 : nullptr;
   a.ent = csr->d_ent;
   a.w = csr->d_w;
-  a.norm = csr->d_norm;
-  a.frames = frames;
-  a.npix = csr->npix;
+  a.stage = stage;
+  a.perm_inv = csr->d_perm_inv;
+  a.npos = csr->h.npos;
   a.nbins = csr->h.nbins;
   a.n_frames = n_frames;
   a.frames_per_cta = frames_per_cta(ctx, n_frames, csr->h.nbins);
   a.cap = std::max(csr->h.max_row, 1);
-  a.ped = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_ped : nullptr;
-  a.gain = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_gain : nullptr;
   a.n_iter = pr->n_iter;
   a.k_clip = pr->k_clip;
   a.k_pick = pr->k_pick;
@@ -230,17 +241,40 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   return a;
 }
 
+// Correction + staging of n frames (contiguous at `frames`, or listed in
+// fptr) into stage [n][npos].
+cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames,
+                          const uint64_t* fptr, int32_t dtype, int32_t n, float* stage, cudaStream_t s) {
+  sep::StageArgs g;
+  g.frames = frames;
+  g.fptr = fptr;
+  g.npix = csr->npix;
+  g.npos = csr->h.npos;
+  g.rows = csr->h.rows;
+  g.cols = csr->h.cols;
+  g.tiles_x = csr->h.tiles_x;
+  g.tiles_y = csr->h.tiles_y;
+  g.n_frames = n;
+  g.frames_per_cta = std::min(n, 8);
+  g.ped = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_ped : nullptr;
+  g.gain = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_gain : nullptr;
+  g.norm = csr->d_norm;
+  g.tile_rank = csr->d_tile_rank;
+  g.tile_base = csr->d_tile_base;
+  g.stage = stage;
+  return sep::launch_stage(g, dtype, csr->has_norm, s);
+}
 
 // Launch the clip kernel for every size class of the plan: one class on the
 // caller's stream, several as parallel branches (fork / join through events,
 // which a stream capture records as graph edges).
-cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int32_t dtype, int32_t precision,
-                         int mode, cudaStream_t s, bool allow_fork = true) {
+cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int32_t precision, int mode,
+                         cudaStream_t s, bool allow_fork = true) {
   const bool split = csr->h.split > 1;
   if (csr->plan.empty()) {
     a.bin_list = nullptr;
     a.cap = std::max(csr->h.max_row, 4);
-    return sep::launch_integrate_clip(a, csr->h.nbins, 256, dtype, split, csr->has_norm, precision, mode, s);
+    return sep::launch_integrate_clip(a, csr->h.nbins, 256, split, csr->has_norm, precision, mode, s);
   }
   const int nc = (int)csr->plan.size();
   if (nc == 1 || mode == 1 || !allow_fork) {
@@ -248,7 +282,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
       a.bin_list = k.d_bins;
       a.cap = k.cap;
       a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
-      cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, dtype, split, csr->has_norm, precision, mode, s);
+      cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->has_norm, precision, mode, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -262,7 +296,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
     a.cap = k.cap;
     a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
     if (e == cudaSuccess)
-      e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, dtype, split, csr->has_norm, precision, mode, si);
+      e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->has_norm, precision, mode, si);
     if (e == cudaSuccess && i > 0) e = cudaEventRecord(ctx->ev_join[i], si);
   }
   for (int i = 1; i < nc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, ctx->ev_join[i], 0);
@@ -314,6 +348,7 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
+  if (ctx->d_stage) cudaFree(ctx->d_stage);
   if (ctx->d_desc) cudaFree(ctx->d_desc);
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   for (int i = 1; i < 4; ++i) {
@@ -372,6 +407,9 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
       (st = upload(ctx, &c->d_ent, c->h.ent.data(), c->h.ent.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_perm_inv, c->h.perm_inv.data(), std::max<size_t>(c->h.perm_inv.size(), 1))) != SEP_OK ||
+      (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
       (c->has_norm && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
       (c->has_norm && (st = upload(ctx, &c->d_norm, norm_host, (size_t)c->npix)) != SEP_OK)) {
     sep_csr_destroy(c);
@@ -395,6 +433,9 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_norm);
   cudaFree(csr->d_bop);
   cudaFree(csr->d_grp);
+  cudaFree(csr->d_perm_inv);
+  cudaFree(csr->d_tile_rank);
+  cudaFree(csr->d_tile_base);
   delete csr;
 }
 
@@ -412,6 +453,13 @@ sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64
   return SEP_OK;
 }
 
+sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos) {
+  if (!csr) return SEP_ERR_ARG;
+  if (perm_inv) memcpy(perm_inv, csr->h.perm_inv.data(), csr->h.perm_inv.size() * 4);
+  if (npos) *npos = csr->h.npos;
+  return SEP_OK;
+}
+
 sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, float* coef, int32_t* bin_of_pixel,
                           float* bin_centers) {
   if (!csr) return SEP_ERR_ARG;
@@ -419,7 +467,7 @@ sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, flo
   if (rowptr) memcpy(rowptr, h.rowptr.data(), h.rowptr.size() * 4);
   if (col)
     for (size_t e = 0; e < h.ent.size(); ++e)
-      col[e] = (h.ent[e] & sep::kPad) ? -1 : (int32_t)(h.ent[e] & sep::kColMask);
+      col[e] = (h.ent[e] & sep::kPad) ? -1 : h.perm_inv[h.ent[e] & sep::kColMask];
   if (coef) memcpy(coef, h.coef.data(), h.coef.size() * 4);
   if (bin_of_pixel) memcpy(bin_of_pixel, h.bop.data(), h.bop.size() * 4);
   if (bin_centers) memcpy(bin_centers, h.centers.data(), h.centers.size() * 4);
@@ -444,27 +492,6 @@ sep_status sep_calib_create(sep_ctx* ctx, const sep_csr* csr, const float* ped_h
     sep_calib_destroy(c);
     return st;
   }
-  // level-0 pedestal and gain copied into matrix-row order: the clip kernel
-  // reads them with the entries (coalesced) instead of gathering by pixel
-  try {
-    const sep::HostCsr& h = csr->h;
-    std::vector<float2> cal0(h.ent.size());
-    for (size_t e = 0; e < h.ent.size(); ++e) {
-      if (h.ent[e] & sep::kPad) {
-        cal0[e] = make_float2(0.0f, 1.0f);
-      } else {
-        const size_t col = h.ent[e] & sep::kColMask;
-        cal0[e] = make_float2(ped_host[col], gain_host[col]);
-      }
-    }
-    if ((st = upload(ctx, &c->d_cal0, cal0.data(), cal0.size())) != SEP_OK) {
-      sep_calib_destroy(c);
-      return st;
-    }
-  } catch (const std::bad_alloc&) {
-    sep_calib_destroy(c);
-    return fail(ctx, SEP_ERR_OOM, "host allocation failed");
-  }
   *out = c;
   return SEP_OK;
 }
@@ -474,7 +501,6 @@ void sep_calib_destroy(sep_calib* calib) {
   if (calib->ctx) cudaSetDevice(calib->ctx->device);
   cudaFree(calib->d_ped);
   cudaFree(calib->d_gain);
-  cudaFree(calib->d_cal0);
   delete calib;
 }
 
@@ -487,9 +513,12 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
   if (n_frames > 0 && (!mean_dev || !sigma_dev || !count_dev)) return fail(ctx, SEP_ERR_ARG, "NULL output");
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
-  sep::ClipArgs a = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
-                              bounds_dev, iters_dev, nullptr, 0);
-  cudaError_t e = enqueue_clip(ctx, csr, a, dtype, params->precision, 0, (cudaStream_t)stream);
+  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, bounds_dev,
+                              iters_dev, nullptr, 0);
+  cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
+  if (e == cudaSuccess) e = enqueue_clip(ctx, csr, a, params->precision, 0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "integrate_clip launch");
   return SEP_OK;
 }
@@ -506,11 +535,14 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
     return fail(ctx, SEP_ERR_ARG, "NULL output");
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
-  sep::ClipArgs a = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
-                              nullptr, nullptr, nullptr, 0);
+  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
+                              nullptr, nullptr, 0);
   a.rec_feat = feat_dev;
   a.rec_target = target_dev;
-  cudaError_t e = enqueue_clip(ctx, csr, a, dtype, params->precision, 0, (cudaStream_t)stream);
+  cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
+  if (e == cudaSuccess) e = enqueue_clip(ctx, csr, a, params->precision, 0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate_record launch");
   return SEP_OK;
 }
@@ -608,15 +640,17 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   if ((st = ensure_scratch(ctx, words * n_frames, 0, sep::consumer_scratch_words(n_frames, words, kept_capacity))) !=
       SEP_OK)
     return st;
+  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
-    sep::ClipArgs a = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
-                                nullptr, nullptr, ctx->d_bitmap, words);
+    sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
+                                nullptr, ctx->d_bitmap, words);
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
     cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
+    if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
     if (e == cudaSuccess)
-      e = enqueue_clip(ctx, csr, a, dtype, params->precision, mode, s);
+      e = enqueue_clip(ctx, csr, a, params->precision, mode, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
                               ctx->d_aux, ctx->d_status, s);
@@ -640,7 +674,8 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev,
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
                                (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
-                               (uint64_t)(uintptr_t)s, csr->plan_version, (uint64_t)(uintptr_t)csr->model};
+                               (uint64_t)(uintptr_t)s, csr->plan_version, (uint64_t)(uintptr_t)csr->model,
+                               (uint64_t)(uintptr_t)ctx->d_stage};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));
@@ -657,9 +692,9 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
       ctx->graphs.erase(lru);
     }
     // the kernel attribute is set before the capture, which then records launches only
-    sep::ClipArgs a0 = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, mean_dev, sigma_dev, count_dev,
-                                 nullptr, nullptr, ctx->d_bitmap, words);
-    cudaError_t e = enqueue_clip(ctx, csr, a0, dtype, params->precision, 1, s);
+    sep::ClipArgs a0 = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
+                                 nullptr, ctx->d_bitmap, words);
+    cudaError_t e = enqueue_clip(ctx, csr, a0, params->precision, 1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute");
     sep_graph_entry g;
     SEP_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -760,14 +795,30 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   cudaEventCreate(&e1);
   float best = 1e30f;
   int best_i = -1;
-  sep::ClipArgs base = clip_args(ctx, csr, calib, frames_dev, dtype, n_frames, params, d_out, d_out + per,
+  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) {
+    cudaFree(d_out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  }
+  // the staged sample is the same for every candidate schedule
+  {
+    cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
+    if (e != cudaSuccess) {
+      cudaFree(d_out);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(ctx, e, "autotune staging");
+    }
+  }
+  sep::ClipArgs base = clip_args(ctx, csr, ctx->d_stage, n_frames, params, d_out, d_out + per,
                                  reinterpret_cast<int32_t*>(d_out + 2 * per), nullptr, nullptr, nullptr, 0);
   for (size_t i = 0; i < cands.size(); ++i) {
     const Cand& c = cands[i];
     if ((st = make_plan(ctx, csr, c.nc, c.t, c.b)) != SEP_OK) break;
-    cudaError_t e = enqueue_clip(ctx, csr, base, dtype, params->precision, 0, s);   // warm-up
+    cudaError_t e = enqueue_clip(ctx, csr, base, params->precision, 0, s);   // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = enqueue_clip(ctx, csr, base, dtype, params->precision, 2, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = enqueue_clip(ctx, csr, base, params->precision, 2, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0;
@@ -852,8 +903,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
   // descriptor table (device): per detector fptr[m], orow[m], fidx[m]
   std::vector<int64_t> desc;
   std::vector<size_t> off_fptr(n_det), off_orow(n_det), off_fidx(n_det);
-  int64_t bm_total = 0, aux_total = 0;
-  std::vector<int64_t> bm_off(n_det), aux_off(n_det), words(n_det);
+  int64_t bm_total = 0, aux_total = 0, stage_total = 0;
+  std::vector<int64_t> bm_off(n_det), aux_off(n_det), words(n_det), soff(n_det);
   for (int d = 0; d < n_det; ++d) {
     const int64_t m = (int64_t)members[d].size();
     off_fptr[d] = desc.size();
@@ -869,8 +920,11 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
     bm_total += words[d] * m;
     aux_off[d] = aux_total;
     aux_total += sep::consumer_scratch_words((int32_t)m, words[d], kept_capacity);
+    soff[d] = stage_total;
+    stage_total += m * csrs[d]->h.npos;
   }
   if ((st = ensure_scratch(ctx, bm_total, 0, aux_total)) != SEP_OK) return st;
+  if ((st = ensure_stage(ctx, stage_total)) != SEP_OK) return st;
   if (desc.size() > ctx->desc_len) {
     if (ctx->d_desc) cudaFree(ctx->d_desc);
     if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
@@ -903,12 +957,12 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       const uint64_t* fptr = reinterpret_cast<const uint64_t*>(ctx->d_desc + off_fptr[d]);
       const int64_t* orow = ctx->d_desc + off_orow[d];
       const int32_t* fidx = reinterpret_cast<const int32_t*>(ctx->d_desc + off_fidx[d]);
-      sep::ClipArgs ca = clip_args(ctx, csr, calib, nullptr, dtype, m, params, mean_dev, sigma_dev, count_dev, nullptr,
-                                   nullptr, bm, words[d]);
-      ca.fptr = fptr;
+      float* stage = ctx->d_stage + soff[d];
+      sep::ClipArgs ca = clip_args(ctx, csr, stage, m, params, mean_dev, sigma_dev, count_dev, nullptr, nullptr, bm,
+                                   words[d]);
       ca.orow = orow;
       if (mode == 1) {
-        e = enqueue_clip(ctx, csr, ca, dtype, params->precision, 1, sd, false);
+        e = enqueue_clip(ctx, csr, ca, params->precision, 1, sd, false);
         continue;
       }
       sep::PixArgs pa = pix_args(csr, calib, nullptr, dtype);
@@ -916,7 +970,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       pa.fidx = fidx;
       pa.orow = orow;
       if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
-      if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, dtype, params->precision, mode, sd, false);
+      if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, nullptr, fptr, dtype, m, stage, sd);
+      if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, params->precision, mode, sd, false);
       if (e == cudaSuccess)
         e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,
                                 sd);
@@ -942,7 +997,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev, (uint64_t)peak_capacity,
                                (uint64_t)(uintptr_t)n_peaks_dev, (uint64_t)(uintptr_t)ctx->d_bitmap,
                                (uint64_t)(uintptr_t)ctx->d_aux, (uint64_t)(uintptr_t)ctx->d_desc,
-                               (uint64_t)(uintptr_t)s};
+                               (uint64_t)(uintptr_t)s, (uint64_t)(uintptr_t)ctx->d_stage};
   for (int d = 0; d < n_det; ++d) {
     key.push_back((uint64_t)(uintptr_t)csrs[d]);
     key.push_back(csrs[d]->plan_version);

@@ -194,6 +194,74 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       if (norm) out->w[e] = (float)(cf * (double)norm[i]);
     }
   }
+  // Staging order of the pixel values. The clip kernel gathers each bin's
+  // values from a staged copy of the frame in which pixels are grouped by
+  // tiles of kTileH x kTileW and, inside a tile, by centre bin (then pixel
+  // index): a bin's entries then read short contiguous runs (one per tile it
+  // crosses) instead of single pixels scattered over the image. Only pixels
+  // with at least one entry are staged. Entries address their pixel by its
+  // staging position; each coefficient group is re-sorted by position.
+  {
+    const int64_t tx = (cols + kTileW - 1) / kTileW, ty = (rows + kTileH - 1) / kTileH;
+    out->tiles_x = (int32_t)tx;
+    out->tiles_y = (int32_t)ty;
+    out->tile_base.assign((size_t)(tx * ty) + 1, 0);
+    out->tile_rank.assign((size_t)npix, (int16_t)-1);
+    out->perm_inv.clear();
+    out->perm_inv.reserve((size_t)npix);
+    std::vector<int32_t> pos_of((size_t)npix, -1);
+    std::vector<std::pair<int32_t, int32_t>> tile_px;
+    tile_px.reserve((size_t)kTileH * kTileW);
+    for (int64_t t = 0; t < tx * ty; ++t) {
+      const int64_t r0 = (t / tx) * kTileH, c0 = (t % tx) * kTileW;
+      tile_px.clear();
+      for (int64_t r = r0; r < std::min<int64_t>(r0 + kTileH, rows); ++r)
+        for (int64_t c = c0; c < std::min<int64_t>(c0 + kTileW, cols); ++c) {
+          const int64_t i = r * cols + c;
+          if (pn[i] > 0) tile_px.emplace_back(bop[i], (int32_t)i);
+        }
+      std::sort(tile_px.begin(), tile_px.end());
+      out->tile_base[t] = (int32_t)out->perm_inv.size();
+      for (size_t k = 0; k < tile_px.size(); ++k) {
+        const int32_t i = tile_px[k].second;
+        out->tile_rank[i] = (int16_t)k;
+        pos_of[i] = (int32_t)out->perm_inv.size();
+        out->perm_inv.push_back(i);
+      }
+    }
+    out->tile_base[tx * ty] = (int32_t)out->perm_inv.size();
+    out->npos = (int64_t)out->perm_inv.size();
+    // remap and re-sort every group (bin, class) by staging position
+    std::vector<std::pair<uint32_t, int64_t>> grp_e;
+    std::vector<uint32_t> ent2;
+    std::vector<float> coef2, w2;
+    for (int32_t b = 0; b < B; ++b) {
+      for (int c = 0; c < NC; ++c) {
+        const int64_t g1 = fill[(size_t)b * NC + c], g0 = g1 - cc[(size_t)b * NC + c];
+        grp_e.clear();
+        for (int64_t e = g0; e < g1; ++e) {
+          const uint32_t u = out->ent[e];
+          const uint32_t p = (uint32_t)pos_of[u & kColMask];
+          grp_e.emplace_back(p, e);
+        }
+        std::sort(grp_e.begin(), grp_e.end());
+        ent2.resize(grp_e.size());
+        coef2.resize(grp_e.size());
+        w2.resize(grp_e.size());
+        for (size_t k = 0; k < grp_e.size(); ++k) {
+          const int64_t e = grp_e[k].second;
+          ent2[k] = (out->ent[e] & ~kColMask) | grp_e[k].first;
+          coef2[k] = out->coef[e];
+          if (norm) w2[k] = out->w[e];
+        }
+        for (size_t k = 0; k < grp_e.size(); ++k) {
+          out->ent[g0 + (int64_t)k] = ent2[k];
+          out->coef[g0 + (int64_t)k] = coef2[k];
+          if (norm) out->w[g0 + (int64_t)k] = w2[k];
+        }
+      }
+    }
+  }
   out->rows = gm.rows;
   out->cols = gm.cols;
   out->nbins = B;

@@ -39,7 +39,15 @@ struct HostCsr {
   std::vector<int32_t> bop;      // [npix] centre bin, -1 masked
   std::vector<float> centers;    // [nbins]
   int32_t max_row = 0;
+  // staging order (entries address pixels by staging position)
+  int64_t npos = 0;                 // staged pixels (those with an entry)
+  int32_t tiles_x = 0, tiles_y = 0;
+  std::vector<int32_t> perm_inv;    // [npos] pixel of each staging position
+  std::vector<int16_t> tile_rank;   // [npix] position inside its tile, -1 not staged
+  std::vector<int32_t> tile_base;   // [tiles + 1] first position of each tile
 };
+
+constexpr int kTileH = 8, kTileW = 128;   // staging tiles (rows x columns)
 
 // Returns an empty string on success, else the reason.
 std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const float* norm, HostCsr* out);
@@ -49,15 +57,12 @@ struct ClipArgs {
   const int32_t* bin_list; // bins handled by this launch (blockIdx.x indexes it); null = all, in order
   const int32_t* rowptr;
   const int32_t* grp;      // [nbins][4] class ends within a row
-  const float2* cal0;      // per entry (ped, gain) of level 0 (raw input)
-  const uint32_t* ent;
+  const uint32_t* ent;     // packed entries: staging position + flags
   const float* w;          // per-entry weight c * norm (NORM variant)
-  const float* norm;       // per-pixel norm (NORM variant)
-  const void* frames;
-  int64_t npix;
+  const float* stage;      // staged values [n_frames][npos]
+  const int32_t* perm_inv; // [npos] pixel of each staging position
+  int64_t npos;
   int32_t nbins, n_frames, frames_per_cta, cap;
-  const float* ped;        // [3][npix] (raw input)
-  const float* gain;       // [3][npix]
   int32_t n_iter;
   float k_clip, k_pick;
   float* mean;
@@ -67,9 +72,8 @@ struct ClipArgs {
   int32_t* iters;          // optional [F][B]
   uint32_t* bitmap;        // optional kept-pixel map [F][words]
   int64_t words;           // bitmap words per frame
-  // mixed batches: per launch frame, its address and the first output row
-  // (in bins) of its profile; null = contiguous frames, rows f * nbins
-  const uint64_t* fptr = nullptr;
+  // mixed batches: per launch frame, the first output row (in bins) of its
+  // profile; null = rows f * nbins
   const int64_t* orow = nullptr;
   // surrogate: record features + targets (training data), or predict + verify
   float* rec_feat = nullptr;           // [rows][20]
@@ -78,6 +82,20 @@ struct ClipArgs {
   const float* mlp_norm = nullptr;
   unsigned long long* surr_stats = nullptr;   // [2]: bins settled by the surrogate, bins that fell back
   int32_t surr_passes = 1;             // verification passes before the plain fallback
+};
+
+struct StageArgs {         // correction + staging of a batch (k_stage)
+  const void* frames;      // contiguous [n_frames][npix], or
+  const uint64_t* fptr;    // per frame address (mixed batches), may be null
+  int64_t npix, npos;
+  int32_t rows, cols, tiles_x, tiles_y;
+  int32_t n_frames, frames_per_cta;
+  const float* ped;        // [3][npix] (raw input)
+  const float* gain;       // [3][npix]
+  const float* norm;       // [npix] or null
+  const int16_t* tile_rank;
+  const int32_t* tile_base;
+  float* stage;            // [n_frames][npos]
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
@@ -97,8 +115,9 @@ struct PixArgs {           // what the consumers need to recompute a pixel value
 
 // mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
 // only (call before a stream capture); 2: launch only.
-cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, int32_t dtype, bool split, bool has_norm,
+cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, bool split, bool has_norm,
                                   int32_t precision, int mode, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaStream_t s);
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
@@ -148,6 +167,8 @@ struct sep_ctx {
   int64_t* h_desc = nullptr;   // its pinned staging copy
   size_t desc_len = 0;
   unsigned long long* d_surr = nullptr;   // surrogate counters: settled, fell back
+  float* d_stage = nullptr;    // staged pixel values of the batch in flight
+  size_t stage_len = 0;
   // captured batches, keyed by every launch argument
   std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
   uint64_t use_clock = 0;
@@ -176,6 +197,9 @@ struct sep_csr {
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
+  int32_t* d_perm_inv = nullptr;      // staging order
+  int16_t* d_tile_rank = nullptr;
+  int32_t* d_tile_base = nullptr;
   const sep_model* model = nullptr;   // surrogate attached by sep_csr_attach_model
 };
 
@@ -198,5 +222,4 @@ struct sep_calib {
   int64_t npix = 0;
   float* d_ped = nullptr;
   float* d_gain = nullptr;
-  float2* d_cal0 = nullptr;    // per matrix entry: (pedestal, gain) of level 0, in row order
 };

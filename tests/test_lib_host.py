@@ -63,6 +63,7 @@ def compare_with_oracle(det, mask=None):
     csr = B.sep_build_csr(None, geom_of(det), mask)
     try:
         ex = B.sep_csr_export(csr)
+        perm_inv = B.sep_csr_staging(csr)
     finally:
         B.sep_csr_destroy(csr)
     W = oracle.weights(det, mask)
@@ -76,7 +77,18 @@ def compare_with_oracle(det, mask=None):
     got = sorted(zip(ex["col"][nz].tolist(), rows[nz].tolist(), ex["coef"][nz].astype(np.float64).tolist()))
     want = sorted(zip(W.pix.tolist(), W.bin.tolist(), W.c.tolist()))
     assert got == want
-    # within a row: coefficient groups, largest first, columns ascending in a group
+    # staging order: a permutation of the pixels with entries, tiles of
+    # 8 x 128 in row-major order, by centre bin then pixel inside a tile
+    used = np.unique(ex["col"][ex["col"] >= 0])
+    assert np.array_equal(np.sort(perm_inv), used)
+    r, cl = perm_inv // det.cols, perm_inv % det.cols
+    tiles_x = (det.cols + 127) // 128
+    key = np.stack([(r // 8) * tiles_x + cl // 128, W.bin_of_pixel[perm_inv], perm_inv], axis=1)
+    order = np.lexsort(key.T[::-1])
+    assert np.array_equal(order, np.arange(perm_inv.size))
+    pos_of = np.full(det.rows * det.cols, -1, np.int64)
+    pos_of[perm_inv] = np.arange(perm_inv.size)
+    # within a row: coefficient groups, largest first, staging positions ascending in a group
     for b in range(det.nbins):
         sl = slice(ex["rowptr"][b], ex["rowptr"][b + 1])
         c, k = ex["col"][sl], ex["coef"][sl]
@@ -84,7 +96,7 @@ def compare_with_oracle(det, mask=None):
         kk = np.where(k[real] == 0, -1.0, k[real])
         assert np.all(np.diff(kk) <= 0)
         for val in np.unique(kk):
-            assert np.all(np.diff(c[real][kk == val]) > 0)
+            assert np.all(np.diff(pos_of[c[real][kk == val]]) > 0)
     # zero-coefficient entries exist only to carry a pixel's centre bin
     zc, zr = ex["col"][~nz & ~pad], rows[~nz & ~pad]
     assert np.array_equal(W.bin_of_pixel[zc], zr)
