@@ -146,9 +146,9 @@ def run_ours(args):
         # the library's autotuner picks the clip schedule on a sample of the batch
         tune_ms = sep.autotune(dev[: min(F, 128)], stream=stream)
     plan = sep.get_plan()
-    # launches of our kernels per step: one clip launch per size class of
-    # the schedule, two for the compaction, two for the peaks
-    launches_per_step = max(len(plan["tpb"]), 1) + 4
+    # launches of our kernels per step: staging, one clip launch per size
+    # class of the schedule, marking, two for the compaction, two for the peaks
+    launches_per_step = max(len(plan["tpb"]), 1) + 6
 
     def step():
         sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)

@@ -26,8 +26,8 @@
 // work is unweighted and the class weight is applied once per thread per
 // pass.
 //
-// After the last evaluation, the bin's centre entries above mu + k_pick sigma
-// set their pixel's bit in the frame's kept-pixel bitmap (Section 3).
+// After the last evaluation the kernel writes mu + k_pick sigma, the bin's
+// sparsification threshold (Section 3), for k_mark_pos (k_consumers.cu).
 //
 // Precision (SEP_PREC_*): per-thread FP32 sums (Kahan-compensated in KAHAN)
 // and FP32 warp shuffles (error-free pairs in KAHAN). The cross-warp merge,
@@ -217,7 +217,7 @@ __device__ __forceinline__ void block_sum(float (&s)[NF], float (&c)[NF], uint32
 #pragma unroll
     for (int v = 0; v < NF; ++v) {
       red_s[v][warp] = s[v];
-      red_c[v][warp] = PREC == SEP_PREC_KAHAN ? c[v] : 0.0f;
+      if (PREC == SEP_PREC_KAHAN) red_c[v][warp] = c[v];
     }
 #pragma unroll
     for (int i = 0; i < NI; ++i) red_i[i][warp] = wi[i];
@@ -238,9 +238,10 @@ __device__ __forceinline__ void block_sum(float (&s)[NF], float (&c)[NF], uint32
       for (int w = 1; w < kWarps; ++w) x = __fadd_rn(x, red_s[lane][w]);
       thi = x;
     } else {   // error-free pairs (value = hs - hc)
-      float hs = red_s[lane][0], hc = red_c[lane][0];
+      float hs = red_s[lane][0], hc = PREC == SEP_PREC_KAHAN ? red_c[lane][0] : 0.0f;
 #pragma unroll
-      for (int w = 1; w < kWarps; ++w) pair_add(hs, hc, red_s[lane][w], red_c[lane][w]);
+      for (int w = 1; w < kWarps; ++w)
+        pair_add(hs, hc, red_s[lane][w], PREC == SEP_PREC_KAHAN ? red_c[lane][w] : 0.0f);
       two_sum(hs, -hc, thi, tlo);
     }
   } else if (warp == 0 && lane < NF + NI) {
@@ -388,20 +389,21 @@ __device__ __forceinline__ void warp_ext(Ext<EXT>& ex, float (*red_x)[kWarps]) {
   }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) red_x[v][threadIdx.x >> 5] = ex.x[v];
+    for (int v = 0; v < 4; ++v)
+      if (EXT == 2 || v == 1 || v == 2) red_x[v][threadIdx.x >> 5] = ex.x[v];
   }
 }
 
-// Lane 0 of warp 0: the extremes over the CTA.
-template <int kWarps>
+// Lane 0 of warp 0: the extremes over the CTA (EXT 1: the two inside only).
+template <int EXT, int kWarps>
 __device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)[4]) {
   e[0] = -INFINITY; e[1] = INFINITY; e[2] = -INFINITY; e[3] = INFINITY;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
-    e[0] = fmaxf(e[0], red_x[0][w]);
+    if (EXT == 2) e[0] = fmaxf(e[0], red_x[0][w]);
     e[1] = fminf(e[1], red_x[1][w]);
     e[2] = fmaxf(e[2], red_x[2][w]);
-    e[3] = fminf(e[3], red_x[3][w]);
+    if (EXT == 2) e[3] = fminf(e[3], red_x[3][w]);
   }
 }
 
@@ -489,14 +491,19 @@ struct FirstPass {
   uint32_t ci[NI];
   Ext<1> ex;
   int cur = 0;            // MODE_CLASS: class of the entries being accumulated
+  int cur_end = 0;        // its end in the row (ge[cur]; a scalar, so ge stays in registers)
   uint32_t cnt = 0;
   Acc<KAHAN> a1, a2;      // MODE_CLASS / MODE_UNIT
   Acc<KAHAN> om, oo, b1;  // MODE_ENTRY (a1 = sum w d, a2 = sum w^2 d^2)
-  __device__ __forceinline__ FirstPass() {
+  __device__ __forceinline__ FirstPass(const int (&ge)[4]) {
 #pragma unroll
     for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
 #pragma unroll
     for (int i = 0; i < NI; ++i) ci[i] = 0u;
+    cur_end = ge[0];
+  }
+  __device__ __forceinline__ static int class_end(const int (&ge)[4], int c) {
+    return c == 0 ? ge[0] : (c == 1 ? ge[1] : (c == 2 ? ge[2] : ge[3]));
   }
   // add the current class (weight w = 1 - cur / 4) to the totals
   __device__ __forceinline__ void flush_class() {
@@ -521,9 +528,10 @@ struct FirstPass {
   // the value of entry e (each thread's entries ascend)
   __device__ __forceinline__ void add1(float v, int e, const int (&ge)[4], const float* wts) {
     if (MODE == MODE_CLASS) {
-      while (cur < 4 && e >= ge[cur]) {
+      while (e >= cur_end && cur < 4) {
         flush_class();
         ++cur;
+        cur_end = cur < 4 ? class_end(ge, cur) : 0x7fffffff;
       }
       if (cur >= 4) return;   // weight-0 carriers
     } else if (MODE == MODE_UNIT) {
@@ -609,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
     // ------------- gather + correct, with the first pass (full set, shift 0) -------------
-    FirstPass<MODE, KAHAN> fp;
+    FirstPass<MODE, KAHAN> fp(ge);
     {
       // Stage the row's packed entries into the value slots (16-byte
       // cp.async copies), then gather with consecutive threads on
@@ -660,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         if (lane == 0) {
           float n_set, h[6], l[6], e[4];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          cta_ext<kWarps>(red_x, e);
+          cta_ext<1, kWarps>(red_x, e);
           st.Ln = -FLT_MAX;
           st.Hn = FLT_MAX;
           st.L = -FLT_MAX;
@@ -807,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           if (lane == 0) {
             float n_set, h[6], l[6], e[4];
             unpack_totals<MODE>(th, tl, n_set, h, l);
-            cta_ext<kWarps>(red_x, e);
+            cta_ext<2, kWarps>(red_x, e);
             st.n_cur = n_set;
             st.L = Ln;
             st.H = Hn;
@@ -858,7 +866,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         if (lane == 0) {
           float n_set, h[6], l[6], e[4];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          cta_ext<kWarps>(red_x, e);
+          cta_ext<1, kWarps>(red_x, e);
           clip_step<PREC>(st, n_set, h, l, e[1], e[2], Kf, Ln, Hn, a.n_iter, a.k_clip);
         }
       }
@@ -881,28 +889,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         a.rec_target[o * 2 + 1] = ok ? logf(st.sd / sv.s1) : __int_as_float(0x7fc00000);
       }
     }
-    // ---------------- sparsification mark (Section 3) ----------------
-    if (a.bitmap) {
-      __shared__ float thr_s;
-      if (tid == 0) thr_s = pick_threshold<PREC>(st, a.k_pick);
-      __syncthreads();
-      const float thr = thr_s;
-      uint32_t* bm = a.bitmap + (int64_t)f * a.words;
-      for (int q = tid; q < nq; q += kThreads) {
-        const float4 v4 = vals4[q];
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (xs[j] > thr) {   // NaN padding never passes
-            const uint32_t u = __ldg(a.ent + r0 + 4 * q + j);
-            if (MODE == MODE_UNIT || (u & kCentre)) {
-              const uint32_t col = (uint32_t)__ldg(a.perm_inv + (u & kColMask));
-              atomicOr(bm + (col >> 5), 1u << (col & 31u));
-            }
-          }
-        }
-      }
-    }
+    // threshold of sparsification (Section 3) for the marking kernel
+    if (a.thr_out && tid == 0) a.thr_out[o] = pick_threshold<PREC>(st, a.k_pick);
     __syncthreads();   // vals and state are rewritten by the next frame
   }
 }

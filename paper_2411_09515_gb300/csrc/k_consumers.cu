@@ -13,6 +13,14 @@
 namespace sep {
 namespace {
 
+// Value of pixel i of launch frame f: the staged copy when the call staged
+// the batch, else recomputed from the frame (the same IEEE sequence).
+template <int DT, bool NORM>
+__device__ __forceinline__ float value_of(const PixArgs& p, const void* frame, int64_t f, int64_t i) {
+  if (p.stage) return __ldg(p.stage + f * p.npos + __ldg(p.pos_of + i));
+  return pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
+}
+
 // Exclusive scan of one int per thread over a block of NT threads.
 template <int NT>
 __device__ __forceinline__ int block_exclusive_scan(int x, int* total, int* sh) {
@@ -62,6 +70,24 @@ __global__ void k_mark(PixArgs p, int32_t nbins, const float* thr, uint32_t* bit
   }
   uint32_t m = __ballot_sync(0xffffffffu, keep);
   if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bitmap[f * words + (i >> 5)] = m;
+}
+
+// Kept bits in staging order: consecutive threads read consecutive staged
+// values (coalesced); only kept pixels touch the bitmap.
+__global__ void __launch_bounds__(256) k_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos,
+                                                  const int32_t* perm_inv, const float* thr, const int64_t* orow,
+                                                  int32_t nbins, uint32_t* bitmap, int64_t words) {
+  const int64_t f = blockIdx.y;
+  const float* v = stage + f * npos;
+  const float* tf = thr + (orow ? orow[f] : f * (int64_t)nbins);
+  uint32_t* bm = bitmap + f * words;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += (int64_t)gridDim.x * blockDim.x) {
+    const float x = __ldg(v + p);
+    if (x > __ldg(tf + __ldg(bin_of_pos + p))) {
+      const uint32_t i = (uint32_t)__ldg(perm_inv + p);
+      atomicOr(bm + (i >> 5), 1u << (i & 31u));
+    }
+  }
 }
 
 constexpr int kCompactThreads = 1024;
@@ -152,7 +178,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
       m &= m - 1u;
       const int64_t i = (w0 + j) * 32 + bit;
       idx[g * cap + pos] = (int32_t)i;
-      val[g * cap + pos] = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
+      val[g * cap + pos] = value_of<DT, NORM>(p, frame, f, i);
       ++pos;
     }
   }
@@ -180,8 +206,8 @@ __device__ __forceinline__ bool is_kept(const uint32_t* bm, int64_t j) { return 
 // Is kept pixel i a peak (Section 4)? At least min_count kept pixels in the
 // patch, and i the maximum of the patch's valid pixels (ties: lowest index).
 template <int DT, bool NORM>
-__device__ __forceinline__ bool peak_test(const PixArgs& p, const void* frame, const uint32_t* bm, int64_t i, int h,
-                                          int32_t min_count, float vi, int& nk_out) {
+__device__ __forceinline__ bool peak_test(const PixArgs& p, const void* frame, int64_t f, const uint32_t* bm, int64_t i,
+                                          int h, int32_t min_count, float vi, int& nk_out) {
   const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
   const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
   const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
@@ -194,7 +220,7 @@ __device__ __forceinline__ bool peak_test(const PixArgs& p, const void* frame, c
     for (int c = clo; c <= chi; ++c) {
       const int64_t j = (int64_t)r * p.cols + c;
       if (j == i || __ldg(p.bop + j) < 0) continue;
-      const float vj = pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
+      const float vj = value_of<DT, NORM>(p, frame, f, j);
       if (!(vi > vj || (vi == vj && i < j))) return false;
     }
   return true;
@@ -219,8 +245,8 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_flags(PixArgs p, const ui
     const int64_t i = k < n ? idx[g * kcap + k] : -1;
     if (i >= 0 && i < p.npix && __ldg(p.bop + i) >= 0) {
       int nk;
-      const float vi = pixel_value<DT, NORM>(frame, i, p.npix, p.ped, p.gain, p.norm);
-      peak = peak_test<DT, NORM>(p, frame, bm, i, h, min_count, vi, nk);
+      const float vi = value_of<DT, NORM>(p, frame, f, i);
+      peak = peak_test<DT, NORM>(p, frame, f, bm, i, h, min_count, vi, nk);
     }
     const uint32_t m = __ballot_sync(0xffffffffu, peak);
     if ((threadIdx.x & 31) == 0) flags[f * ((int64_t)n_chunks * 8) + ch * 8 + (threadIdx.x >> 5)] = m;
@@ -290,7 +316,7 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
               const int64_t j = (int64_t)r * p.cols + cc;
               if (!is_kept(bm, j)) continue;
               const int32_t bj = __ldg(p.bop + j);
-              const float vj = pixel_value<DT, NORM>(frame, j, p.npix, p.ped, p.gain, p.norm);
+              const float vj = value_of<DT, NORM>(p, frame, f, j);
               const float w = vj - __ldg(mu + bj);
               const float s = __ldg(sd + bj);
               ++nk;
@@ -320,6 +346,16 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_thresholds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mean, sigma, k_pick, n, thr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos, const int32_t* perm_inv,
+                            const float* thr, const int64_t* orow, int32_t nbins, int32_t n_frames, uint32_t* bitmap,
+                            int64_t words, cudaStream_t s) {
+  if (n_frames <= 0 || npos <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((npos + 255) / 256, 4096);
+  dim3 grid((unsigned)blocks, (unsigned)n_frames);
+  k_mark_pos<<<grid, 256, 0, s>>>(stage, npos, bin_of_pos, perm_inv, thr, orow, nbins, bitmap, words);
   return cudaGetLastError();
 }
 

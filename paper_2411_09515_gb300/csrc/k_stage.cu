@@ -3,10 +3,10 @@
 // its staging position, where the clip kernel reads it.
 //
 // One CTA per staging tile (kTileH x kTileW pixels of the image) and group
-// of frames. Raw words and calibration planes are read in image order
-// (consecutive threads on consecutive pixels); the tile's values are placed
-// in shared memory at their rank inside the tile, then written out as one
-// contiguous run. Each value is the same IEEE sequence as pixel_value():
+// of frames. A warp reads one tile row: each thread four consecutive pixels
+// (one vector load where the row is aligned), two frames per step; the
+// tile's values are placed in shared memory at their rank inside the tile,
+// then written out as one contiguous run. Each value is the same IEEE sequence as pixel_value():
 // RN32(RN32(adc - pedestal) / gain), then RN32(. / norm).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,70 +19,112 @@ namespace {
 
 constexpr int kStageThreads = 256;
 constexpr int kTilePix = kTileH * kTileW;
-constexpr int kPerThread = kTilePix / kStageThreads;
-static_assert(kTilePix % kStageThreads == 0, "tile size");
+constexpr int kPerThread = kTilePix / kStageThreads;   // consecutive pixels of one row
+static_assert(kPerThread == 4 && kTileW % (4 * 32) == 0, "one warp covers a tile row, 4 pixels a thread");
 
-template <int DT, bool NORM>
+// Four consecutive raw words / values of one frame (VEC: one aligned vector load).
+template <int DT, bool VEC>
+__device__ __forceinline__ void load4(const void* frame, int64_t p, bool (&in)[4], uint32_t (&w)[4]) {
+  if (DT == SEP_DTYPE_U16_JF) {
+    const uint16_t* f = reinterpret_cast<const uint16_t*>(frame);
+    if (VEC) {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(f + p));
+      w[0] = v.x & 0xffffu; w[1] = v.x >> 16; w[2] = v.y & 0xffffu; w[3] = v.y >> 16;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = in[k] ? __ldg(f + p + k) : 0u;
+    }
+  } else {
+    const float* f = reinterpret_cast<const float*>(frame);
+    if (VEC) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(f + p));
+      w[0] = __float_as_uint(v.x); w[1] = __float_as_uint(v.y); w[2] = __float_as_uint(v.z); w[3] = __float_as_uint(v.w);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = in[k] ? __float_as_uint(__ldg(f + p + k)) : 0u;
+    }
+  }
+}
+
+template <int DT, bool NORM, bool VEC>
 __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
-  __shared__ float tv[kTilePix];
+  __shared__ float tv[2][kTilePix];
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)(t / a.tiles_x) * kTileH, c0 = (int64_t)(t % a.tiles_x) * kTileW;
   const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
   if (cnt == 0) return;
-  int64_t pix[kPerThread];
-  int rank[kPerThread];
-  float p0[kPerThread], g0[kPerThread], nm[kPerThread];
+  const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / 32;
+  const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % 32);
+  const int64_t p = r * a.cols + c;    // first of this thread's 4 pixels
+  bool in[4];
+  int rank[4];
+  float p0[4], g0[4], nm[4];
+  bool any = false;
 #pragma unroll
-  for (int k = 0; k < kPerThread; ++k) {
-    const int idx = tid + k * kStageThreads;
-    const int64_t r = r0 + idx / kTileW, c = c0 + idx % kTileW;
-    rank[k] = -1;
-    pix[k] = 0;
+  for (int k = 0; k < 4; ++k) {
+    in[k] = r < a.rows && c + k < a.cols;
+    rank[k] = in[k] ? __ldg(a.tile_rank + p + k) : -1;
+    any = any || rank[k] >= 0;
     p0[k] = 0.0f;
     g0[k] = 1.0f;
     nm[k] = 1.0f;
-    if (r < a.rows && c < a.cols) {
-      pix[k] = r * a.cols + c;
-      rank[k] = __ldg(a.tile_rank + pix[k]);
-      if (rank[k] >= 0) {
-        if (DT == SEP_DTYPE_U16_JF) {
-          p0[k] = __ldg(a.ped + pix[k]);
-          g0[k] = __ldg(a.gain + pix[k]);
-        }
-        if (NORM) nm[k] = __ldg(a.norm + pix[k]);
+    if (rank[k] >= 0) {
+      if (DT == SEP_DTYPE_U16_JF) {
+        p0[k] = __ldg(a.ped + p + k);
+        g0[k] = __ldg(a.gain + p + k);
       }
+      if (NORM) nm[k] = __ldg(a.norm + p + k);
     }
   }
   const int f0 = blockIdx.y * a.frames_per_cta;
   const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
-  for (int f = f0; f < f1; ++f) {
-    const void* frame = a.fptr ? (const void*)a.fptr[f] : frame_ptr<DT>(a.frames, f, a.npix);
+  // two frames per step: both frames' loads are in flight together
+  for (int f = f0; f < f1; f += 2) {
+    const int nf = min(2, f1 - f);
+    uint32_t w[2][4];
 #pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      if (rank[k] < 0) continue;
-      float x;
-      if (DT == SEP_DTYPE_U16_JF) {
-        const uint32_t u = __ldg(reinterpret_cast<const uint16_t*>(frame) + pix[k]);
-        const uint32_t code = u >> 14;
-        float ped = p0[k], gain = g0[k];
-        if (code != 0) {   // gain levels 1 and 2
-          const int64_t lvl = code == 1 ? 1 : 2;
-          ped = __ldg(a.ped + lvl * a.npix + pix[k]);
-          gain = __ldg(a.gain + lvl * a.npix + pix[k]);
-        }
-        x = __fdiv_rn(__fsub_rn((float)(u & 0x3FFFu), ped), gain);
-      } else {
-        x = __ldg(reinterpret_cast<const float*>(frame) + pix[k]);
+    for (int h = 0; h < 2; ++h) {
+      if (h < nf && any) {
+        const void* frame = a.fptr ? (const void*)a.fptr[f + h] : frame_ptr<DT>(a.frames, f + h, a.npix);
+        load4<DT, VEC>(frame, p, in, w[h]);
       }
-      if (NORM) x = __fdiv_rn(x, nm[k]);
-      tv[rank[k]] = x;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nf) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (rank[k] < 0) continue;
+        float x;
+        if (DT == SEP_DTYPE_U16_JF) {
+          const uint32_t u = w[h][k], code = u >> 14;
+          float ped = p0[k], gain = g0[k];
+          if (code != 0) {   // gain levels 1 and 2
+            const int64_t lvl = code == 1 ? 1 : 2;
+            ped = __ldg(a.ped + lvl * a.npix + p + k);
+            gain = __ldg(a.gain + lvl * a.npix + p + k);
+          }
+          x = __fdiv_rn(__fsub_rn((float)(u & 0x3FFFu), ped), gain);
+        } else {
+          x = __uint_as_float(w[h][k]);
+        }
+        if (NORM) x = __fdiv_rn(x, nm[k]);
+        tv[h][rank[k]] = x;
+      }
     }
     __syncthreads();
-    float* out = a.stage + (int64_t)f * a.npos + base;
-    for (int j = tid; j < cnt; j += kStageThreads) out[j] = tv[j];
+    for (int h = 0; h < nf; ++h) {
+      float* out = a.stage + (int64_t)(f + h) * a.npos + base;
+      for (int j = tid; j < cnt; j += kStageThreads) out[j] = tv[h][j];
+    }
     __syncthreads();
   }
+}
+
+template <int DT, bool NORM>
+void launch_v(const StageArgs& a, dim3 grid, bool vec, cudaStream_t s) {
+  if (vec) k_stage<DT, NORM, true><<<grid, kStageThreads, 0, s>>>(a);
+  else k_stage<DT, NORM, false><<<grid, kStageThreads, 0, s>>>(a);
 }
 
 }  // namespace
@@ -91,12 +133,17 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
   if (a.n_frames <= 0) return cudaSuccess;
   const int n_tiles = a.tiles_x * a.tiles_y;
   dim3 grid(n_tiles, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
+  // vector loads need every thread's 4 pixels aligned: a column count that
+  // is a multiple of 4 (tiles start at multiples of 128), frames contiguous
+  // or listed at 16-byte aligned addresses
+  bool vec = a.cols % 4 == 0;
+  if (!a.fptr) vec = vec && ((uintptr_t)a.frames % 16 == 0);
   if (dtype == SEP_DTYPE_U16_JF) {
-    if (has_norm) k_stage<SEP_DTYPE_U16_JF, true><<<grid, kStageThreads, 0, s>>>(a);
-    else k_stage<SEP_DTYPE_U16_JF, false><<<grid, kStageThreads, 0, s>>>(a);
+    if (has_norm) launch_v<SEP_DTYPE_U16_JF, true>(a, grid, vec && !a.fptr, s);
+    else launch_v<SEP_DTYPE_U16_JF, false>(a, grid, vec && !a.fptr, s);
   } else {
-    if (has_norm) k_stage<SEP_DTYPE_F32, true><<<grid, kStageThreads, 0, s>>>(a);
-    else k_stage<SEP_DTYPE_F32, false><<<grid, kStageThreads, 0, s>>>(a);
+    if (has_norm) launch_v<SEP_DTYPE_F32, true>(a, grid, vec && !a.fptr, s);
+    else launch_v<SEP_DTYPE_F32, false>(a, grid, vec && !a.fptr, s);
   }
   return cudaGetLastError();
 }

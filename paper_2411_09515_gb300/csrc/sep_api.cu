@@ -207,8 +207,7 @@ int frames_per_cta(const sep_ctx* ctx, int32_t n_frames, int32_t nbins) {
 }
 
 sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, int32_t n_frames, const sep_params* pr,
-                        float* mean, float* sigma, int32_t* count, float* bounds, int32_t* iters, uint32_t* bitmap,
-                        int64_t words) {
+                        float* mean, float* sigma, int32_t* count, float* bounds, int32_t* iters, float* thr_out) {
   sep::ClipArgs a;
   a.bin_list = nullptr;
   a.rowptr = csr->d_rowptr;
@@ -230,8 +229,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.count = count;
   a.bounds = bounds;
   a.iters = iters;
-  a.bitmap = bitmap;
-  a.words = words;
+  a.thr_out = thr_out;
   if (pr->surrogate > 0 && csr->model) {
     a.mlp_w = csr->model->d_wbf;
     a.mlp_norm = csr->model->d_norm;
@@ -255,7 +253,7 @@ cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* cal
   g.tiles_x = csr->h.tiles_x;
   g.tiles_y = csr->h.tiles_y;
   g.n_frames = n;
-  g.frames_per_cta = std::min(n, 8);
+  g.frames_per_cta = std::min(n, 32);   // calibration and ranks are read once per CTA
   g.ped = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_ped : nullptr;
   g.gain = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_gain : nullptr;
   g.norm = csr->d_norm;
@@ -408,6 +406,8 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_perm_inv, c->h.perm_inv.data(), std::max<size_t>(c->h.perm_inv.size(), 1))) != SEP_OK ||
+      (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_bin_of_pos, c->h.bin_of_pos.data(), std::max<size_t>(c->h.bin_of_pos.size(), 1))) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
       (c->has_norm && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
@@ -434,6 +434,8 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_bop);
   cudaFree(csr->d_grp);
   cudaFree(csr->d_perm_inv);
+  cudaFree(csr->d_pos_of);
+  cudaFree(csr->d_bin_of_pos);
   cudaFree(csr->d_tile_rank);
   cudaFree(csr->d_tile_base);
   delete csr;
@@ -516,7 +518,7 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
   if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, bounds_dev,
-                              iters_dev, nullptr, 0);
+                              iters_dev, nullptr);
   cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
   if (e == cudaSuccess) e = enqueue_clip(ctx, csr, a, params->precision, 0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "integrate_clip launch");
@@ -538,7 +540,7 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
   if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
-                              nullptr, nullptr, 0);
+                              nullptr, nullptr);
   a.rec_feat = feat_dev;
   a.rec_target = target_dev;
   cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
@@ -637,20 +639,26 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
   const int64_t words = bitmap_words(csr->npix);
-  if ((st = ensure_scratch(ctx, words * n_frames, 0, sep::consumer_scratch_words(n_frames, words, kept_capacity))) !=
-      SEP_OK)
+  if ((st = ensure_scratch(ctx, words * n_frames, (int64_t)n_frames * csr->h.nbins,
+                           sep::consumer_scratch_words(n_frames, words, kept_capacity))) != SEP_OK)
     return st;
   if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
     sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
-                                nullptr, ctx->d_bitmap, words);
+                                nullptr, ctx->d_thr);
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
+    p.stage = ctx->d_stage;
+    p.pos_of = csr->d_pos_of;
+    p.npos = csr->h.npos;
     cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
     if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
     if (e == cudaSuccess)
       e = enqueue_clip(ctx, csr, a, params->precision, mode, s);
+    if (e == cudaSuccess)
+      e = sep::launch_mark_pos(ctx->d_stage, csr->h.npos, csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, nullptr,
+                               csr->h.nbins, n_frames, ctx->d_bitmap, words, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
                               ctx->d_aux, ctx->d_status, s);
@@ -675,7 +683,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
                                (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
                                (uint64_t)(uintptr_t)s, csr->plan_version, (uint64_t)(uintptr_t)csr->model,
-                               (uint64_t)(uintptr_t)ctx->d_stage};
+                               (uint64_t)(uintptr_t)ctx->d_stage, (uint64_t)(uintptr_t)ctx->d_thr};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));
@@ -693,7 +701,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
     }
     // the kernel attribute is set before the capture, which then records launches only
     sep::ClipArgs a0 = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
-                                 nullptr, ctx->d_bitmap, words);
+                                 nullptr, ctx->d_thr);
     cudaError_t e = enqueue_clip(ctx, csr, a0, params->precision, 1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute");
     sep_graph_entry g;
@@ -812,7 +820,7 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
     }
   }
   sep::ClipArgs base = clip_args(ctx, csr, ctx->d_stage, n_frames, params, d_out, d_out + per,
-                                 reinterpret_cast<int32_t*>(d_out + 2 * per), nullptr, nullptr, nullptr, 0);
+                                 reinterpret_cast<int32_t*>(d_out + 2 * per), nullptr, nullptr, nullptr);
   for (size_t i = 0; i < cands.size(); ++i) {
     const Cand& c = cands[i];
     if ((st = make_plan(ctx, csr, c.nc, c.t, c.b)) != SEP_OK) break;
@@ -903,7 +911,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
   // descriptor table (device): per detector fptr[m], orow[m], fidx[m]
   std::vector<int64_t> desc;
   std::vector<size_t> off_fptr(n_det), off_orow(n_det), off_fidx(n_det);
-  int64_t bm_total = 0, aux_total = 0, stage_total = 0;
+  int64_t bm_total = 0, aux_total = 0, stage_total = 0, thr_total = rows[n_frames];
   std::vector<int64_t> bm_off(n_det), aux_off(n_det), words(n_det), soff(n_det);
   for (int d = 0; d < n_det; ++d) {
     const int64_t m = (int64_t)members[d].size();
@@ -923,7 +931,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
     soff[d] = stage_total;
     stage_total += m * csrs[d]->h.npos;
   }
-  if ((st = ensure_scratch(ctx, bm_total, 0, aux_total)) != SEP_OK) return st;
+  if ((st = ensure_scratch(ctx, bm_total, thr_total, aux_total)) != SEP_OK) return st;
   if ((st = ensure_stage(ctx, stage_total)) != SEP_OK) return st;
   if (desc.size() > ctx->desc_len) {
     if (ctx->d_desc) cudaFree(ctx->d_desc);
@@ -958,8 +966,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       const int64_t* orow = ctx->d_desc + off_orow[d];
       const int32_t* fidx = reinterpret_cast<const int32_t*>(ctx->d_desc + off_fidx[d]);
       float* stage = ctx->d_stage + soff[d];
-      sep::ClipArgs ca = clip_args(ctx, csr, stage, m, params, mean_dev, sigma_dev, count_dev, nullptr, nullptr, bm,
-                                   words[d]);
+      sep::ClipArgs ca = clip_args(ctx, csr, stage, m, params, mean_dev, sigma_dev, count_dev, nullptr, nullptr,
+                                   ctx->d_thr);
       ca.orow = orow;
       if (mode == 1) {
         e = enqueue_clip(ctx, csr, ca, params->precision, 1, sd, false);
@@ -969,9 +977,15 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       pa.fptr = fptr;
       pa.fidx = fidx;
       pa.orow = orow;
+      pa.stage = stage;
+      pa.pos_of = csr->d_pos_of;
+      pa.npos = csr->h.npos;
       if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
       if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, nullptr, fptr, dtype, m, stage, sd);
       if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, params->precision, mode, sd, false);
+      if (e == cudaSuccess)
+        e = sep::launch_mark_pos(stage, csr->h.npos, csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, orow,
+                                 csr->h.nbins, m, bm, words[d], sd);
       if (e == cudaSuccess)
         e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,
                                 sd);
@@ -997,7 +1011,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
                                (uint64_t)(uintptr_t)n_kept_dev, (uint64_t)(uintptr_t)peaks_dev, (uint64_t)peak_capacity,
                                (uint64_t)(uintptr_t)n_peaks_dev, (uint64_t)(uintptr_t)ctx->d_bitmap,
                                (uint64_t)(uintptr_t)ctx->d_aux, (uint64_t)(uintptr_t)ctx->d_desc,
-                               (uint64_t)(uintptr_t)s, (uint64_t)(uintptr_t)ctx->d_stage};
+                               (uint64_t)(uintptr_t)s, (uint64_t)(uintptr_t)ctx->d_stage,
+                               (uint64_t)(uintptr_t)ctx->d_thr};
   for (int d = 0; d < n_det; ++d) {
     key.push_back((uint64_t)(uintptr_t)csrs[d]);
     key.push_back(csrs[d]->plan_version);

@@ -43,6 +43,8 @@ struct HostCsr {
   int64_t npos = 0;                 // staged pixels (those with an entry)
   int32_t tiles_x = 0, tiles_y = 0;
   std::vector<int32_t> perm_inv;    // [npos] pixel of each staging position
+  std::vector<int32_t> pos_of;      // [npix] staging position of each pixel, -1 if not staged
+  std::vector<int16_t> bin_of_pos;  // [npos] centre bin of the pixel at each position
   std::vector<int16_t> tile_rank;   // [npix] position inside its tile, -1 not staged
   std::vector<int32_t> tile_base;   // [tiles + 1] first position of each tile
 };
@@ -70,8 +72,7 @@ struct ClipArgs {
   int32_t* count;
   float* bounds;           // optional [F][B][2]
   int32_t* iters;          // optional [F][B]
-  uint32_t* bitmap;        // optional kept-pixel map [F][words]
-  int64_t words;           // bitmap words per frame
+  float* thr_out;          // optional [F][B] sparsification thresholds (Section 3)
   // mixed batches: per launch frame, the first output row (in bins) of its
   // profile; null = rows f * nbins
   const int64_t* orow = nullptr;
@@ -111,6 +112,11 @@ struct PixArgs {           // what the consumers need to recompute a pixel value
   const uint64_t* fptr = nullptr;
   const int32_t* fidx = nullptr;
   const int64_t* orow = nullptr;
+  // staged values of the batch ([frame][npos], frame = launch index), when
+  // the call staged them: read instead of recomputing from the raw word
+  const float* stage = nullptr;
+  const int32_t* pos_of = nullptr;   // [npix] staging position, -1 if not staged
+  int64_t npos = 0;
 };
 
 // mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
@@ -121,6 +127,11 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
+// Kept-pixel bitmap from staged values: pixel perm_inv[p] is kept iff its
+// staged value exceeds the threshold of its centre bin.
+cudaError_t launch_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos, const int32_t* perm_inv,
+                            const float* thr, const int64_t* orow, int32_t nbins, int32_t n_frames, uint32_t* bitmap,
+                            int64_t words, cudaStream_t s);
 cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* thr, uint32_t* bitmap,
                         int64_t words, cudaStream_t s);
 // Ordered compaction of the kept-pixel bitmap (two launches; scratch holds
@@ -198,6 +209,8 @@ struct sep_csr {
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
   int32_t* d_perm_inv = nullptr;      // staging order
+  int32_t* d_pos_of = nullptr;
+  int16_t* d_bin_of_pos = nullptr;
   int16_t* d_tile_rank = nullptr;
   int32_t* d_tile_base = nullptr;
   const sep_model* model = nullptr;   // surrogate attached by sep_csr_attach_model
