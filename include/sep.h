@@ -364,6 +364,15 @@ sep_status sep_surrogate_train(sep_model* model, const float* x_dev, const float
  * surrogate. */
 sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
 
+/* Corrected frames (Section 1.2 and Eq. 1): out_dev [n_frames][npix] float32
+ * receives RN32(RN32(adc - ped[g]) / gain[g]) (raw Jungfrau words, dtype
+ * SEP_DTYPE_U16_JF) or the float32 input, divided by the norm when the
+ * matrix has one, for every pixel the matrix uses; pixels it does not use
+ * (masked, outside the radial range) receive NaN. These are the values the
+ * integration reads. Uses the context's staging buffer. */
+sep_status sep_correct(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
+                       int32_t dtype, int32_t n_frames, float* out_dev, sep_stream stream);
+
 /* Plain clip (params->surrogate must be 0) that also records, per frame and
  * bin, the surrogate's input features feat_dev [n_frames][nbins][SEP_MLP_IN]
  * and its training targets target_dev [n_frames][nbins][2] =

@@ -163,6 +163,14 @@ class Separator:
     def export_csr(self):
         return B.sep_csr_export(self.csr)
 
+    def correct(self, frames, stream=None):
+        """Corrected frames (float32 [F][npix]; NaN where the matrix uses no pixel)."""
+        t = self.torch
+        F = self._check_frames(frames)
+        out = t.empty((F, self.npix), dtype=t.float32, device=frames.device)
+        B.sep_correct(self.ctx, self.csr, self.calib, frames, self._dtype(frames), F, out, stream)
+        return out
+
     def integrate_clip(self, frames, bounds=False, iters=False, stream=None):
         t = self.torch
         F = self._check_frames(frames)

@@ -32,7 +32,7 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune", "sep_process_mixed",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
-           "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging"]
+           "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 
@@ -123,6 +123,7 @@ def lib():
     L.sep_model_load.argtypes = [_vp, C.c_char_p, C.POINTER(_vp)]
     L.sep_csr_attach_model.argtypes = [_vp, _vp]
     L.sep_csr_staging.argtypes = [_vp, _vp, C.POINTER(C.c_int64)]
+    L.sep_correct.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp]
     L.sep_surrogate_record.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp,
                                        _vp, _vp, _vp, _vp]
     L.sep_surrogate_prepare.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_int64), _vp]
@@ -414,3 +415,7 @@ def sep_csr_staging(csr):
     out = np.zeros(max(n.value, 1), np.int32)
     lib().sep_csr_staging(csr, _ptr(out), C.byref(n))
     return out[: n.value]
+
+
+def sep_correct(ctx, csr, calib, frames, dtype, n_frames, out, stream=None):
+    _check(ctx, lib().sep_correct(ctx, csr, calib, _ptr(frames), dtype, n_frames, _ptr(out), _stream(stream)))

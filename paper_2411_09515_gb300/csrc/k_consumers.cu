@@ -72,22 +72,37 @@ __global__ void k_mark(PixArgs p, int32_t nbins, const float* thr, uint32_t* bit
   if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bitmap[f * words + (i >> 5)] = m;
 }
 
-// Kept bits in staging order: consecutive threads read consecutive staged
-// values (coalesced); only kept pixels touch the bitmap.
-__global__ void __launch_bounds__(256) k_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos,
-                                                  const int32_t* perm_inv, const float* thr, const int64_t* orow,
-                                                  int32_t nbins, uint32_t* bitmap, int64_t words) {
+// Kept bits in staging order: each thread reads four consecutive staged
+// values and their centre bins (vector loads; rows are 128-byte aligned);
+// only kept pixels touch the bitmap.
+__global__ void __launch_bounds__(256) k_mark_pos(const float* stage, int64_t npos, int64_t stride,
+                                                  const int16_t* bin_of_pos, const int32_t* perm_inv, const float* thr,
+                                                  const int64_t* orow, int32_t nbins, uint32_t* bitmap, int64_t words) {
   const int64_t f = blockIdx.y;
-  const float* v = stage + f * npos;
+  const int64_t p = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (p >= npos) return;
+  const float4 v = __ldg(reinterpret_cast<const float4*>(stage + f * stride + p));
+  const short4 bq = __ldg(reinterpret_cast<const short4*>(bin_of_pos + p));
   const float* tf = thr + (orow ? orow[f] : f * (int64_t)nbins);
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  const int bb[4] = {bq.x, bq.y, bq.z, bq.w};
   uint32_t* bm = bitmap + f * words;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += (int64_t)gridDim.x * blockDim.x) {
-    const float x = __ldg(v + p);
-    if (x > __ldg(tf + __ldg(bin_of_pos + p))) {
-      const uint32_t i = (uint32_t)__ldg(perm_inv + p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (p + k < npos && x[k] > __ldg(tf + bb[k])) {
+      const uint32_t i = (uint32_t)__ldg(perm_inv + p + k);
       atomicOr(bm + (i >> 5), 1u << (i & 31u));
     }
   }
+}
+
+// Staged values back to image order; pixels without a position get NaN.
+__global__ void k_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, float* out) {
+  const int64_t f = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  const int32_t q = __ldg(pos_of + i);
+  out[f * npix + i] = q >= 0 ? __ldg(stage + f * stride + q) : __int_as_float(0x7fc00000);
 }
 
 constexpr int kCompactThreads = 1024;
@@ -349,13 +364,20 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
   return cudaGetLastError();
 }
 
-cudaError_t launch_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos, const int32_t* perm_inv,
-                            const float* thr, const int64_t* orow, int32_t nbins, int32_t n_frames, uint32_t* bitmap,
-                            int64_t words, cudaStream_t s) {
+cudaError_t launch_mark_pos(const float* stage, int64_t npos, int64_t stride, const int16_t* bin_of_pos,
+                            const int32_t* perm_inv, const float* thr, const int64_t* orow, int32_t nbins,
+                            int32_t n_frames, uint32_t* bitmap, int64_t words, cudaStream_t s) {
   if (n_frames <= 0 || npos <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((npos + 255) / 256, 4096);
-  dim3 grid((unsigned)blocks, (unsigned)n_frames);
-  k_mark_pos<<<grid, 256, 0, s>>>(stage, npos, bin_of_pos, perm_inv, thr, orow, nbins, bitmap, words);
+  dim3 grid((unsigned)((npos + 1023) / 1024), (unsigned)n_frames);
+  k_mark_pos<<<grid, 256, 0, s>>>(stage, npos, stride, bin_of_pos, perm_inv, thr, orow, nbins, bitmap, words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, int32_t n_frames,
+                           float* out, cudaStream_t s) {
+  if (n_frames <= 0 || npix <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((npix + 255) / 256), (unsigned)n_frames);
+  k_unstage<<<grid, 256, 0, s>>>(stage, stride, pos_of, npix, out);
   return cudaGetLastError();
 }
 

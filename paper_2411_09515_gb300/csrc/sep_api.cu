@@ -45,6 +45,10 @@ sep_status upload(sep_ctx* ctx, T** dst, const T* src, size_t n) {
   return SEP_OK;
 }
 
+// Row stride of a frame's staged values: positions rounded up to 32 floats,
+// so every frame's row starts 128-byte aligned (vector loads).
+int64_t stage_stride(const sep_csr* csr) { return (csr->h.npos + 31) & ~(int64_t)31; }
+
 int64_t bitmap_words(int64_t npix) {
   int64_t w = (npix + 31) / 32;
   return (w + 7) & ~(int64_t)7;   // 32-byte multiple: vector loads per frame stay aligned
@@ -216,7 +220,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.w = csr->d_w;
   a.stage = stage;
   a.perm_inv = csr->d_perm_inv;
-  a.npos = csr->h.npos;
+  a.npos = stage_stride(csr);
   a.nbins = csr->h.nbins;
   a.n_frames = n_frames;
   a.frames_per_cta = frames_per_cta(ctx, n_frames, csr->h.nbins);
@@ -240,14 +244,14 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
 }
 
 // Correction + staging of n frames (contiguous at `frames`, or listed in
-// fptr) into stage [n][npos].
+// fptr) into stage [n][stage_stride].
 cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames,
                           const uint64_t* fptr, int32_t dtype, int32_t n, float* stage, cudaStream_t s) {
   sep::StageArgs g;
   g.frames = frames;
   g.fptr = fptr;
   g.npix = csr->npix;
-  g.npos = csr->h.npos;
+  g.npos = stage_stride(csr);
   g.rows = csr->h.rows;
   g.cols = csr->h.cols;
   g.tiles_x = csr->h.tiles_x;
@@ -515,13 +519,35 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
   if (n_frames > 0 && (!mean_dev || !sigma_dev || !count_dev)) return fail(ctx, SEP_ERR_ARG, "NULL output");
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
-  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
+  if ((st = ensure_stage(ctx, stage_stride(csr) * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, bounds_dev,
                               iters_dev, nullptr);
   cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
   if (e == cudaSuccess) e = enqueue_clip(ctx, csr, a, params->precision, 0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "integrate_clip launch");
+  return SEP_OK;
+}
+
+sep_status sep_correct(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
+                       int32_t dtype, int32_t n_frames, float* out_dev, sep_stream stream) {
+  sep_params p{};
+  p.n_iter = 0;
+  p.k_clip = 1.0f;
+  p.k_pick = 0.0f;
+  p.patch = 1;
+  p.min_count = 1;
+  p.precision = SEP_PREC_DWORD;
+  sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, &p);
+  if (st != SEP_OK) return st;
+  if (n_frames > 0 && !out_dev) return fail(ctx, SEP_ERR_ARG, "NULL output");
+  if (n_frames == 0) return SEP_OK;
+  if ((st = ensure_stage(ctx, stage_stride(csr) * n_frames)) != SEP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
+  if (e == cudaSuccess)
+    e = sep::launch_unstage(ctx->d_stage, stage_stride(csr), csr->d_pos_of, csr->npix, n_frames, out_dev, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "correct launch");
   return SEP_OK;
 }
 
@@ -537,7 +563,7 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
     return fail(ctx, SEP_ERR_ARG, "NULL output");
   if ((st = check_bin_fits(ctx, csr)) != SEP_OK) return st;
   if (n_frames == 0) return SEP_OK;
-  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
+  if ((st = ensure_stage(ctx, stage_stride(csr) * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
                               nullptr, nullptr);
@@ -642,7 +668,7 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   if ((st = ensure_scratch(ctx, words * n_frames, (int64_t)n_frames * csr->h.nbins,
                            sep::consumer_scratch_words(n_frames, words, kept_capacity))) != SEP_OK)
     return st;
-  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) return st;
+  if ((st = ensure_stage(ctx, stage_stride(csr) * n_frames)) != SEP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
@@ -651,13 +677,13 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
     p.stage = ctx->d_stage;
     p.pos_of = csr->d_pos_of;
-    p.npos = csr->h.npos;
+    p.npos = stage_stride(csr);
     cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
     if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
     if (e == cudaSuccess)
       e = enqueue_clip(ctx, csr, a, params->precision, mode, s);
     if (e == cudaSuccess)
-      e = sep::launch_mark_pos(ctx->d_stage, csr->h.npos, csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, nullptr,
+      e = sep::launch_mark_pos(ctx->d_stage, csr->h.npos, stage_stride(csr), csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, nullptr,
                                csr->h.nbins, n_frames, ctx->d_bitmap, words, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
@@ -803,7 +829,7 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   cudaEventCreate(&e1);
   float best = 1e30f;
   int best_i = -1;
-  if ((st = ensure_stage(ctx, csr->h.npos * n_frames)) != SEP_OK) {
+  if ((st = ensure_stage(ctx, stage_stride(csr) * n_frames)) != SEP_OK) {
     cudaFree(d_out);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -929,7 +955,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
     aux_off[d] = aux_total;
     aux_total += sep::consumer_scratch_words((int32_t)m, words[d], kept_capacity);
     soff[d] = stage_total;
-    stage_total += m * csrs[d]->h.npos;
+    stage_total += m * stage_stride(csrs[d]);
   }
   if ((st = ensure_scratch(ctx, bm_total, thr_total, aux_total)) != SEP_OK) return st;
   if ((st = ensure_stage(ctx, stage_total)) != SEP_OK) return st;
@@ -979,12 +1005,12 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       pa.orow = orow;
       pa.stage = stage;
       pa.pos_of = csr->d_pos_of;
-      pa.npos = csr->h.npos;
+      pa.npos = stage_stride(csr);
       if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
       if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, nullptr, fptr, dtype, m, stage, sd);
       if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, params->precision, mode, sd, false);
       if (e == cudaSuccess)
-        e = sep::launch_mark_pos(stage, csr->h.npos, csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, orow,
+        e = sep::launch_mark_pos(stage, csr->h.npos, stage_stride(csr), csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, orow,
                                  csr->h.nbins, m, bm, words[d], sd);
       if (e == cudaSuccess)
         e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,

@@ -61,7 +61,7 @@ struct ClipArgs {
   const int32_t* grp;      // [nbins][4] class ends within a row
   const uint32_t* ent;     // packed entries: staging position + flags
   const float* w;          // per-entry weight c * norm (NORM variant)
-  const float* stage;      // staged values [n_frames][npos]
+  const float* stage;      // staged values [n_frames][npos] (npos here: the row stride)
   const int32_t* perm_inv; // [npos] pixel of each staging position
   int64_t npos;
   int32_t nbins, n_frames, frames_per_cta, cap;
@@ -129,9 +129,12 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
                               cudaStream_t s);
 // Kept-pixel bitmap from staged values: pixel perm_inv[p] is kept iff its
 // staged value exceeds the threshold of its centre bin.
-cudaError_t launch_mark_pos(const float* stage, int64_t npos, const int16_t* bin_of_pos, const int32_t* perm_inv,
+cudaError_t launch_mark_pos(const float* stage, int64_t npos, int64_t stride, const int16_t* bin_of_pos,
+                            const int32_t* perm_inv,
                             const float* thr, const int64_t* orow, int32_t nbins, int32_t n_frames, uint32_t* bitmap,
                             int64_t words, cudaStream_t s);
+cudaError_t launch_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, int32_t n_frames,
+                           float* out, cudaStream_t s);
 cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* thr, uint32_t* bitmap,
                         int64_t words, cudaStream_t s);
 // Ordered compaction of the kept-pixel bitmap (two launches; scratch holds

@@ -151,6 +151,52 @@ def test_correction_bit_exact_all_raw_codes():
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
+def test_staged_correction_bit_exact_all_raw_codes():
+    """Every 16-bit raw word through the staging kernel (the values the
+    integration reads), against the oracle's binary32 definition, bit for
+    bit, on four calibrations; masked pixels come back as NaN."""
+    rows, cols = 256, 256
+    det = synth.Detector("codes", rows, cols, dist_m=0.1, center_px=(128.3, 120.7), nbins=8, split=2)
+    raw = np.arange(rows * cols, dtype=np.uint32).astype(np.uint16)
+    frames = np.stack([raw, raw[::-1], np.roll(raw, 12345), np.roll(raw, -777)])
+    mask = np.zeros(rows * cols, np.uint8)
+    mask[::97] = 1
+    for seed in range(4):
+        rng = np.random.default_rng(100 + seed)
+        ped = np.stack([rng.normal(m, s, rows * cols) for m, s in ((1500, 50), (14000, 200), (15000, 200))])
+        gain = np.stack([40 * (1 + rng.uniform(-.02, .02, rows * cols)), -1.5 * (1 + rng.uniform(-.02, .02, rows * cols)),
+                         -0.1 * (1 + rng.uniform(-.02, .02, rows * cols))])
+        ped, gain = ped.astype(np.float32), gain.astype(np.float32)
+        sep = Separator.from_detector(det, mask=mask, calib=(ped, gain))
+        got = sep.correct(torch.from_numpy(frames.astype(np.int16)).cuda()).cpu().numpy()
+        for f in range(frames.shape[0]):
+            want = oracle.jf_photons(frames[f], ped, gain)
+            ok = mask == 0
+            assert np.array_equal(got[f][ok].view(np.uint32), want[ok].view(np.uint32))
+            assert np.all(np.isnan(got[f][~ok]))
+
+
+def test_staged_division_many_adc_values():
+    """Level-0 words with 256 different ADC values per pixel (every ADC value
+    reaches 1024 pixels): the staged quotient equals the oracle's binary32
+    division everywhere."""
+    rows, cols = 256, 256
+    det = synth.Detector("adc", rows, cols, dist_m=0.1, center_px=(128.3, 120.7), nbins=8, split=1)
+    rng = np.random.default_rng(55)
+    ped = np.stack([rng.normal(m, s, rows * cols) for m, s in ((1500, 50), (14000, 200), (15000, 200))]).astype(np.float32)
+    gain = np.stack([40 * (1 + rng.uniform(-.02, .02, rows * cols)), -1.5 * (1 + rng.uniform(-.02, .02, rows * cols)),
+                     -0.1 * (1 + rng.uniform(-.02, .02, rows * cols))]).astype(np.float32)
+    sep = Separator.from_detector(det, calib=(ped, gain))
+    i = np.arange(rows * cols)
+    for chunk in range(4):
+        f = np.arange(64 * chunk, 64 * chunk + 64)[:, None]
+        frames = ((i[None, :] * 7 + f * 64) % 16384).astype(np.uint16)   # gain code 0
+        got = sep.correct(torch.from_numpy(frames.astype(np.int16)).cuda()).cpu().numpy()
+        for k in range(frames.shape[0]):
+            want = oracle.jf_photons(frames[k], ped, gain)
+            assert np.array_equal(got[k].view(np.uint32), want.view(np.uint32)), (chunk, k)
+
+
 def test_edge_cases():
     det = synth.Detector("e", 40, 50, dist_m=0.05, center_px=(20.3, 18.7), nbins=30, split=2, unit=synth.UNIT_R_MM)
     mask = np.zeros(det.npix, np.uint8)
