@@ -364,6 +364,23 @@ sep_status sep_surrogate_train(sep_model* model, const float* x_dev, const float
  * surrogate. */
 sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
 
+/* The whole path from host memory to host memory, pipelined: the batch is
+ * cut into chunks of chunk_frames frames (0 = 64); chunk c+1 is copied in
+ * while chunk c is processed (sep_process_batch on device buffers owned by
+ * the context) and chunk c-1's results are copied out, on three streams.
+ * Host arrays are as sep_process_batch's device arrays (frames_host
+ * [n_frames][npix], mean/sigma/count [n_frames][nbins], idx/val
+ * [n_frames][kept_capacity], n_kept [n_frames], peaks [n_frames][peak_capacity],
+ * n_peaks [n_frames]); they should be pinned (cudaHostAlloc / torch
+ * pin_memory) for the copies to overlap, and must stay valid until `stream`
+ * completes: the call returns once everything is enqueued, with the work
+ * ordered before any later work on `stream`. */
+sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_host,
+                            int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_host,
+                            float* sigma_host, int32_t* count_host, int32_t* idx_host, float* val_host,
+                            int64_t kept_capacity, int32_t* n_kept_host, sep_peak* peaks_host,
+                            int64_t peak_capacity, int32_t* n_peaks_host, int32_t chunk_frames, sep_stream stream);
+
 /* Corrected frames (Section 1.2 and Eq. 1): out_dev [n_frames][npix] float32
  * receives RN32(RN32(adc - ped[g]) / gain[g]) (raw Jungfrau words, dtype
  * SEP_DTYPE_U16_JF) or the float32 input, divided by the norm when the

@@ -231,18 +231,34 @@ class Separator:
                             peak_capacity, o["n_peaks"], int(use_graph), stream)
         return o
 
-    def process_host(self, frames_host, dev_frames, out, host_out, kept_capacity, peak_capacity, stream=None):
-        """End to end from host memory: copy the batch in (pinned host ->
-        device), run the path, copy the per-frame results back (counts,
-        background profiles, kept lists and peaks)."""
+    def alloc_host_outputs(self, F, kept_capacity, peak_capacity):
+        """Pinned host tensors for process_host."""
         t = self.torch
-        s = stream if stream is not None else t.cuda.current_stream()
-        with t.cuda.stream(s):
-            dev_frames.copy_(frames_host, non_blocking=True)
-            self.process_batch(dev_frames, kept_capacity, peak_capacity, out=out, stream=s)
-            for k, v in host_out.items():
-                v.copy_(out[k], non_blocking=True)
-        return host_out
+        kw = dict(pin_memory=True)
+        return {"mean": t.empty((F, self.nbins), dtype=t.float32, **kw),
+                "sigma": t.empty((F, self.nbins), dtype=t.float32, **kw),
+                "count": t.empty((F, self.nbins), dtype=t.int32, **kw),
+                "idx": t.empty((F, kept_capacity), dtype=t.int32, **kw),
+                "val": t.empty((F, kept_capacity), dtype=t.float32, **kw),
+                "n_kept": t.empty(F, dtype=t.int32, **kw),
+                "peaks": t.empty((F, peak_capacity, 6), dtype=t.int32, **kw),
+                "n_peaks": t.empty(F, dtype=t.int32, **kw)}
+
+    def process_host(self, frames_host, host_out, kept_capacity, peak_capacity, chunk_frames=0, stream=None):
+        """End to end from (pinned) host memory to host memory: the library
+        copies chunks in, runs the path and copies results out, overlapping
+        the copies with compute. Results are complete once `stream` (default:
+        the current stream) has been synchronised."""
+        if frames_host.is_cuda or not frames_host.is_contiguous():
+            raise ValueError("frames_host must be a contiguous host tensor")
+        if frames_host.numel() % self.npix:
+            raise ValueError("frames size is not a multiple of the detector's pixel count")
+        F = frames_host.numel() // self.npix
+        o = host_out
+        B.sep_process_host(self.ctx, self.csr, self.calib, frames_host, self._dtype(frames_host), F, self.params,
+                           o["mean"], o["sigma"], o["count"], o["idx"], o["val"], kept_capacity, o["n_kept"],
+                           o["peaks"], peak_capacity, o["n_peaks"], chunk_frames, stream)
+        return o
 
     def device_status(self, stream=None):
         return B.sep_get_device_status(self.ctx, stream)

@@ -32,7 +32,8 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_sparsify_noalloc", "sep_csr_set_plan", "sep_csr_get_plan", "sep_autotune", "sep_process_mixed",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
-           "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct"]
+           "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct",
+           "sep_process_host"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 
@@ -124,6 +125,8 @@ def lib():
     L.sep_csr_attach_model.argtypes = [_vp, _vp]
     L.sep_csr_staging.argtypes = [_vp, _vp, C.POINTER(C.c_int64)]
     L.sep_correct.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp]
+    L.sep_process_host.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
+                                   _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
     L.sep_surrogate_record.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp,
                                        _vp, _vp, _vp, _vp]
     L.sep_surrogate_prepare.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_int64), _vp]
@@ -419,3 +422,11 @@ def sep_csr_staging(csr):
 
 def sep_correct(ctx, csr, calib, frames, dtype, n_frames, out, stream=None):
     _check(ctx, lib().sep_correct(ctx, csr, calib, _ptr(frames), dtype, n_frames, _ptr(out), _stream(stream)))
+
+
+def sep_process_host(ctx, csr, calib, frames_host, dtype, n_frames, params, mean, sigma, count, idx, val,
+                     kept_capacity, n_kept, peaks, peak_capacity, n_peaks, chunk_frames=0, stream=None):
+    _check(ctx, lib().sep_process_host(ctx, csr, calib, _ptr(frames_host), dtype, n_frames, C.byref(params),
+                                       _ptr(mean), _ptr(sigma), _ptr(count), _ptr(idx), _ptr(val), kept_capacity,
+                                       _ptr(n_kept), _ptr(peaks), peak_capacity, _ptr(n_peaks), int(chunk_frames),
+                                       _stream(stream)))

@@ -351,6 +351,15 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
   if (ctx->d_stage) cudaFree(ctx->d_stage);
+  if (ctx->d_pipe) cudaFree(ctx->d_pipe);
+  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
+    if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+    if (ctx->ev_out[i]) cudaEventDestroy(ctx->ev_out[i]);
+  }
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   if (ctx->d_desc) cudaFree(ctx->d_desc);
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   for (int i = 1; i < 4; ++i) {
@@ -752,6 +761,99 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   return SEP_OK;
 }
 
+
+sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_host,
+                            int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_host,
+                            float* sigma_host, int32_t* count_host, int32_t* idx_host, float* val_host,
+                            int64_t kept_capacity, int32_t* n_kept_host, sep_peak* peaks_host,
+                            int64_t peak_capacity, int32_t* n_peaks_host, int32_t chunk_frames, sep_stream stream) {
+  sep_status st = check_common(ctx, csr, calib, frames_host, dtype, n_frames, params);
+  if (st != SEP_OK) return st;
+  if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
+  if (chunk_frames < 0) return fail(ctx, SEP_ERR_ARG, "chunk_frames < 0");
+  if (n_frames > 0 && (!mean_host || !sigma_host || !count_host || !n_kept_host || !n_peaks_host ||
+                       (kept_capacity > 0 && (!idx_host || !val_host)) || (peak_capacity > 0 && !peaks_host)))
+    return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  if (n_frames == 0) return SEP_OK;
+  const int32_t C = std::min(n_frames, chunk_frames > 0 ? chunk_frames : 64);
+  const int64_t B = csr->h.nbins, N = csr->npix;
+  const size_t px = dtype == SEP_DTYPE_U16_JF ? 2 : 4;
+  // one slot: frames, mean, sigma, count, idx, val, n_kept, peaks, n_peaks (256-byte aligned pieces)
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t sz[9] = {al(px * N * C), al(4 * B * C), al(4 * B * C), al(4 * B * C), al(4 * kept_capacity * C),
+                        al(4 * kept_capacity * C), al(4 * (size_t)C), al(sizeof(sep_peak) * peak_capacity * C),
+                        al(4 * (size_t)C)};
+  size_t slot = 0, off[9];
+  for (int i = 0; i < 9; ++i) {
+    off[i] = slot;
+    slot += sz[i];
+  }
+  if (2 * slot > ctx->pipe_len) {
+    if (ctx->d_pipe) cudaFree(ctx->d_pipe);
+    ctx->d_pipe = nullptr;
+    ctx->pipe_len = 0;
+    if (cudaMalloc((void**)&ctx->d_pipe, 2 * slot) != cudaSuccess)
+      return fail(ctx, SEP_ERR_OOM, "pipeline buffer allocation failed");
+    ctx->pipe_len = 2 * slot;
+  }
+  if (!ctx->s_in) {
+    SEP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    SEP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+      SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming));
+      SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
+    }
+    SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // the copy streams start after everything already on the caller's stream
+  SEP_CUDA(ctx, cudaEventRecord(ctx->ev_start, s));
+  SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
+  SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0));
+  const int32_t nch = (n_frames + C - 1) / C;
+  for (int32_t c = 0; c < nch; ++c) {
+    const int32_t f0 = c * C, m = std::min(C, n_frames - f0), k = c & 1;
+    unsigned char* base = ctx->d_pipe + (size_t)k * slot;
+    void* d_fr = base + off[0];
+    float* d_mean = reinterpret_cast<float*>(base + off[1]);
+    float* d_sigma = reinterpret_cast<float*>(base + off[2]);
+    int32_t* d_count = reinterpret_cast<int32_t*>(base + off[3]);
+    int32_t* d_idx = reinterpret_cast<int32_t*>(base + off[4]);
+    float* d_val = reinterpret_cast<float*>(base + off[5]);
+    int32_t* d_nk = reinterpret_cast<int32_t*>(base + off[6]);
+    sep_peak* d_pk = reinterpret_cast<sep_peak*>(base + off[7]);
+    int32_t* d_np = reinterpret_cast<int32_t*>(base + off[8]);
+    // slot k is free once chunk c-2's results have left it
+    if (c >= 2) SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_out[k], 0));
+    SEP_CUDA(ctx, cudaMemcpyAsync(d_fr, static_cast<const unsigned char*>(frames_host) + px * N * f0, px * N * m,
+                                  cudaMemcpyHostToDevice, ctx->s_in));
+    SEP_CUDA(ctx, cudaEventRecord(ctx->ev_in[k], ctx->s_in));
+    SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_in[k], 0));
+    st = sep_process_batch(ctx, csr, calib, d_fr, dtype, m, params, d_mean, d_sigma, d_count, d_idx, d_val,
+                           kept_capacity, d_nk, d_pk, peak_capacity, d_np, 1, stream);
+    if (st != SEP_OK) return st;
+    SEP_CUDA(ctx, cudaEventRecord(ctx->ev_done[k], s));
+    SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[k], 0));
+    auto out = [&](void* h, const void* d, size_t bytes) -> cudaError_t {
+      return bytes ? cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, ctx->s_out) : cudaSuccess;
+    };
+    cudaError_t e = out(mean_host + B * f0, d_mean, 4 * B * m);
+    if (e == cudaSuccess) e = out(sigma_host + B * f0, d_sigma, 4 * B * m);
+    if (e == cudaSuccess) e = out(count_host + B * f0, d_count, 4 * B * m);
+    if (e == cudaSuccess && kept_capacity > 0) e = out(idx_host + kept_capacity * f0, d_idx, 4 * kept_capacity * m);
+    if (e == cudaSuccess && kept_capacity > 0) e = out(val_host + kept_capacity * f0, d_val, 4 * kept_capacity * m);
+    if (e == cudaSuccess) e = out(n_kept_host + f0, d_nk, 4 * (size_t)m);
+    if (e == cudaSuccess && peak_capacity > 0)
+      e = out(peaks_host + peak_capacity * f0, d_pk, sizeof(sep_peak) * peak_capacity * m);
+    if (e == cudaSuccess) e = out(n_peaks_host + f0, d_np, 4 * (size_t)m);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out[k], ctx->s_out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "process_host copy out");
+  }
+  // the caller's stream waits for the last copies
+  SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_out[(nch - 1) & 1], 0));
+  return SEP_OK;
+}
 
 sep_status sep_csr_set_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds,
                             const int32_t* tpb) {

@@ -294,3 +294,29 @@ def test_autotune_picks_a_plan_and_caches_it(jf_small, tmp_path):
     sig = oracle.jf_photons(fr[0], cal[0], cal[1])
     bnd = sep2.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
     check_frame(det, W, sig, o, 0, kcap=det.npix // 4, bounds=bnd[0])
+
+
+def test_process_host_pipeline_equals_device_batch(jf_small):
+    """Host-to-host pipelined path (chunks of 2, ragged last chunk) returns
+    exactly what the device batch returns."""
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal)
+    kcap, pcap = det.npix // 4, 20000
+    frames = np.ascontiguousarray(fr[:5])
+    o_dev, _ = run_batch(sep, frames, kcap, pcap)
+    host = torch.from_numpy(frames.view(np.int16)).pin_memory()
+    ho = sep.alloc_host_outputs(frames.shape[0], kcap, pcap)
+    for chunk in (2, 64):
+        for v in ho.values():
+            v.zero_()
+        sep.process_host(host, ho, kcap, pcap, chunk_frames=chunk)
+        torch.cuda.synchronize()
+        for k in ("mean", "sigma", "count", "n_kept", "n_peaks"):
+            assert np.array_equal(ho[k].numpy(), o_dev[k]), (chunk, k)
+        for f in range(frames.shape[0]):
+            n = int(o_dev["n_kept"][f])
+            assert np.array_equal(ho["idx"][f, :n].numpy(), o_dev["idx"][f, :n])
+            assert np.array_equal(ho["val"][f, :n].numpy(), o_dev["val"][f, :n])
+            p = int(o_dev["n_peaks"][f])
+            assert np.array_equal(ho["peaks"][f, :p].numpy(), o_dev["peaks"][f, :p])
+    assert sep.device_status() == 0
