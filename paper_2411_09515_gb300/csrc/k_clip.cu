@@ -13,15 +13,12 @@
 //   mu = K + A1 / Omega,  VV = B2 - 2 (mu - K) B1 + (mu - K)^2 OO  (Eq. 11),
 //   sigma = sqrt(VV / OO)  (Eq. 13),
 // which is exact algebra; with K close to mu the correction terms are small,
-// so one pass per moment evaluation suffices. The gather itself accumulates
-// the sums of the full set about 0, which serve as the first pass whenever
-// that shift is adequate (|mu| <= 2 sigma).
+// so one pass per moment evaluation suffices. The first pass takes the full
+// set about 0 and is kept whenever that shift is adequate (|mu| <= 2 sigma).
 //
 // Rejection is cumulative and symmetric about the current mean, so the set
 // after t steps is every entry whose value lies in an interval [L_t, H_t]:
-// no per-entry flag is kept. Each pass also finds the smallest and largest
-// member of the set it measured; when both lie inside the next interval, the
-// next pass could discard nothing and the loop ends without it. Row entries
+// no per-entry flag is kept. Row entries
 // are grouped by coefficient class (a group shares one weight), so per-entry
 // work is unweighted and the class weight is applied once per thread per
 // pass.
@@ -62,6 +59,11 @@ struct Acc {
     } else {
       s = __fadd_rn(s, x);
     }
+  }
+  // += x * y: compensated product in KAHAN, one fused multiply-add otherwise
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    if (KAHAN) add(__fmul_rn(x, y));
+    else s = __fmaf_rn(x, y, s);
   }
   __device__ __forceinline__ float val() const { return KAHAN ? __fsub_rn(s, c) : s; }
 };
@@ -310,7 +312,7 @@ __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts,
             const float d = __fsub_rn(xs[j], Kf);
             ++cnt;
             a1.add(d);
-            a2.add(__fmul_rn(d, d));
+            a2.add_prod(d, d);
           }
         }
       }
@@ -341,7 +343,7 @@ __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts,
           const float d = __fsub_rn(xs[j], Kf);
           ++cnt;
           a1.add(d);
-          a2.add(__fmul_rn(d, d));
+          a2.add_prod(d, d);
         }
       }
     }
@@ -366,7 +368,7 @@ __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts,
           a1.add(__fmul_rn(w, d));
           oo.add(w2);
           b1.add(w2d);
-          b2.add(__fmul_rn(w2d, d));
+          b2.add_prod(w2d, d);
         }
       }
     }
@@ -408,17 +410,14 @@ __device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)
 }
 
 // One step of the clip loop (lane 0 of warp 0) after a pass measured the set
-// S' = S ∩ [Ln, Hn] (count n_set, sums h/l about Kf, smallest and largest
-// member e_lo, e_hi). S' == S means nothing was discarded: the loop ends
-// with the moments of S. Otherwise S' becomes the set, its moments are
-// evaluated and the next interval is the intersection with
-// [mu - k sd, mu + k sd] (Eq. 19, cumulative); when every member of S' lies
-// inside it, the next pass would discard nothing and the loop ends here.
+// S' = S ∩ [Ln, Hn] (count n_set, sums h/l about Kf). S' == S means nothing
+// was discarded: the loop ends with the moments of S. Otherwise S' becomes
+// the set, its moments are evaluated and the next interval is the
+// intersection with [mu - k sd, mu + k sd] (Eq. 19, cumulative).
 // (have_moments: st already holds the moments of S'.)
 template <int PREC>
-__device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&h)[6], const float (&l)[6],
-                                          float e_lo, float e_hi, float Kf, float Ln, float Hn, int n_iter,
-                                          float k, bool have_moments = false) {
+__device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&h)[6], const float (&l)[6], float Kf,
+                                          float Ln, float Hn, int n_iter, float k, bool have_moments = false) {
   if (st.steps >= 0 && n_set == st.n_cur) {
     st.done = 1;
     return;
@@ -434,10 +433,6 @@ __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&
   }
   float L2 = Ln, H2 = Hn;
   clip_bounds<PREC>(st, k, L2, H2);
-  if (e_lo >= L2 && e_hi <= H2) {
-    st.done = 1;
-    return;
-  }
   st.Ln = L2;
   st.Hn = H2;
   st.Kf = choose_shift(st.mu_hi, st.sd);
@@ -482,98 +477,6 @@ struct SurrShared {
   int accepted;
 };
 
-// Per-thread sums of the first pass (the full set, shift 0), accumulated
-// while the values are gathered, in the order and layout of pass_sums.
-template <int MODE, bool KAHAN>
-struct FirstPass {
-  static constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
-  float ss[NF], cc[NF];
-  uint32_t ci[NI];
-  Ext<1> ex;
-  int cur = 0;            // MODE_CLASS: class of the entries being accumulated
-  int cur_end = 0;        // its end in the row (ge[cur]; a scalar, so ge stays in registers)
-  uint32_t cnt = 0;
-  Acc<KAHAN> a1, a2;      // MODE_CLASS / MODE_UNIT
-  Acc<KAHAN> om, oo, b1;  // MODE_ENTRY (a1 = sum w d, a2 = sum w^2 d^2)
-  __device__ __forceinline__ FirstPass(const int (&ge)[4]) {
-#pragma unroll
-    for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NI; ++i) ci[i] = 0u;
-    cur_end = ge[0];
-  }
-  __device__ __forceinline__ static int class_end(const int (&ge)[4], int c) {
-    return c == 0 ? ge[0] : (c == 1 ? ge[1] : (c == 2 ? ge[2] : ge[3]));
-  }
-  // add the current class (weight w = 1 - cur / 4) to the totals
-  __device__ __forceinline__ void flush_class() {
-    const float w = 1.0f - 0.25f * (float)cur, w2 = w * w;
-    const float s1 = a1.val(), s2 = a2.val();
-    if (cur >> 1) ci[1] += cnt << (16 * (cur & 1));
-    else ci[0] += cnt << (16 * (cur & 1));
-    if (KAHAN) {
-      Acc<true> t0, t1, t2;
-      t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
-      t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
-      t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
-    } else {
-      ss[0] = fmaf(w, s1, ss[0]);
-      ss[1] = fmaf(w2, s1, ss[1]);
-      ss[2] = fmaf(w2, s2, ss[2]);
-    }
-    cnt = 0;
-    a1 = Acc<KAHAN>();
-    a2 = Acc<KAHAN>();
-  }
-  // the value of entry e (each thread's entries ascend)
-  __device__ __forceinline__ void add1(float v, int e, const int (&ge)[4], const float* wts) {
-    if (MODE == MODE_CLASS) {
-      while (e >= cur_end && cur < 4) {
-        flush_class();
-        ++cur;
-        cur_end = cur < 4 ? class_end(ge, cur) : 0x7fffffff;
-      }
-      if (cur >= 4) return;   // weight-0 carriers
-    } else if (MODE == MODE_UNIT) {
-      if (e >= ge[0]) return;
-    }
-    if (MODE == MODE_ENTRY) {
-      const float w = wts[e];
-      if (w != 0.0f && v >= -FLT_MAX && v <= FLT_MAX) {
-        const float w2 = __fmul_rn(w, w);
-        const float w2d = __fmul_rn(w2, v);
-        ++cnt;
-        om.add(w);
-        a1.add(__fmul_rn(w, v));
-        oo.add(w2);
-        b1.add(w2d);
-        a2.add(__fmul_rn(w2d, v));
-        ex.add(v, -FLT_MAX, FLT_MAX);
-      }
-    } else if (v >= -FLT_MAX && v <= FLT_MAX) {
-      ++cnt;
-      a1.add(v);
-      a2.add(__fmul_rn(v, v));
-      ex.add(v, -FLT_MAX, FLT_MAX);
-    }
-  }
-  __device__ __forceinline__ void finish() {
-    if (MODE == MODE_CLASS) {
-      while (cur < 4) {
-        flush_class();
-        ++cur;
-      }
-    } else if (MODE == MODE_UNIT) {
-      ci[0] = cnt;
-      ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
-    } else {
-      ci[0] = cnt;
-      ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
-      ss[3] = b1.s; cc[3] = b1.c; ss[4] = a2.s; cc[4] = a2.c;
-    }
-  }
-};
-
 // Registers are capped so that 1024 threads stay resident per SM (the
 // serial step of one CTA overlaps the passes of the others).
 template <int MODE, int PREC, int kThreads, int SURR>
@@ -616,48 +519,43 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
     const float* vf = a.stage + (int64_t)f * a.npos;   // this frame's staged values
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
     if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
-    // ------------- gather + correct, with the first pass (full set, shift 0) -------------
-    FirstPass<MODE, KAHAN> fp(ge);
+    // ------------- gather, then the first pass (full set, shift 0) -------------
+    float ss0[NF], cc0[NF];
+    uint32_t ci0[NI];
+    Ext<0> ex0;
     {
       // Stage the row's packed entries into the value slots (16-byte
-      // cp.async copies), then gather with consecutive threads on
-      // consecutive entries: inside a coefficient group the entries ascend
-      // in staging position, so a warp's loads fall on short contiguous runs.
-      // Slot e is read (entry) and then written (value) by the same thread
-      // only, so one barrier after the staging suffices.
-      {
-        const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
-        for (int q = tid; q < nq; q += kThreads)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
-                       : "memory");
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-      }
+      // cp.async copies); then every thread replaces each of its entries by
+      // the staged value it addresses with a 4-byte cp.async: all of a
+      // thread's loads are in flight at once and land in shared memory
+      // without passing through registers. Inside a coefficient group the
+      // entries ascend in staging position, so a warp's loads fall on short
+      // contiguous runs. Slot e is read (entry) and then overwritten (value)
+      // by the same thread.
+      const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
+      for (int q = tid; q < nq; q += kThreads)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
+                     : "memory");
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
       const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
-      constexpr int U = 8;   // entries per thread in flight
-      for (int e0 = tid; e0 < n; e0 += U * kThreads) {
-        float xv[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * kThreads;
-          const uint32_t u = e < n ? ents[e] : kPad;
-          // padding: NaN lies outside every interval
-          xv[k] = (u & kPad) ? __int_as_float(0x7fc00000) : __ldg(vf + (u & kColMask));
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * kThreads;
-          if (e >= n) break;
-          vals[e] = xv[k];
-          fp.add1(xv[k], e, ge, wts);
+      for (int e = tid; e < n; e += kThreads) {
+        const uint32_t u = ents[e];
+        if (u & kPad) {
+          vals[e] = __int_as_float(0x7fc00000);   // NaN: outside every interval
+        } else {
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + 4u * (unsigned)e),
+                       "l"(vf + (u & kColMask))
+                       : "memory");
         }
       }
-      fp.finish();
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+      pass_sums<MODE, KAHAN, 0, kThreads>(vals4, wts, ge, -FLT_MAX, FLT_MAX, 0.0f, ex0, ss0, cc0, ci0);
     }
     {
-      warp_ext<1, kWarps>(fp.ex, red_x);
       float thi, tlo;
-      block_sum<NF, NI, PREC, kWarps>(fp.ss, fp.cc, fp.ci, red_s, red_c, red_i, thi, tlo);
+      block_sum<NF, NI, PREC, kWarps>(ss0, cc0, ci0, red_s, red_c, red_i, thi, tlo);
       if (warp == 0) {
         float th[NF + NI], tl[NF + NI];
 #pragma unroll
@@ -666,9 +564,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           tl[v] = __shfl_sync(0xffffffffu, tlo, v);
         }
         if (lane == 0) {
-          float n_set, h[6], l[6], e[4];
+          float n_set, h[6], l[6];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          cta_ext<1, kWarps>(red_x, e);
           st.Ln = -FLT_MAX;
           st.Hn = FLT_MAX;
           st.L = -FLT_MAX;
@@ -686,8 +583,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
             sv.accepted = 0;
           }
           if (choose_shift(st.mu_hi, st.sd) == 0.0f) {
-            // the shift 0 suits this set: the gather was the first pass
-            clip_step<PREC>(st, n_set, h, l, e[1], e[2], 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true);
+            // the shift 0 suits this set: this was the first pass
+            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true);
           } else {
             // cancellation about 0 is too large: the first pass runs again about the mean
             st.Kf = st.mu_hi;
@@ -851,9 +748,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
       const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
       float ss[NF], cc[NF];
       uint32_t ci[NI];
-      Ext<1> ex;
-      pass_sums<MODE, KAHAN, 1, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
-      warp_ext<1, kWarps>(ex, red_x);
+      Ext<0> ex;
+      pass_sums<MODE, KAHAN, 0, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
       float thi, tlo;
       block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
       if (warp == 0) {
@@ -866,8 +762,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         if (lane == 0) {
           float n_set, h[6], l[6], e[4];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          cta_ext<1, kWarps>(red_x, e);
-          clip_step<PREC>(st, n_set, h, l, e[1], e[2], Kf, Ln, Hn, a.n_iter, a.k_clip);
+          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip);
         }
       }
       __syncthreads();
