@@ -165,10 +165,10 @@ sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64
                         int32_t* max_row, double* range);
 /* Staging order: every pixel with at least one matrix entry has a staging
  * position (its corrected value is written there once per frame and the
- * integration reads it from there). Pixels are grouped by tiles of 8 rows x
- * 128 columns (tiles in row-major order); inside a tile, by centre bin, then
- * pixel index. perm_inv [npos] receives the pixel of each position (may be
- * NULL); *npos the number of positions. */
+ * integration reads it from there). Pixels are grouped by tiles of 32 rows x
+ * 32 columns (tiles in row-major order); inside a tile, by centre bin, then
+ * radius of the pixel centre, then pixel index. perm_inv [npos] receives the
+ * pixel of each position (may be NULL); *npos the number of positions. */
 sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos);
 /* Host copies for inspection (any pointer may be NULL):
  * rowptr [nbins+1], col [nnz] (-1 for padding), coef [nnz] (c_{i,r}; 0 for

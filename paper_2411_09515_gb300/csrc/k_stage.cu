@@ -3,7 +3,7 @@
 // its staging position, where the clip kernel reads it.
 //
 // One CTA per staging tile (kTileH x kTileW pixels of the image) and group
-// of frames. A warp reads one tile row: each thread four consecutive pixels
+// of frames. Threads read tile rows: each thread four consecutive pixels
 // (one vector load where the row is aligned), two frames per step; the
 // tile's values are placed in shared memory at their rank inside the tile,
 // then written out as one contiguous run. Each value is the same IEEE sequence as pixel_value():
@@ -17,10 +17,10 @@
 namespace sep {
 namespace {
 
-constexpr int kStageThreads = 256;
 constexpr int kTilePix = kTileH * kTileW;
-constexpr int kPerThread = kTilePix / kStageThreads;   // consecutive pixels of one row
-static_assert(kPerThread == 4 && kTileW % (4 * 32) == 0, "one warp covers a tile row, 4 pixels a thread");
+constexpr int kStageThreads = kTilePix / 4;   // 4 consecutive pixels of one row a thread
+constexpr int kRowThreads = kTileW / 4;       // threads covering one tile row
+static_assert(kTileW % 4 == 0 && kStageThreads % 32 == 0 && kStageThreads <= 1024, "tile shape");
 
 // Four consecutive raw words / values of one frame (VEC: one aligned vector load).
 template <int DT, bool VEC>
@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
   const int tid = threadIdx.x;
   const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
   if (cnt == 0) return;
-  const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / 32;
-  const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % 32);
+  const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / kRowThreads;
+  const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % kRowThreads);
   const int64_t p = r * a.cols + c;    // first of this thread's 4 pixels
   bool in[4];
   int rank[4];

@@ -97,6 +97,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   std::vector<uint8_t> pk((size_t)npix * maxe, 0);
   std::vector<uint8_t> pn((size_t)npix, 0);
   std::vector<int32_t> bop((size_t)npix, -1);
+  std::vector<float> xcen((size_t)npix, 0.0f);   // radial value of the pixel centre (staging order)
 #pragma omp parallel for schedule(static)
   for (int64_t row = 0; row < rows; ++row) {
     for (int64_t col = 0; col < cols; ++col) {
@@ -106,6 +107,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       double xc = radial(g, row, col, 0.5, 0.5);
       int32_t bc = xc < lo ? 0 : (xc > hi ? B - 1 : bin_index(xc, lo, hi, B));
       bop[i] = bc;
+      xcen[i] = (float)xc;
       int32_t sb[4];
       int m = 0;
       for (int a = 0; a < s; ++a)
@@ -196,9 +198,9 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   }
   // Staging order of the pixel values. The clip kernel gathers each bin's
   // values from a staged copy of the frame in which pixels are grouped by
-  // tiles of kTileH x kTileW and, inside a tile, by centre bin (then pixel
-  // index): a bin's entries then read short contiguous runs (one per tile it
-  // crosses) instead of single pixels scattered over the image. Only pixels
+  // tiles of kTileH x kTileW and, inside a tile, by centre bin (then radius,
+  // then pixel index): a bin's entries then read short contiguous runs (one
+  // per tile it crosses) instead of single pixels scattered over the image. Only pixels
   // with at least one entry are staged. Entries address their pixel by its
   // staging position; each coefficient group is re-sorted by position.
   {
@@ -210,7 +212,8 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     out->perm_inv.clear();
     out->perm_inv.reserve((size_t)npix);
     std::vector<int32_t> pos_of((size_t)npix, -1);
-    std::vector<std::pair<int32_t, int32_t>> tile_px;
+    struct Px { int32_t bin; float x; int32_t i; };
+    std::vector<Px> tile_px;
     tile_px.reserve((size_t)kTileH * kTileW);
     for (int64_t t = 0; t < tx * ty; ++t) {
       const int64_t r0 = (t / tx) * kTileH, c0 = (t % tx) * kTileW;
@@ -218,12 +221,18 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       for (int64_t r = r0; r < std::min<int64_t>(r0 + kTileH, rows); ++r)
         for (int64_t c = c0; c < std::min<int64_t>(c0 + kTileW, cols); ++c) {
           const int64_t i = r * cols + c;
-          if (pn[i] > 0) tile_px.emplace_back(bop[i], (int32_t)i);
+          if (pn[i] > 0) tile_px.push_back({bop[i], xcen[i], (int32_t)i});
         }
-      std::sort(tile_px.begin(), tile_px.end());
+      // by centre bin, then radius: the pixels of a bin that spill into the
+      // next (previous) bin sit at the end (start) of its run, next to that bin
+      std::sort(tile_px.begin(), tile_px.end(), [](const Px& a, const Px& b) {
+        if (a.bin != b.bin) return a.bin < b.bin;
+        if (a.x != b.x) return a.x < b.x;
+        return a.i < b.i;
+      });
       out->tile_base[t] = (int32_t)out->perm_inv.size();
       for (size_t k = 0; k < tile_px.size(); ++k) {
-        const int32_t i = tile_px[k].second;
+        const int32_t i = tile_px[k].i;
         out->tile_rank[i] = (int16_t)k;
         pos_of[i] = (int32_t)out->perm_inv.size();
         out->perm_inv.push_back(i);

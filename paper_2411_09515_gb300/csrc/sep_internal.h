@@ -49,7 +49,7 @@ struct HostCsr {
   std::vector<int32_t> tile_base;   // [tiles + 1] first position of each tile
 };
 
-constexpr int kTileH = 8, kTileW = 128;   // staging tiles (rows x columns)
+constexpr int kTileH = 32, kTileW = 32;   // staging tiles (rows x columns)
 
 // Returns an empty string on success, else the reason.
 std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const float* norm, HostCsr* out);

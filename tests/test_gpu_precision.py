@@ -7,7 +7,8 @@ the bins whose clip decisions are outside the 1e-5 band, kept-pixel
 mismatches outside the band, and the peak centroid error in pixels. The
 default mode must meet the parity tolerances; the others are reported.
 Set SEP_PRECISION_REPORT=path to write the numbers as JSON, and
-SEP_PRECISION_FULL=1 to run the full-size study (256 Jungfrau-4M frames).
+SEP_PRECISION_FULL=1 to run the full-size study (Jungfrau-4M frames, 256 or
+SEP_PRECISION_FRAMES).
 """
 import json
 import os
@@ -99,7 +100,8 @@ def test_precision_modes_small():
 @pytest.mark.slow
 @pytest.mark.skipif(os.environ.get("SEP_PRECISION_FULL") != "1", reason="full-size study on request")
 def test_precision_modes_jf4m_256():
-    r = study(synth.det_jf4m(), 256)
+    # SEP_PRECISION_FRAMES bounds the oracle's share of the run (default 256)
+    r = study(synth.det_jf4m(), int(os.environ.get("SEP_PRECISION_FRAMES", "256")))
     _emit(r)
     for name in ("dword", "fp64merge"):
         assert r[name]["mean_rel_err_max"] < 1e-5 and r[name]["sigma_rel_err_max"] < 1e-5

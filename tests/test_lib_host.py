@@ -59,6 +59,9 @@ def test_invalid_geometry_rejected(bad):
     assert e.value.status == B.SEP_ERR_ARG
 
 
+TILE = (32, 32)   # staging tile (rows, columns) of the library
+
+
 def compare_with_oracle(det, mask=None):
     csr = B.sep_build_csr(None, geom_of(det), mask)
     try:
@@ -77,15 +80,21 @@ def compare_with_oracle(det, mask=None):
     got = sorted(zip(ex["col"][nz].tolist(), rows[nz].tolist(), ex["coef"][nz].astype(np.float64).tolist()))
     want = sorted(zip(W.pix.tolist(), W.bin.tolist(), W.c.tolist()))
     assert got == want
-    # staging order: a permutation of the pixels with entries, tiles of
-    # 8 x 128 in row-major order, by centre bin then pixel inside a tile
+    # staging order: a permutation of the pixels with entries, tiles in
+    # row-major order, by centre bin inside a tile (then radius)
     used = np.unique(ex["col"][ex["col"] >= 0])
     assert np.array_equal(np.sort(perm_inv), used)
     r, cl = perm_inv // det.cols, perm_inv % det.cols
-    tiles_x = (det.cols + 127) // 128
-    key = np.stack([(r // 8) * tiles_x + cl // 128, W.bin_of_pixel[perm_inv], perm_inv], axis=1)
-    order = np.lexsort(key.T[::-1])
-    assert np.array_equal(order, np.arange(perm_inv.size))
+    th, tw = TILE
+    tiles_x = (det.cols + tw - 1) // tw
+    tile = (r // th) * tiles_x + cl // tw
+    key = tile.astype(np.int64) * 100000 + W.bin_of_pixel[perm_inv]
+    assert np.all(np.diff(key) >= 0)
+    # inside a (tile, bin) group the radius grows
+    yy, xx = r + 0.5 - det.center_px[1], cl + 0.5 - det.center_px[0]
+    rad = np.hypot(yy, xx)
+    same = np.diff(key) == 0
+    assert np.all(np.diff(rad)[same] >= -1e-3)   # float32 keys: ties within a rounding
     pos_of = np.full(det.rows * det.cols, -1, np.int64)
     pos_of[perm_inv] = np.arange(perm_inv.size)
     # within a row: coefficient groups, largest first, staging positions ascending in a group
