@@ -389,7 +389,8 @@ def run_mixed(args):
     for d in range(3):
         sample = torch.stack(per[d][:8])
         tuned[d] = {"ms": seps[d].autotune(sample), **seps[d].get_plan()}
-    kcap, pcap = max(args.kept_capacity, 1 << 20), args.peak_capacity   # 16M frames keep ~0.7 M pixels
+    # 16M frames keep ~0.7 M pixels and carry up to a few thousand peaks
+    kcap, pcap = max(args.kept_capacity, 1 << 20), max(args.peak_capacity, 1 << 15)
     for _ in range(args.warmup):
         out = process_mixed(seps, frames, kcap, pcap)
     torch.cuda.synchronize()
@@ -420,6 +421,8 @@ def run_mixed(args):
             "unit": "frames/s", "ms_per_step": round(ms, 3), "steps": args.steps, "warmup": args.warmup,
             "frames_per_step": n, "gbs_input": round(byts / (ms * 1e-3) / 1e9, 1), "per_size_frames_s": per_size,
             "plans": tuned, "dtype": "f32", "data": "synthetic", "device_status": seps[0].device_status(),
+            "max_kept_per_frame": int(out["n_kept"].max().item()), "max_peaks_per_frame": int(out["n_peaks"].max().item()),
+            "capacities": [kcap, pcap],
             "config": {"workload": "mixed f32 1M:4M:16M = 3:2:1, 600/1000/2000 bins, no split"}}
     print(json.dumps(line), flush=True)
 

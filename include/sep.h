@@ -367,14 +367,17 @@ sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
 /* The whole path from host memory to host memory, pipelined: the batch is
  * cut into chunks of chunk_frames frames (0 = 64); chunk c+1 is copied in
  * while chunk c is processed (sep_process_batch on device buffers owned by
- * the context) and chunk c-1's results are copied out, on three streams.
+ * the context, three chunk slots) and chunk c-1's results are copied out,
+ * on three streams.
  * Host arrays are as sep_process_batch's device arrays (frames_host
  * [n_frames][npix], mean/sigma/count [n_frames][nbins], idx/val
  * [n_frames][kept_capacity], n_kept [n_frames], peaks [n_frames][peak_capacity],
  * n_peaks [n_frames]); they should be pinned (cudaHostAlloc / torch
  * pin_memory) for the copies to overlap, and must stay valid until `stream`
  * completes: the call returns once everything is enqueued, with the work
- * ordered before any later work on `stream`. */
+ * ordered before any later work on `stream`. frames_host must hold its data
+ * when the call is made: the copy-in does not wait for earlier work on
+ * `stream`, so that consecutive calls overlap. */
 sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_host,
                             int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_host,
                             float* sigma_host, int32_t* count_host, int32_t* idx_host, float* val_host,

@@ -352,10 +352,12 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_aux) cudaFree(ctx->d_aux);
   if (ctx->d_stage) cudaFree(ctx->d_stage);
   if (ctx->d_pipe) cudaFree(ctx->d_pipe);
-  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  for (int j = 0; j < sep_ctx::kCopyStreams; ++j)
+    if (ctx->s_in[j]) cudaStreamDestroy(ctx->s_in[j]);
   if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
-  for (int i = 0; i < 2; ++i) {
-    if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
+  for (int i = 0; i < sep_ctx::kSlots; ++i) {
+    for (int j = 0; j < sep_ctx::kCopyStreams; ++j)
+      if (ctx->ev_in[i][j]) cudaEventDestroy(ctx->ev_in[i][j]);
     if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
     if (ctx->ev_out[i]) cudaEventDestroy(ctx->ev_out[i]);
   }
@@ -788,32 +790,33 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
     off[i] = slot;
     slot += sz[i];
   }
-  if (2 * slot > ctx->pipe_len) {
+  constexpr int NSL = sep_ctx::kSlots;
+  if (NSL * slot > ctx->pipe_len) {
     if (ctx->d_pipe) cudaFree(ctx->d_pipe);
     ctx->d_pipe = nullptr;
     ctx->pipe_len = 0;
-    if (cudaMalloc((void**)&ctx->d_pipe, 2 * slot) != cudaSuccess)
+    if (cudaMalloc((void**)&ctx->d_pipe, NSL * slot) != cudaSuccess)
       return fail(ctx, SEP_ERR_OOM, "pipeline buffer allocation failed");
-    ctx->pipe_len = 2 * slot;
+    ctx->pipe_len = NSL * slot;
   }
-  if (!ctx->s_in) {
-    SEP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+  constexpr int NS = sep_ctx::kCopyStreams;
+  if (!ctx->s_out) {
+    for (int j = 0; j < NS; ++j) SEP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in[j], cudaStreamNonBlocking));
     SEP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; ++i) {
-      SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+    for (int i = 0; i < sep_ctx::kSlots; ++i) {
+      for (int j = 0; j < NS; ++j) SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i][j], cudaEventDisableTiming));
       SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming));
       SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
     }
     SEP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
   }
   cudaStream_t s = (cudaStream_t)stream;
-  // the copy streams start after everything already on the caller's stream
-  SEP_CUDA(ctx, cudaEventRecord(ctx->ev_start, s));
-  SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
-  SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_start, 0));
+  // Copy-in does not wait for earlier work on the caller's stream (the host
+  // input is ready when the call is made), only for its slot to be free:
+  // consecutive calls overlap their copies with each other's compute.
   const int32_t nch = (n_frames + C - 1) / C;
   for (int32_t c = 0; c < nch; ++c) {
-    const int32_t f0 = c * C, m = std::min(C, n_frames - f0), k = c & 1;
+    const int32_t f0 = c * C, m = std::min(C, n_frames - f0), k = c % NSL;
     unsigned char* base = ctx->d_pipe + (size_t)k * slot;
     void* d_fr = base + off[0];
     float* d_mean = reinterpret_cast<float*>(base + off[1]);
@@ -824,12 +827,20 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
     int32_t* d_nk = reinterpret_cast<int32_t*>(base + off[6]);
     sep_peak* d_pk = reinterpret_cast<sep_peak*>(base + off[7]);
     int32_t* d_np = reinterpret_cast<int32_t*>(base + off[8]);
-    // slot k is free once chunk c-2's results have left it
-    if (c >= 2) SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_out[k], 0));
-    SEP_CUDA(ctx, cudaMemcpyAsync(d_fr, static_cast<const unsigned char*>(frames_host) + px * N * f0, px * N * m,
-                                  cudaMemcpyHostToDevice, ctx->s_in));
-    SEP_CUDA(ctx, cudaEventRecord(ctx->ev_in[k], ctx->s_in));
-    SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_in[k], 0));
+    // slot k is free once its previous chunk's results have left it; the chunk's
+    // frames are copied in NS pieces on as many streams (copy engines)
+    const size_t bytes = px * N * m, piece = ((bytes + NS - 1) / NS + 255) & ~(size_t)255;
+    for (int j = 0; j < NS; ++j) {
+      const size_t o = (size_t)j * piece;
+      // (an event never recorded yet is no dependency)
+      SEP_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in[j], ctx->ev_out[k], 0));
+      if (o < bytes)
+        SEP_CUDA(ctx, cudaMemcpyAsync(static_cast<unsigned char*>(d_fr) + o,
+                                      static_cast<const unsigned char*>(frames_host) + px * N * f0 + o,
+                                      std::min(piece, bytes - o), cudaMemcpyHostToDevice, ctx->s_in[j]));
+      SEP_CUDA(ctx, cudaEventRecord(ctx->ev_in[k][j], ctx->s_in[j]));
+      SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_in[k][j], 0));
+    }
     st = sep_process_batch(ctx, csr, calib, d_fr, dtype, m, params, d_mean, d_sigma, d_count, d_idx, d_val,
                            kept_capacity, d_nk, d_pk, peak_capacity, d_np, 1, stream);
     if (st != SEP_OK) return st;
@@ -851,7 +862,7 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
     if (e != cudaSuccess) return cuda_fail(ctx, e, "process_host copy out");
   }
   // the caller's stream waits for the last copies
-  SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_out[(nch - 1) & 1], 0));
+  SEP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_out[(nch - 1) % NSL], 0));
   return SEP_OK;
 }
 
@@ -979,7 +990,7 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   if (cache_path) {
     FILE* fp = fopen(cache_path, "a");
     if (fp) {
-      fprintf(fp, "%s\t%d %d %d %d %d %d %d %d %.4f\n", key, w.nc, w.t[0], w.t[1], w.t[2], w.b[0], w.b[1], w.b[2],
+      fprintf(fp, "%s\t%d %d %d %d %d %d %d %d %.9g\n", key, w.nc, w.t[0], w.t[1], w.t[2], w.b[0], w.b[1], w.b[2],
               w.b[3], best);
       fclose(fp);
     }

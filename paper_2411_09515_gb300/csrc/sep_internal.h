@@ -183,11 +183,13 @@ struct sep_ctx {
   unsigned long long* d_surr = nullptr;   // surrogate counters: settled, fell back
   float* d_stage = nullptr;    // staged pixel values of the batch in flight
   size_t stage_len = 0;
-  // host pipeline (sep_process_host): two chunk slots of frames + outputs
+  // host pipeline (sep_process_host): chunk slots of frames + outputs
   unsigned char* d_pipe = nullptr;
   size_t pipe_len = 0;
-  cudaStream_t s_in = nullptr, s_out = nullptr;
-  cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {}, ev_start = nullptr;
+  static constexpr int kCopyStreams = 1;   // streams a chunk's copy-in is split over (more measured slower)
+  static constexpr int kSlots = 3;         // chunks in flight: copy-in, compute, copy-out
+  cudaStream_t s_in[kCopyStreams] = {}, s_out = nullptr;
+  cudaEvent_t ev_in[kSlots][kCopyStreams] = {}, ev_done[kSlots] = {}, ev_out[kSlots] = {}, ev_start = nullptr;
   // captured batches, keyed by every launch argument
   std::map<std::vector<uint64_t>, sep_graph_entry> graphs;
   uint64_t use_clock = 0;

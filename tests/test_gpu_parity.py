@@ -297,16 +297,16 @@ def test_autotune_picks_a_plan_and_caches_it(jf_small, tmp_path):
 
 
 def test_process_host_pipeline_equals_device_batch(jf_small):
-    """Host-to-host pipelined path (chunks of 2, ragged last chunk) returns
-    exactly what the device batch returns."""
+    """Host-to-host pipelined path (chunks of 1 and 4: slots reused, ragged
+    last chunk; one chunk) returns exactly what the device batch returns."""
     det, mask, cal, fr, W = jf_small
     sep = Separator.from_detector(det, mask=mask, calib=cal)
     kcap, pcap = det.npix // 4, 20000
-    frames = np.ascontiguousarray(fr[:5])
+    frames = np.ascontiguousarray(fr)
     o_dev, _ = run_batch(sep, frames, kcap, pcap)
     host = torch.from_numpy(frames.view(np.int16)).pin_memory()
     ho = sep.alloc_host_outputs(frames.shape[0], kcap, pcap)
-    for chunk in (2, 64):
+    for chunk in (1, 4, 64):
         for v in ho.values():
             v.zero_()
         sep.process_host(host, ho, kcap, pcap, chunk_frames=chunk)
