@@ -295,7 +295,9 @@ sep_status sep_csr_set_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const
 sep_status sep_csr_get_plan(const sep_csr* csr, int32_t* n_classes, int32_t* thresholds, int32_t* tpb);
 /*
  * Time candidate plans (single class at 64/128/256 threads; two classes split
- * at 1024/2048/4096/8192 entries with every block-size pair) on a sample
+ * at 1024/2048/4096/8192 entries with every block-size pair; three classes
+ * split at 4096/8192, 6144/10240 or 4096/10240 entries with four block-size
+ * triples) on a sample
  * batch of device frames with sep_integrate_clip's work, keep the fastest on
  * csr and report its time per call in *best_ms (may be NULL). cache_path
  * (may be NULL): a text file keyed by detector shape, matrix, dtype,

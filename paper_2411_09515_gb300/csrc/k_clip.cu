@@ -528,26 +528,23 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
       // cp.async copies); then every thread replaces each of its entries by
       // the staged value it addresses with a 4-byte cp.async: all of a
       // thread's loads are in flight at once and land in shared memory
-      // without passing through registers. Inside a coefficient group the
-      // entries ascend in staging position, so a warp's loads fall on short
-      // contiguous runs. Slot e is read (entry) and then overwritten (value)
-      // by the same thread.
+      // without passing through registers. Consecutive threads take
+      // consecutive entries, which ascend in staging position inside a
+      // coefficient group, so a warp's loads fall on short contiguous runs.
+      // Slot e is read (entry) and then overwritten (value) by one thread.
       const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
       for (int q = tid; q < nq; q += kThreads)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
                      : "memory");
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
+      // (padding entries address the row's NaN slot, outside every interval)
       const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
       for (int e = tid; e < n; e += kThreads) {
         const uint32_t u = ents[e];
-        if (u & kPad) {
-          vals[e] = __int_as_float(0x7fc00000);   // NaN: outside every interval
-        } else {
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + 4u * (unsigned)e),
-                       "l"(vf + (u & kColMask))
-                       : "memory");
-        }
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + 4u * (unsigned)e),
+                     "l"(vf + (u & kColMask))
+                     : "memory");
       }
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();

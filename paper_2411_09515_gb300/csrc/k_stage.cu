@@ -52,6 +52,11 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
   const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
+  if (t == 0 && tid == 0) {   // the NaN slot of padding entries, once per frame
+    const int f1n = min((int)(blockIdx.y + 1) * a.frames_per_cta, a.n_frames);
+    for (int f = blockIdx.y * a.frames_per_cta; f < f1n; ++f)
+      a.stage[(int64_t)f * a.npos + a.nan_pos] = __int_as_float(0x7fc00000);
+  }
   if (cnt == 0) return;
   const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / kRowThreads;
   const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % kRowThreads);

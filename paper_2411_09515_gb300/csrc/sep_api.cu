@@ -45,9 +45,10 @@ sep_status upload(sep_ctx* ctx, T** dst, const T* src, size_t n) {
   return SEP_OK;
 }
 
-// Row stride of a frame's staged values: positions rounded up to 32 floats,
-// so every frame's row starts 128-byte aligned (vector loads).
-int64_t stage_stride(const sep_csr* csr) { return (csr->h.npos + 31) & ~(int64_t)31; }
+// Row stride of a frame's staged values: the positions plus the NaN slot
+// that padding entries address, rounded up to 32 floats so every frame's row
+// starts 128-byte aligned (vector loads).
+int64_t stage_stride(const sep_csr* csr) { return (csr->h.npos + 1 + 31) & ~(int64_t)31; }
 
 int64_t bitmap_words(int64_t npix) {
   int64_t w = (npix + 31) / 32;
@@ -252,6 +253,7 @@ cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* cal
   g.fptr = fptr;
   g.npix = csr->npix;
   g.npos = stage_stride(csr);
+  g.nan_pos = csr->h.npos;
   g.rows = csr->h.rows;
   g.cols = csr->h.cols;
   g.tiles_x = csr->h.tiles_x;
@@ -934,6 +936,11 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   for (int thr : {1024, 2048, 4096, 8192})
     for (int b0 : {64, 128, 256})
       for (int b1 : {128, 256}) cands.push_back({2, {thr, 0, 0}, {b0, b1, 0, 0}});
+  // three classes: small rows need little shared memory and fit more CTAs per SM
+  const int t3[3][2] = {{4096, 8192}, {6144, 10240}, {4096, 10240}};
+  const int b3[4][3] = {{128, 128, 256}, {128, 256, 256}, {64, 128, 256}, {128, 128, 128}};
+  for (const auto& tt : t3)
+    for (const auto& bb : b3) cands.push_back({3, {tt[0], tt[1], 0}, {bb[0], bb[1], bb[2], 0}});
   float* d_out = nullptr;
   const size_t per = (size_t)n_frames * csr->h.nbins;
   SEP_CUDA(ctx, cudaMalloc((void**)&d_out, per * 12));

@@ -240,9 +240,13 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     }
     out->tile_base[tx * ty] = (int32_t)out->perm_inv.size();
     out->pos_of = pos_of;
-    out->bin_of_pos.assign((out->perm_inv.size() + 31) & ~(size_t)31, 0);   // padded to the staging stride
+    out->bin_of_pos.assign((out->perm_inv.size() + 1 + 31) & ~(size_t)31, 0);   // padded to the staging stride
     for (size_t k = 0; k < out->perm_inv.size(); ++k) out->bin_of_pos[k] = (int16_t)bop[out->perm_inv[k]];
     out->npos = (int64_t)out->perm_inv.size();
+    // padding entries address position npos, which the staging kernel
+    // fills with NaN (outside every interval): the gather needs no branch
+    for (auto& u : out->ent)
+      if (u & kPad) u = kPad | (uint32_t)out->npos;
     // remap and re-sort every group (bin, class) by staging position
     std::vector<std::pair<uint32_t, int64_t>> grp_e;
     std::vector<uint32_t> ent2;

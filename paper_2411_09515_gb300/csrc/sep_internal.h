@@ -96,7 +96,8 @@ struct StageArgs {         // correction + staging of a batch (k_stage)
   const float* norm;       // [npix] or null
   const int16_t* tile_rank;
   const int32_t* tile_base;
-  float* stage;            // [n_frames][npos]
+  float* stage;            // [n_frames][npos] (npos: the row stride)
+  int64_t nan_pos;         // the position padding entries address (set to NaN)
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
