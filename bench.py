@@ -170,8 +170,9 @@ def run_ours(args):
         tune_ms = sep.autotune(dev[: min(F, 128)], stream=stream)
     plan = sep.get_plan()
     # launches of our kernels per step: staging, one clip launch per size
-    # class of the schedule, marking, two for the compaction, two for the peaks
-    launches_per_step = max(len(plan["tpb"]), 1) + 6
+    # class of the schedule (it also marks the kept pixels), two for the
+    # compaction, two for the peaks
+    launches_per_step = max(len(plan["tpb"]), 1) + 5
 
     def step():
         sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)

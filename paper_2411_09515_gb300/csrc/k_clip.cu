@@ -24,7 +24,8 @@
 // pass.
 //
 // After the last evaluation the kernel writes mu + k_pick sigma, the bin's
-// sparsification threshold (Section 3), for k_mark_pos (k_consumers.cu).
+// sparsification threshold (Section 3); with a bitmap it also marks the
+// bin's kept pixels (its centre entries above the threshold).
 //
 // Precision (SEP_PREC_*): per-thread FP32 sums (Kahan-compensated in KAHAN)
 // and FP32 warp shuffles (error-free pairs in KAHAN). The cross-warp merge,
@@ -477,6 +478,14 @@ struct SurrShared {
   int accepted;
 };
 
+// Kept-pixel marks issued ahead by the clip kernel (see its frame loop).
+constexpr int kMarkAhead = 4;
+__device__ __forceinline__ void mark_flush(uint32_t* bm, const int32_t (&px)[kMarkAhead]) {
+#pragma unroll
+  for (int k = 0; k < kMarkAhead; ++k)
+    if (px[k] >= 0) atomicOr(bm + (px[k] >> 5), 1u << (px[k] & 31));
+}
+
 // Registers are capped so that 1024 threads stay resident per SM (the
 // serial step of one CTA overlaps the passes of the others).
 template <int MODE, int PREC, int kThreads, int SURR>
@@ -515,6 +524,14 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
     }
   }
 
+  // Kept-pixel marks of the previous frame still to be written: the pixel
+  // loads of its first kMarkAhead kept centre entries are issued at the end
+  // of that frame and consumed after the next frame's entry copy, so their
+  // latency hides behind it (a pixel of -1: nothing to mark).
+  uint32_t* mk_bm = nullptr;
+  int32_t mk_px[kMarkAhead];
+#pragma unroll
+  for (int k = 0; k < kMarkAhead; ++k) mk_px[k] = -1;
   for (int f = f0; f < f1; ++f) {
     const float* vf = a.stage + (int64_t)f * a.npos;   // this frame's staged values
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
@@ -537,6 +554,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
                      : "memory");
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+      if (mk_bm) mark_flush(mk_bm, mk_px);   // the previous frame's marks
+      mk_bm = nullptr;
       __syncthreads();
       // (padding entries address the row's NaN slot, outside every interval)
       const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
@@ -757,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           tl[v] = __shfl_sync(0xffffffffu, tlo, v);
         }
         if (lane == 0) {
-          float n_set, h[6], l[6], e[4];
+          float n_set, h[6], l[6];
           unpack_totals<MODE>(th, tl, n_set, h, l);
           clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip);
         }
@@ -781,10 +800,41 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         a.rec_target[o * 2 + 1] = ok ? logf(st.sd / sv.s1) : __int_as_float(0x7fc00000);
       }
     }
-    // threshold of sparsification (Section 3) for the marking kernel
-    if (a.thr_out && tid == 0) a.thr_out[o] = pick_threshold<PREC>(st, a.k_pick);
+    // threshold of sparsification (Section 3), evaluated by every thread
+    // from the final state
+    const float thr = pick_threshold<PREC>(st, a.k_pick);
+    if (a.thr_out && tid == 0) a.thr_out[o] = thr;
+    if (a.bitmap) {
+      // kept pixels of this bin: its centre entries (one per pixel whose
+      // centre bin this is) whose value exceeds the threshold; the values
+      // are still in shared memory, only kept pixels touch global memory
+      // (consecutive threads read consecutive values: no bank conflicts;
+      // the entry's pixel is looked up only for values above the threshold)
+      uint32_t* bm = a.bitmap + (int64_t)f * a.words;
+      int np = 0;
+      int32_t g[kMarkAhead];
+#pragma unroll
+      for (int k = 0; k < kMarkAhead; ++k) g[k] = -1;
+      for (int e = tid; e < n; e += kThreads) {
+        if (vals[e] > thr) {
+          if (np < kMarkAhead) {   // kept for later (a shift register: static indexing)
+#pragma unroll
+            for (int k = kMarkAhead - 1; k > 0; --k) g[k] = g[k - 1];
+            g[0] = r0 + e;
+            ++np;
+          } else {                 // beyond the look-ahead: marked now
+            const int32_t i = __ldg(a.cpix + r0 + e);
+            if (i >= 0) atomicOr(bm + (i >> 5), 1u << (i & 31));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMarkAhead; ++k) mk_px[k] = g[k] >= 0 ? __ldg(a.cpix + g[k]) : -1;
+      mk_bm = bm;
+    }
     __syncthreads();   // vals and state are rewritten by the next frame
   }
+  if (mk_bm) mark_flush(mk_bm, mk_px);
 }
 
 // mode 0: set the shared-memory attribute and launch; 1: attribute only

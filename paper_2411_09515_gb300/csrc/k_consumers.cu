@@ -72,45 +72,6 @@ __global__ void k_mark(PixArgs p, int32_t nbins, const float* thr, uint32_t* bit
   if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bitmap[f * words + (i >> 5)] = m;
 }
 
-// Kept bits in staging order: each thread reads groups of four consecutive
-// staged values and their centre bins (vector loads; rows are 128-byte
-// aligned), kMarkGroups groups per thread (more than one measured slower);
-// only kept pixels touch the bitmap.
-constexpr int kMarkGroups = 1;
-
-__global__ void __launch_bounds__(256) k_mark_pos(const float* stage, int64_t npos, int64_t stride,
-                                                  const int16_t* bin_of_pos, const int32_t* perm_inv, const float* thr,
-                                                  const int64_t* orow, int32_t nbins, uint32_t* bitmap, int64_t words) {
-  const int64_t f = blockIdx.y;
-  const float* tf = thr + (orow ? orow[f] : f * (int64_t)nbins);
-  uint32_t* bm = bitmap + f * words;
-  const int64_t p0 = 4 * ((int64_t)blockIdx.x * blockDim.x * kMarkGroups + threadIdx.x);
-  float4 v[kMarkGroups];
-  short4 bq[kMarkGroups];
-#pragma unroll
-  for (int g = 0; g < kMarkGroups; ++g) {   // every load in flight before any use
-    const int64_t p = p0 + 4 * (int64_t)g * blockDim.x;
-    if (p < npos) {
-      v[g] = __ldg(reinterpret_cast<const float4*>(stage + f * stride + p));
-      bq[g] = __ldg(reinterpret_cast<const short4*>(bin_of_pos + p));
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < kMarkGroups; ++g) {
-    const int64_t p = p0 + 4 * (int64_t)g * blockDim.x;
-    if (p >= npos) break;
-    const float x[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
-    const int bb[4] = {bq[g].x, bq[g].y, bq[g].z, bq[g].w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (p + k < npos && x[k] > __ldg(tf + bb[k])) {
-        const uint32_t i = (uint32_t)__ldg(perm_inv + p + k);
-        atomicOr(bm + (i >> 5), 1u << (i & 31u));
-      }
-    }
-  }
-}
-
 // Staged values back to image order; pixels without a position get NaN.
 __global__ void k_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, float* out) {
   const int64_t f = blockIdx.y;
@@ -376,15 +337,6 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_thresholds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mean, sigma, k_pick, n, thr);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mark_pos(const float* stage, int64_t npos, int64_t stride, const int16_t* bin_of_pos,
-                            const int32_t* perm_inv, const float* thr, const int64_t* orow, int32_t nbins,
-                            int32_t n_frames, uint32_t* bitmap, int64_t words, cudaStream_t s) {
-  if (n_frames <= 0 || npos <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((npos + 1024 * kMarkGroups - 1) / (1024 * kMarkGroups)), (unsigned)n_frames);
-  k_mark_pos<<<grid, 256, 0, s>>>(stage, npos, stride, bin_of_pos, perm_inv, thr, orow, nbins, bitmap, words);
   return cudaGetLastError();
 }
 

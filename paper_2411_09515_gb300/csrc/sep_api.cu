@@ -221,6 +221,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.w = csr->d_w;
   a.stage = stage;
   a.perm_inv = csr->d_perm_inv;
+  a.cpix = csr->d_cpix;
   a.npos = stage_stride(csr);
   a.nbins = csr->h.nbins;
   a.n_frames = n_frames;
@@ -420,11 +421,11 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
   }
   if ((st = upload(ctx, &c->d_rowptr, c->h.rowptr.data(), c->h.rowptr.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_ent, c->h.ent.data(), c->h.ent.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_cpix, c->h.cpix.data(), c->h.cpix.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_perm_inv, c->h.perm_inv.data(), std::max<size_t>(c->h.perm_inv.size(), 1))) != SEP_OK ||
       (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
-      (st = upload(ctx, &c->d_bin_of_pos, c->h.bin_of_pos.data(), std::max<size_t>(c->h.bin_of_pos.size(), 1))) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
       (c->has_norm && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
@@ -446,13 +447,13 @@ void sep_csr_destroy(sep_csr* csr) {
   free_plan(csr);
   cudaFree(csr->d_rowptr);
   cudaFree(csr->d_ent);
+  cudaFree(csr->d_cpix);
   cudaFree(csr->d_w);
   cudaFree(csr->d_norm);
   cudaFree(csr->d_bop);
   cudaFree(csr->d_grp);
   cudaFree(csr->d_perm_inv);
   cudaFree(csr->d_pos_of);
-  cudaFree(csr->d_bin_of_pos);
   cudaFree(csr->d_tile_rank);
   cudaFree(csr->d_tile_base);
   delete csr;
@@ -685,8 +686,11 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
+    // the clip kernel marks the kept pixels as each bin's threshold is known
     sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
-                                nullptr, ctx->d_thr);
+                                nullptr, nullptr);
+    a.bitmap = ctx->d_bitmap;
+    a.words = words;
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
     p.stage = ctx->d_stage;
     p.pos_of = csr->d_pos_of;
@@ -695,9 +699,6 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
     if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
     if (e == cudaSuccess)
       e = enqueue_clip(ctx, csr, a, params->precision, mode, s);
-    if (e == cudaSuccess)
-      e = sep::launch_mark_pos(ctx->d_stage, csr->h.npos, stage_stride(csr), csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, nullptr,
-                               csr->h.nbins, n_frames, ctx->d_bitmap, words, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
                               ctx->d_aux, ctx->d_status, s);
@@ -1113,8 +1114,10 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       const int32_t* fidx = reinterpret_cast<const int32_t*>(ctx->d_desc + off_fidx[d]);
       float* stage = ctx->d_stage + soff[d];
       sep::ClipArgs ca = clip_args(ctx, csr, stage, m, params, mean_dev, sigma_dev, count_dev, nullptr, nullptr,
-                                   ctx->d_thr);
+                                   nullptr);
       ca.orow = orow;
+      ca.bitmap = bm;   // kept pixels are marked by the clip kernel
+      ca.words = words[d];
       if (mode == 1) {
         e = enqueue_clip(ctx, csr, ca, params->precision, 1, sd, false);
         continue;
@@ -1129,9 +1132,6 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
       if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, nullptr, fptr, dtype, m, stage, sd);
       if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, params->precision, mode, sd, false);
-      if (e == cudaSuccess)
-        e = sep::launch_mark_pos(stage, csr->h.npos, stage_stride(csr), csr->d_bin_of_pos, csr->d_perm_inv, ctx->d_thr, orow,
-                                 csr->h.nbins, m, bm, words[d], sd);
       if (e == cudaSuccess)
         e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,
                                 sd);

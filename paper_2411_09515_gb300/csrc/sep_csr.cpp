@@ -240,8 +240,6 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     }
     out->tile_base[tx * ty] = (int32_t)out->perm_inv.size();
     out->pos_of = pos_of;
-    out->bin_of_pos.assign((out->perm_inv.size() + 1 + 31) & ~(size_t)31, 0);   // padded to the staging stride
-    for (size_t k = 0; k < out->perm_inv.size(); ++k) out->bin_of_pos[k] = (int16_t)bop[out->perm_inv[k]];
     out->npos = (int64_t)out->perm_inv.size();
     // padding entries address position npos, which the staging kernel
     // fills with NaN (outside every interval): the gather needs no branch
@@ -277,6 +275,14 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
         }
       }
     }
+  }
+  // per entry: its pixel if the entry carries the pixel's centre bin (one
+  // such entry per staged pixel), else -1; the clip kernel marks kept
+  // pixels through these
+  out->cpix.assign((size_t)nnz, -1);
+  for (int64_t e = 0; e < nnz; ++e) {
+    const uint32_t u = out->ent[e];
+    if ((u & kCentre) && !(u & kPad)) out->cpix[(size_t)e] = out->perm_inv[u & kColMask];
   }
   out->rows = gm.rows;
   out->cols = gm.cols;

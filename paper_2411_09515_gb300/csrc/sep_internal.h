@@ -35,6 +35,7 @@ struct HostCsr {
   std::vector<int32_t> grp;      // [nbins][4]: end of coefficient class 0..3 within the row
   std::vector<uint32_t> ent;     // [nnz] packed
   std::vector<float> coef;       // [nnz] c_{i,r} (0 for centre-only entries)
+  std::vector<int32_t> cpix;     // [nnz] pixel of a centre entry (it carries its pixel's centre bin), else -1
   std::vector<float> w;          // [nnz] c * norm (only with a norm)
   std::vector<int32_t> bop;      // [npix] centre bin, -1 masked
   std::vector<float> centers;    // [nbins]
@@ -44,7 +45,6 @@ struct HostCsr {
   int32_t tiles_x = 0, tiles_y = 0;
   std::vector<int32_t> perm_inv;    // [npos] pixel of each staging position
   std::vector<int32_t> pos_of;      // [npix] staging position of each pixel, -1 if not staged
-  std::vector<int16_t> bin_of_pos;  // [npos] centre bin of the pixel at each position
   std::vector<int16_t> tile_rank;   // [npix] position inside its tile, -1 not staged
   std::vector<int32_t> tile_base;   // [tiles + 1] first position of each tile
 };
@@ -73,6 +73,13 @@ struct ClipArgs {
   float* bounds;           // optional [F][B][2]
   int32_t* iters;          // optional [F][B]
   float* thr_out;          // optional [F][B] sparsification thresholds (Section 3)
+  // optional kept-pixel marking (Section 3) at the end of each bin's clip:
+  // cpix[e] = pixel of entry e if the entry carries its pixel's centre bin,
+  // else -1; a centre entry whose value exceeds the bin's threshold sets its
+  // pixel's bit in row f of bitmap (words per frame). Null bitmap = no marking.
+  const int32_t* cpix = nullptr;
+  uint32_t* bitmap = nullptr;
+  int64_t words = 0;
   // mixed batches: per launch frame, the first output row (in bins) of its
   // profile; null = rows f * nbins
   const int64_t* orow = nullptr;
@@ -128,12 +135,7 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
-// Kept-pixel bitmap from staged values: pixel perm_inv[p] is kept iff its
-// staged value exceeds the threshold of its centre bin.
-cudaError_t launch_mark_pos(const float* stage, int64_t npos, int64_t stride, const int16_t* bin_of_pos,
-                            const int32_t* perm_inv,
-                            const float* thr, const int64_t* orow, int32_t nbins, int32_t n_frames, uint32_t* bitmap,
-                            int64_t words, cudaStream_t s);
+// Staged values back to image order (NaN where a pixel has no position).
 cudaError_t launch_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, int32_t n_frames,
                            float* out, cudaStream_t s);
 cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* thr, uint32_t* bitmap,
@@ -215,13 +217,13 @@ struct sep_csr {
   bool has_norm = false;
   int32_t* d_rowptr = nullptr;
   uint32_t* d_ent = nullptr;
+  int32_t* d_cpix = nullptr;          // pixel of each centre entry, else -1
   float* d_w = nullptr;
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
   int32_t* d_perm_inv = nullptr;      // staging order
   int32_t* d_pos_of = nullptr;
-  int16_t* d_bin_of_pos = nullptr;
   int16_t* d_tile_rank = nullptr;
   int32_t* d_tile_base = nullptr;
   const sep_model* model = nullptr;   // surrogate attached by sep_csr_attach_model
