@@ -126,9 +126,121 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
   }
 }
 
+// The aligned case with the frames' loads ahead of their use: each thread
+// copies its four raw words (8 bytes; 16 for FP32 input) of the next frames
+// into its own slots of a ring in shared memory (cp.async, no registers
+// held), kRing frames ahead, and reads them back when their frame comes.
+// A thread reads only what it copied itself, so the ring needs no barrier.
+constexpr int kRing = 6;
+template <int DT, bool NORM>
+__global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
+  constexpr int kVec = DT == SEP_DTYPE_U16_JF ? 8 : 16;   // bytes of 4 raw words
+  __shared__ float tv[2][kTilePix];
+  __shared__ __align__(16) unsigned char ring[kRing][kStageThreads * kVec];
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
+  if (t == 0 && tid == 0) {   // the NaN slot of padding entries, once per frame
+    const int f1n = min((int)(blockIdx.y + 1) * a.frames_per_cta, a.n_frames);
+    for (int f = blockIdx.y * a.frames_per_cta; f < f1n; ++f)
+      a.stage[(int64_t)f * a.npos + a.nan_pos] = __int_as_float(0x7fc00000);
+  }
+  if (cnt == 0) return;
+  const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / kRowThreads;
+  const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % kRowThreads);
+  const int64_t p = r * a.cols + c;    // first of this thread's 4 pixels
+  // (columns are a multiple of 4: a thread's 4 pixels are all inside or all outside)
+  const bool inside = r < a.rows && c < a.cols;
+  int rank[4];
+  float p0[4], g0[4], nm[4];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    rank[k] = inside ? __ldg(a.tile_rank + p + k) : -1;
+    any = any || rank[k] >= 0;
+    p0[k] = 0.0f;
+    g0[k] = 1.0f;
+    nm[k] = 1.0f;
+    if (rank[k] >= 0) {
+      if (DT == SEP_DTYPE_U16_JF) {
+        p0[k] = __ldg(a.ped + p + k);
+        g0[k] = __ldg(a.gain + p + k);
+      }
+      if (NORM) nm[k] = __ldg(a.norm + p + k);
+    }
+  }
+  const int f0 = blockIdx.y * a.frames_per_cta;
+  const int nfr = min(f0 + a.frames_per_cta, a.n_frames) - f0;
+  const unsigned slot0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid * kVec]);
+  // one commit group per frame (empty past the last frame or for idle threads)
+  auto issue = [&](int j) {
+    if (any && j < nfr) {
+      const char* src = reinterpret_cast<const char*>(frame_ptr<DT>(a.frames, f0 + j, a.npix)) +
+                        p * (DT == SEP_DTYPE_U16_JF ? 2 : 4);
+      const unsigned dst = slot0 + (unsigned)((j % kRing) * kStageThreads * kVec);
+      if (kVec == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+      else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+#pragma unroll
+  for (int j = 0; j < kRing; ++j) issue(j);
+  for (int j = 0; j < nfr; j += 2) {
+    const int nf = min(2, nfr - j);
+    // groups 0 .. j + kRing - 1 issued: frames j and j + 1 have landed
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 2) : "memory");
+    uint32_t w[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned char* sl = &ring[(j + h) % kRing][tid * kVec];
+      if (DT == SEP_DTYPE_U16_JF) {
+        const uint2 v = *reinterpret_cast<const uint2*>(sl);
+        w[h][0] = v.x & 0xffffu; w[h][1] = v.x >> 16; w[h][2] = v.y & 0xffffu; w[h][3] = v.y >> 16;
+      } else {
+        const uint4 v = *reinterpret_cast<const uint4*>(sl);
+        w[h][0] = v.x; w[h][1] = v.y; w[h][2] = v.z; w[h][3] = v.w;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nf) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (rank[k] < 0) continue;
+        float x;
+        if (DT == SEP_DTYPE_U16_JF) {
+          const uint32_t u = w[h][k], code = u >> 14;
+          float ped = p0[k], gain = g0[k];
+          if (code != 0) {   // gain levels 1 and 2
+            const int64_t lvl = code == 1 ? 1 : 2;
+            ped = __ldg(a.ped + lvl * a.npix + p + k);
+            gain = __ldg(a.gain + lvl * a.npix + p + k);
+          }
+          x = __fdiv_rn(__fsub_rn((float)(u & 0x3FFFu), ped), gain);
+        } else {
+          x = __uint_as_float(w[h][k]);
+        }
+        if (NORM) x = __fdiv_rn(x, nm[k]);
+        tv[h][rank[k]] = x;
+      }
+    }
+    // the two slots just read are refilled (this thread's own words, already in registers)
+    issue(j + kRing);
+    issue(j + kRing + 1);
+    __syncthreads();
+    for (int h = 0; h < nf; ++h) {
+      float* out = a.stage + (int64_t)(f0 + j + h) * a.npos + base;
+      for (int q = tid; q < cnt; q += kStageThreads) out[q] = tv[h][q];
+    }
+    __syncthreads();
+  }
+}
+
 template <int DT, bool NORM>
 void launch_v(const StageArgs& a, dim3 grid, bool vec, cudaStream_t s) {
-  if (vec) k_stage<DT, NORM, true><<<grid, kStageThreads, 0, s>>>(a);
+  if (vec) k_stage_ring<DT, NORM><<<grid, kStageThreads, 0, s>>>(a);
   else k_stage<DT, NORM, false><<<grid, kStageThreads, 0, s>>>(a);
 }
 
