@@ -196,17 +196,19 @@ __device__ __forceinline__ bool is_kept(const uint32_t* bm, int64_t j) { return 
 
 // Is kept pixel i a peak (Section 4)? At least min_count kept pixels in the
 // patch, and i the maximum of the patch's valid pixels (ties: lowest index).
+// (the pixel's own value is loaded only once the bitmap has shown enough
+// kept pixels: most kept pixels are isolated and fail on the count alone)
 template <int DT, bool NORM>
 __device__ __forceinline__ bool peak_test(const PixArgs& p, const void* frame, int64_t f, const uint32_t* bm, int64_t i,
-                                          int h, int32_t min_count, float vi, int& nk_out) {
+                                          int h, int32_t min_count) {
   const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
   const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
   const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
   int nk = 0;
   for (int r = rlo; r <= rhi; ++r)
     for (int c = clo; c <= chi; ++c) nk += is_kept(bm, (int64_t)r * p.cols + c);
-  nk_out = nk;
   if (nk < min_count) return false;
+  const float vi = value_of<DT, NORM>(p, frame, f, i);
   for (int r = rlo; r <= rhi; ++r)
     for (int c = clo; c <= chi; ++c) {
       const int64_t j = (int64_t)r * p.cols + c;
@@ -234,11 +236,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_flags(PixArgs p, const ui
     const int64_t k = ch * kPeakChunk + threadIdx.x;
     bool peak = false;
     const int64_t i = k < n ? idx[g * kcap + k] : -1;
-    if (i >= 0 && i < p.npix && __ldg(p.bop + i) >= 0) {
-      int nk;
-      const float vi = value_of<DT, NORM>(p, frame, f, i);
-      peak = peak_test<DT, NORM>(p, frame, f, bm, i, h, min_count, vi, nk);
-    }
+    if (i >= 0 && i < p.npix && __ldg(p.bop + i) >= 0) peak = peak_test<DT, NORM>(p, frame, f, bm, i, h, min_count);
     const uint32_t m = __ballot_sync(0xffffffffu, peak);
     if ((threadIdx.x & 31) == 0) flags[f * ((int64_t)n_chunks * 8) + ch * 8 + (threadIdx.x >> 5)] = m;
     const int c = __syncthreads_count(peak);

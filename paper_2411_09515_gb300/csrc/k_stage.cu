@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
 // into its own slots of a ring in shared memory (cp.async, no registers
 // held), kRing frames ahead, and reads them back when their frame comes.
 // A thread reads only what it copied itself, so the ring needs no barrier.
-constexpr int kRing = 6;
 template <int DT, bool NORM>
 __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   constexpr int kVec = DT == SEP_DTYPE_U16_JF ? 8 : 16;   // bytes of 4 raw words
+  constexpr int kRing = 6;   // frames ahead (even; 10 measured no faster)
   __shared__ float tv[2][kTilePix];
   __shared__ __align__(16) unsigned char ring[kRing][kStageThreads * kVec];
   const int t = blockIdx.x;
