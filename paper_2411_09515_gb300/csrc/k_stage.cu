@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   // (columns are a multiple of 4: a thread's 4 pixels are all inside or all outside)
   const bool inside = r < a.rows && c < a.cols;
   int rank[4];
-  float p0[4], g0[4], nm[4];
+  float p0[4], g0[4], r0[4], nm[4];
   bool any = false;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -168,6 +168,10 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
       }
       if (NORM) nm[k] = __ldg(a.norm + p + k);
     }
+    // level-0 reciprocal for the division below; 0 (= use the IEEE
+    // division) outside the range where the correction step is exact
+    const float ag = fabsf(g0[k]);
+    r0[k] = ag >= 0x1p-100f && ag <= 0x1p100f ? __frcp_rn(g0[k]) : 0.0f;
   }
   const int f0 = blockIdx.y * a.frames_per_cta;
   const int nfr = min(f0 + a.frames_per_cta, a.n_frames) - f0;
@@ -212,13 +216,24 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
         float x;
         if (DT == SEP_DTYPE_U16_JF) {
           const uint32_t u = w[h][k], code = u >> 14;
-          float ped = p0[k], gain = g0[k];
-          if (code != 0) {   // gain levels 1 and 2
-            const int64_t lvl = code == 1 ? 1 : 2;
-            ped = __ldg(a.ped + lvl * a.npix + p + k);
-            gain = __ldg(a.gain + lvl * a.npix + p + k);
+          if (code == 0 && r0[k] != 0.0f) {
+            // RN((adc - ped) / gain) without a division: with r = RN(1/gain)
+            // and q = RN(d r), the residual e = d - q gain is exact under a
+            // fused multiply-add, and RN(q + e r) is the correctly rounded
+            // quotient (Markstein's correction, IBM J. Res. Dev. 34(1), 1990;
+            // gain and quotient are normal here)
+            const float d = __fsub_rn((float)(u & 0x3FFFu), p0[k]);
+            const float q = __fmul_rn(d, r0[k]);
+            x = __fmaf_rn(__fmaf_rn(-q, g0[k], d), r0[k], q);
+          } else {
+            float ped = p0[k], gain = g0[k];
+            if (code != 0) {   // gain levels 1 and 2
+              const int64_t lvl = code == 1 ? 1 : 2;
+              ped = __ldg(a.ped + lvl * a.npix + p + k);
+              gain = __ldg(a.gain + lvl * a.npix + p + k);
+            }
+            x = __fdiv_rn(__fsub_rn((float)(u & 0x3FFFu), ped), gain);
           }
-          x = __fdiv_rn(__fsub_rn((float)(u & 0x3FFFu), ped), gain);
         } else {
           x = __uint_as_float(w[h][k]);
         }
