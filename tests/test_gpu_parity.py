@@ -319,4 +319,16 @@ def test_process_host_pipeline_equals_device_batch(jf_small):
             assert np.array_equal(ho["val"][f, :n].numpy(), o_dev["val"][f, :n])
             p = int(o_dev["n_peaks"][f])
             assert np.array_equal(ho["peaks"][f, :p].numpy(), o_dev["peaks"][f, :p])
+    # pageable (not pinned) host outputs: the same results
+    pageable = {k: torch.zeros(v.shape, dtype=v.dtype) for k, v in ho.items()}
+    assert not any(t.is_pinned() for t in pageable.values())
+    sep.process_host(host, pageable, kcap, pcap, chunk_frames=4)
+    torch.cuda.synchronize()
+    for k in ("mean", "sigma", "count", "n_kept", "n_peaks"):
+        assert np.array_equal(pageable[k].numpy(), o_dev[k]), k
+    for f in range(frames.shape[0]):
+        n, p = int(o_dev["n_kept"][f]), int(o_dev["n_peaks"][f])
+        assert np.array_equal(pageable["idx"][f, :n].numpy(), o_dev["idx"][f, :n])
+        assert np.array_equal(pageable["val"][f, :n].numpy(), o_dev["val"][f, :n])
+        assert np.array_equal(pageable["peaks"][f, :p].numpy(), o_dev["peaks"][f, :p])
     assert sep.device_status() == 0
