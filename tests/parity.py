@@ -139,3 +139,19 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3):
     for k in ("y", "x", "I", "sigma"):
         assert np.all(close(g[k], r[k], rtol=PEAK_RTOL)), (k, g[k][:5], r[k][:5])
     return ref.size, int(clean.sum())
+
+
+def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None):
+    """Frame f of a batch's outputs `o` (numpy arrays as returned by the
+    library) against the oracle on the frame's signal. Returns (banded bins,
+    bins on another trajectory, excused pixels)."""
+    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm)
+    if bounds is None:
+        bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
+    nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
+    excused = check_kept(fr, o["idx"][f], o["val"][f], o["n_kept"][f], moved, capacity=kcap)
+    peaks = o["peaks"][f][: int(o["n_peaks"][f])].copy().view(np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"),
+                                                                      ("I", "<f4"), ("sigma", "<f4"),
+                                                                      ("npix", "<i4")])).reshape(-1)
+    check_peaks(det, fr, peaks, excused)
+    return nb, len(moved), len(excused)

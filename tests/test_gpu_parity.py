@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from parity import Frame, check_clip, check_kept, check_peaks
+from parity import Frame, check_clip, check_frame, check_kept, check_peaks
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -24,19 +24,6 @@ def run_batch(sep, frames_np, kcap, pcap, use_graph=True):
     out = sep.process_batch(fr, kcap, pcap, use_graph=use_graph)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}, fr
-
-
-def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None):
-    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm)
-    if bounds is None:
-        bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
-    nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
-    excused = check_kept(fr, o["idx"][f], o["val"][f], o["n_kept"][f], moved, capacity=kcap)
-    peaks = o["peaks"][f][: int(o["n_peaks"][f])].copy().view(np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"),
-                                                                      ("I", "<f4"), ("sigma", "<f4"),
-                                                                      ("npix", "<i4")])).reshape(-1)
-    check_peaks(det, fr, peaks, excused)
-    return nb, len(moved), len(excused)
 
 
 def test_config1_ten_seeds_batch():
