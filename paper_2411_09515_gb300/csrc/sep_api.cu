@@ -220,7 +220,6 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.ent = csr->d_ent;
   a.w = csr->d_w;
   a.stage = stage;
-  a.perm_inv = csr->d_perm_inv;
   a.cpix = csr->d_cpix;
   a.npos = stage_stride(csr);
   a.nbins = csr->h.nbins;
@@ -424,7 +423,6 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
       (st = upload(ctx, &c->d_cpix, c->h.cpix.data(), c->h.cpix.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
-      (st = upload(ctx, &c->d_perm_inv, c->h.perm_inv.data(), std::max<size_t>(c->h.perm_inv.size(), 1))) != SEP_OK ||
       (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
@@ -452,7 +450,6 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_norm);
   cudaFree(csr->d_bop);
   cudaFree(csr->d_grp);
-  cudaFree(csr->d_perm_inv);
   cudaFree(csr->d_pos_of);
   cudaFree(csr->d_tile_rank);
   cudaFree(csr->d_tile_base);

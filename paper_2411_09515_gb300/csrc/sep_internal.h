@@ -62,7 +62,6 @@ struct ClipArgs {
   const uint32_t* ent;     // packed entries: staging position + flags
   const float* w;          // per-entry weight c * norm (NORM variant)
   const float* stage;      // staged values [n_frames][npos] (npos here: the row stride)
-  const int32_t* perm_inv; // [npos] pixel of each staging position
   int64_t npos;
   int32_t nbins, n_frames, frames_per_cta, cap;
   int32_t n_iter;
@@ -222,7 +221,6 @@ struct sep_csr {
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
-  int32_t* d_perm_inv = nullptr;      // staging order
   int32_t* d_pos_of = nullptr;
   int16_t* d_tile_rank = nullptr;
   int32_t* d_tile_base = nullptr;
