@@ -235,6 +235,24 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
                         sep_stream stream);
 
 /*
+ * Densification (Section 3, "Densification / Decompression"): rebuild dense
+ * frames from their sparse form. Every pixel with a centre bin b gets the
+ * bin's background level mean_dev[f][b]; when noise_dev is given (standard
+ * normal deviates z, float32 [n_frames][npix], drawn by the caller) it gets
+ * RN32(mean_b + RN32(sigma_b * z_i)) instead (the noisy background some
+ * reduction programs need); then the first min(n_kept[f], kept_capacity)
+ * kept pixels of the frame (idx_dev / val_dev [n_frames][kept_capacity], as
+ * sep_sparsify writes them; indices outside the detector are skipped) get
+ * their recorded values back. Pixels without a bin (masked) get `fill`.
+ * mean/sigma: [n_frames][nbins] float32 (sigma may be NULL without noise).
+ * out_dev: float32 [n_frames][npix], caller-owned. No scratch is used.
+ */
+sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const float* mean_dev,
+                       const float* sigma_dev, const int32_t* idx_dev, const float* val_dev,
+                       int64_t kept_capacity, const int32_t* n_kept_dev, const float* noise_dev, float fill,
+                       float* out_dev, sep_stream stream);
+
+/*
  * The whole path on a batch in one call: integrate + clip, sparsify and peak
  * picking, with the kept-pixel map passed between the steps on the device.
  * Outputs as in the three calls above. The launch sequence is captured once

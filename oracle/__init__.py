@@ -197,6 +197,29 @@ def sparsify(W: Weights, signal, mean, sigma, k_pick=3.0, norm=None):
     return idx, val
 
 
+def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan):
+    """Decompression of Section 3 ("Densification / Decompression"): the
+    background of every pixel with a radial bin is its bin's mean level, with
+    noise of the bin's deviation when standard normal deviates z are given
+    (binary32, one rounding per operation: mean_b + (sigma_b * z_i)); the
+    pixels that were kept get their recorded values back; pixels without a
+    bin get `fill`. Plain numpy statement (no arithmetic in the C library)."""
+    bop = np.asarray(W.bin_of_pixel)
+    out = np.full(W.npix, fill, np.float32)
+    has = bop >= 0
+    mu = np.asarray(mean, np.float32)[bop[has]]
+    if noise is None:
+        out[has] = mu
+    else:
+        sd = np.asarray(sigma, np.float32)[bop[has]]
+        z = np.asarray(noise, np.float32).reshape(-1)[has]
+        out[has] = mu + sd * z          # float32 operands: each operation rounds to binary32
+    idx = np.asarray(idx, np.int64)
+    ok = (idx >= 0) & (idx < W.npix)
+    out[idx[ok]] = np.asarray(val, np.float32)[ok]
+    return out
+
+
 def peaks(det, W: Weights, signal, mean, sigma, k_pick=3.0, patch=3, min_count=3, norm=None):
     """Peak picking of Section 4 over the kept pixels; structured array."""
     sig = _c(signal, np.float32).reshape(-1)

@@ -175,6 +175,37 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
   }
 }
 
+// Densification (Section 3): the background level of every binned pixel
+// (its bin's mean, or RN(mean + RN(sigma z)) with the caller's deviates z),
+// fill where a pixel has no bin; one thread per pixel, four pixels a thread
+// where the frame row allows vector stores.
+__global__ void __launch_bounds__(256) k_dense_background(const int32_t* bop, int64_t npix, int32_t nbins,
+                                                          const float* mean, const float* sigma,
+                                                          const float* noise, float fill, float* out) {
+  const int64_t f = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  const int32_t b = __ldg(bop + i);
+  float x = fill;
+  if (b >= 0) {
+    x = __ldg(mean + f * nbins + b);
+    if (noise) x = __fadd_rn(x, __fmul_rn(__ldg(sigma + f * nbins + b), __ldg(noise + f * npix + i)));
+  }
+  out[f * npix + i] = x;
+}
+
+// ... then the recorded values of the kept pixels.
+__global__ void __launch_bounds__(256) k_dense_scatter(const int32_t* idx, const float* val, int64_t cap,
+                                                       const int32_t* n_kept, int64_t npix, float* out) {
+  const int64_t f = blockIdx.y;
+  int64_t n = n_kept[f];
+  n = n < 0 ? 0 : (n > cap ? cap : n);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = idx[f * cap + k];
+    if (i >= 0 && i < npix) out[f * npix + i] = val[f * cap + k];
+  }
+}
+
 // Indices outside the detector are ignored (a caller's list is not trusted).
 __global__ void k_scatter_list(const int32_t* idx, const int32_t* n_kept, int64_t kcap, int64_t npix,
                                uint32_t* bitmap, int64_t words) {
@@ -381,6 +412,19 @@ cudaError_t launch_compact(const PixArgs& p, int32_t n_frames, const uint32_t* b
     else k_emit_kept<SEP_DTYPE_F32, false><<<grid, kCompactThreads, 0, s>>>(SEP_EMIT_ARGS);
   }
 #undef SEP_EMIT_ARGS
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,
+                           const float* sigma, const int32_t* idx, const float* val, int64_t cap,
+                           const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s) {
+  if (n_frames <= 0 || npix <= 0) return cudaSuccess;
+  dim3 g1((unsigned)((npix + 255) / 256), (unsigned)n_frames);
+  k_dense_background<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+  if (cap > 0) {
+    dim3 g2((unsigned)std::min<int64_t>((cap + 255) / 256, 64), (unsigned)n_frames);
+    k_dense_scatter<<<g2, 256, 0, s>>>(idx, val, cap, n_kept, npix, out);
+  }
   return cudaGetLastError();
 }
 

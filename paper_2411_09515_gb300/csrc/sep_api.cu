@@ -662,6 +662,26 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   return SEP_OK;
 }
 
+sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const float* mean_dev,
+                       const float* sigma_dev, const int32_t* idx_dev, const float* val_dev,
+                       int64_t kept_capacity, const int32_t* n_kept_dev, const float* noise_dev, float fill,
+                       float* out_dev, sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (!csr) return fail(ctx, SEP_ERR_ARG, "NULL matrix");
+  if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "matrix belongs to another context");
+  if (n_frames < 0 || kept_capacity < 0) return fail(ctx, SEP_ERR_ARG, "negative size");
+  if (n_frames == 0) return SEP_OK;
+  if (!mean_dev || !out_dev || (noise_dev && !sigma_dev) ||
+      (kept_capacity > 0 && (!idx_dev || !val_dev || !n_kept_dev)))
+    return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaError_t e = sep::launch_densify(csr->d_bop, csr->npix, csr->h.nbins, n_frames, mean_dev, sigma_dev, idx_dev,
+                                      val_dev, kept_capacity, n_kept_dev, noise_dev, fill, out_dev,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "densify launch");
+  return SEP_OK;
+}
+
 sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                              int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                              float* sigma_dev, int32_t* count_dev, int32_t* idx_dev, float* val_dev,

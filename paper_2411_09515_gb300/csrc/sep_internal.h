@@ -134,6 +134,11 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
+// Dense frames from their sparse form (Section 3): background by bin, then
+// the kept pixels' values.
+cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,
+                           const float* sigma, const int32_t* idx, const float* val, int64_t cap,
+                           const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s);
 // Staged values back to image order (NaN where a pixel has no position).
 cudaError_t launch_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, int32_t n_frames,
                            float* out, cudaStream_t s);
