@@ -303,12 +303,7 @@ __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts,
       const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
       uint32_t cnt = 0;
       Acc<KAHAN> a1, a2;
-      // thread t takes the row's float4 groups g = t mod kThreads across all
-      // classes (not from each class's start): every thread gets an equal
-      // share of the row, so no warp waits at the barrier for the others'
-      // partial last iterations of four classes
-      const int lo4 = lo >> 2;
-      for (int q = lo4 + (tid - lo4 % kThreads + kThreads) % kThreads; q < (hi >> 2); q += kThreads) {
+      for (int q = (lo >> 2) + tid; q < (hi >> 2); q += kThreads) {
         const float4 v4 = vals4[q];
         const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
