@@ -528,8 +528,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
   // loads of its first kMarkAhead kept centre entries are issued at the end
   // of that frame and consumed after the next frame's entry copy, so their
   // latency hides behind it (a pixel of -1: nothing to mark).
-  uint64_t keep_l2;   // L2 policy: evict the matrix last
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(keep_l2));
   uint32_t* mk_bm = nullptr;
   int32_t mk_px[kMarkAhead];
 #pragma unroll
@@ -551,12 +549,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
       // consecutive entries, which ascend in staging position inside a
       // coefficient group, so a warp's loads fall on short contiguous runs.
       // Slot e is read (entry) and then overwritten (value) by one thread.
-      // (the matrix is reread for every frame: its lines are kept in L2
-      // ahead of the staged values, which stream through once)
       const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
       for (int q = tid; q < nq; q += kThreads)
-        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sb + 16u * (unsigned)q),
-                     "l"(ent4 + q), "l"(keep_l2)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
                      : "memory");
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       if (mk_bm) mark_flush(mk_bm, mk_px);   // the previous frame's marks

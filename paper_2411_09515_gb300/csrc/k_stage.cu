@@ -176,8 +176,6 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   const int f0 = blockIdx.y * a.frames_per_cta;
   const int nfr = min(f0 + a.frames_per_cta, a.n_frames) - f0;
   const unsigned slot0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid * kVec]);
-  uint64_t evict_l2;   // L2 policy of the staged rows: evict first
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(evict_l2));
   // one commit group per frame (empty past the last frame or for idle threads)
   auto issue = [&](int j) {
     if (any && j < nfr) {
@@ -249,11 +247,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
     __syncthreads();
     for (int h = 0; h < nf; ++h) {
       float* out = a.stage + (int64_t)(f0 + j + h) * a.npos + base;
-      // (staged rows are read once by the clip kernel much later: they
-      // leave L2 first, ahead of the matrix and calibration)
-      for (int q = tid; q < cnt; q += kStageThreads)
-        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;\n" ::"l"(out + q), "f"(tv[h][q]), "l"(evict_l2)
-                     : "memory");
+      for (int q = tid; q < cnt; q += kStageThreads) out[q] = tv[h][q];
     }
     __syncthreads();
   }
