@@ -243,6 +243,9 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # densification (Section 3) of the batch's sparse output, timed alone
+    dens = densify_eval(sep, out, F, stream, args)
+
     # the learned surrogate against the plain loop on the same batch
     sur = None
     if args.surrogate_train_frames > 0:
@@ -279,6 +282,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "surrogate": sur,
+            "densify": dens,
             "device_status": status,
             "mean_kept_per_frame": float(n_kept.mean()), "mean_peaks_per_frame": float(n_peaks.mean()),
             "setup_s": round(t_gen, 1),
@@ -286,6 +290,39 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def densify_eval(sep, out, F, stream, args):
+    """Dense frames rebuilt from the batch's per-bin levels and kept lists,
+    without and with a noisy background (normal deviates drawn once, outside
+    the timed region). Algorithmic bytes per frame: the dense frame written
+    (4N), the kept list read (8 per kept pixel), mean and sigma (8B), and the
+    deviates read (4N) with noise."""
+    import torch
+    N = sep.npix
+    dense = torch.empty((F, N), dtype=torch.float32, device=out["mean"].device)
+    z = torch.randn((F, N), dtype=torch.float32, device=out["mean"].device)
+    kept = int(out["n_kept"].clamp(max=out["idx"].shape[1]).sum().item())
+    res = {}
+    for name, noise in (("plain", None), ("noise", z)):
+        run = lambda: sep.densify(out["mean"], out["sigma"], out["idx"], out["val"], out["n_kept"], noise=noise,
+                                  out=dense, stream=stream)
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nbytes = 4 * N * F + 8 * kept + 8 * sep.nbins * F + (4 * N * F if noise is not None else 0)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"frames_s": round(F / (ms * 1e-3), 1), "ms": round(ms, 3), "achieved_gbs": round(gbs, 1),
+                     "frac_of_hbm": round(gbs / peaks_file()[0]["hbm_gbs"], 4), "peak_source": peaks_file()[1]}
+    del dense, z
+    return res
 
 
 def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):

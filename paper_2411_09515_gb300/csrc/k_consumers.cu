@@ -177,8 +177,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
 
 // Densification (Section 3): the background level of every binned pixel
 // (its bin's mean, or RN(mean + RN(sigma z)) with the caller's deviates z),
-// fill where a pixel has no bin; one thread per pixel, four pixels a thread
-// where the frame row allows vector stores.
+// fill where a pixel has no bin; one thread per pixel.
 __global__ void __launch_bounds__(256) k_dense_background(const int32_t* bop, int64_t npix, int32_t nbins,
                                                           const float* mean, const float* sigma,
                                                           const float* noise, float fill, float* out) {
@@ -192,6 +191,34 @@ __global__ void __launch_bounds__(256) k_dense_background(const int32_t* bop, in
     if (noise) x = __fadd_rn(x, __fmul_rn(__ldg(sigma + f * nbins + b), __ldg(noise + f * npix + i)));
   }
   out[f * npix + i] = x;
+}
+
+// The same, four consecutive pixels a thread (vector loads and stores; the
+// pixel count is a multiple of 4 and the rows are 16-byte aligned).
+__global__ void __launch_bounds__(256) k_dense_background4(const int32_t* bop, int64_t npix, int32_t nbins,
+                                                           const float* mean, const float* sigma,
+                                                           const float* noise, float fill, float* out) {
+  const int64_t f = blockIdx.y;
+  const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= npix) return;
+  const int4 b = __ldg(reinterpret_cast<const int4*>(bop + i));
+  const int bb[4] = {b.x, b.y, b.z, b.w};
+  const float* mu = mean + f * nbins;
+  float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (noise) {
+    const float4 zz = __ldg(reinterpret_cast<const float4*>(noise + f * npix + i));
+    z[0] = zz.x; z[1] = zz.y; z[2] = zz.z; z[3] = zz.w;
+  }
+  float x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    x[k] = fill;
+    if (bb[k] >= 0) {
+      x[k] = __ldg(mu + bb[k]);
+      if (noise) x[k] = __fadd_rn(x[k], __fmul_rn(__ldg(sigma + f * nbins + bb[k]), z[k]));
+    }
+  }
+  *reinterpret_cast<float4*>(out + f * npix + i) = make_float4(x[0], x[1], x[2], x[3]);
 }
 
 // ... then the recorded values of the kept pixels.
@@ -419,8 +446,15 @@ cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int3
                            const float* sigma, const int32_t* idx, const float* val, int64_t cap,
                            const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s) {
   if (n_frames <= 0 || npix <= 0) return cudaSuccess;
-  dim3 g1((unsigned)((npix + 255) / 256), (unsigned)n_frames);
-  k_dense_background<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+  const bool vec = npix % 4 == 0 && (uintptr_t)out % 16 == 0 && (!noise || (uintptr_t)noise % 16 == 0) &&
+                   (uintptr_t)bop % 16 == 0;
+  if (vec) {
+    dim3 g1((unsigned)((npix / 4 + 255) / 256), (unsigned)n_frames);
+    k_dense_background4<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+  } else {
+    dim3 g1((unsigned)((npix + 255) / 256), (unsigned)n_frames);
+    k_dense_background<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+  }
   if (cap > 0) {
     dim3 g2((unsigned)std::min<int64_t>((cap + 255) / 256, 64), (unsigned)n_frames);
     k_dense_scatter<<<g2, 256, 0, s>>>(idx, val, cap, n_kept, npix, out);

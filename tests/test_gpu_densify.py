@@ -72,3 +72,25 @@ def test_capacity_and_foreign_indices(small):
         assert np.array_equal(out[f].view(np.uint32), want.view(np.uint32)), f
     with pytest.raises(SepError):   # noise without deviations
         sep.densify(t["mean"], None, t["idx"], t["val"], t["n"], noise=torch.zeros((F, det.npix), device="cuda"))
+
+
+def test_odd_pixel_count_takes_the_scalar_kernel():
+    det = synth.Detector("odd", 37, 41, dist_m=0.05, center_px=(18.3, 20.1), nbins=12, split=2)
+    mask = np.zeros(det.npix, np.uint8)
+    mask[::11] = 1
+    W = oracle.weights(det, mask)
+    sep = Separator.from_detector(det, mask=mask)
+    rng = np.random.default_rng(4)
+    F, cap = 2, 40
+    mean = rng.uniform(1, 5, (F, W.nbins)).astype(np.float32)
+    sigma = rng.uniform(0, 1, (F, W.nbins)).astype(np.float32)
+    idx = np.stack([np.sort(rng.permutation(det.npix)[:cap]) for _ in range(F)]).astype(np.int32)
+    val = rng.uniform(100, 200, (F, cap)).astype(np.float32)
+    n_kept = np.array([cap, 7], np.int32)
+    z = rng.standard_normal((F, det.npix)).astype(np.float32)
+    t = [torch.from_numpy(a).cuda() for a in (mean, sigma, idx, val, n_kept, z)]
+    out = sep.densify(t[0], t[1], t[2], t[3], t[4], noise=t[5], fill=0.5).cpu().numpy()
+    for f in range(F):
+        k = int(n_kept[f])
+        want = oracle.densify(W, mean[f], sigma[f], idx[f, :k], val[f, :k], noise=z[f], fill=0.5)
+        assert np.array_equal(out[f].view(np.uint32), want.view(np.uint32)), f
