@@ -75,7 +75,7 @@ def lib():
         L.oracle_weights.argtypes = [C.POINTER(Geom), vp, C.c_int64, vp, vp, vp, vp, vp]
         L.oracle_weights.restype = C.c_int64
         L.oracle_integrate_clip.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, C.c_int32, vp, vp,
-                                            C.c_int32, C.c_double, vp, vp, vp, vp, vp, vp]
+                                            C.c_int32, C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp]
         L.oracle_integrate_clip.restype = C.c_int
         L.oracle_moments_subset.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp]
         L.oracle_moments_subset.restype = None
@@ -121,6 +121,12 @@ def jf_photons(raw, ped, gain):
     return out
 
 
+def chauvenet_k(n):
+    """Clip cut-off of Eq. 20 for a set of n entries: sqrt(2 ln(n / sqrt(2 pi)))
+    (None for n <= 2, where the logarithm is not positive: no clipping)."""
+    return math.sqrt(2.0 * math.log(n / math.sqrt(2.0 * math.pi))) if n > 2 else None
+
+
 def unit_range(det, mask=None):
     g = geom_of(det)
     lo, hi = C.c_double(), C.c_double()
@@ -152,8 +158,9 @@ def weights(det, mask=None) -> Weights:
     return Weights(pix[:n].copy(), b[:n].copy(), c[:n].copy(), bop, (rng[0], rng[1]), det.nbins, npix)
 
 
-def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=False):
-    """Integration (Eqs. 2, 8-13) and sigma-clipping (Eq. 19, Section 2.4) of one frame.
+def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=False, chauvenet=False):
+    """Integration (Eqs. 2, 8-13) and sigma-clipping (Eq. 19, Section 2.4) of one frame;
+    with ``chauvenet`` the cut-off of every step is Eq. 20's for the size of the set.
 
     Returns dict(mean, sigma, count, iters, band[, keep]) per bin."""
     sig = _c(signal, np.float32).reshape(-1)
@@ -163,7 +170,7 @@ def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=Fal
            "iters": np.zeros(B, np.int32), "band": np.zeros(B)}
     keep = np.zeros(W.pix.size, np.uint8) if want_keep else None
     rc = lib().oracle_integrate_clip(W.npix, W.pix.size, _p(W.pix), _p(W.bin), _p(W.c), B, _p(sig),
-                                     _p(nrm), n_iter, k, _p(out["mean"]), _p(out["sigma"]),
+                                     _p(nrm), n_iter, k, int(bool(chauvenet)), _p(out["mean"]), _p(out["sigma"]),
                                      _p(out["count"]), _p(out["iters"]), _p(out["band"]), _p(keep))
     assert rc == 0
     if want_keep:

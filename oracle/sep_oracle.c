@@ -236,8 +236,11 @@ static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, con
  *   S_0 = all entries of the bin;
  *   for t = 0 .. n_iter-1:
  *       (mu_t, sigma_t) = moments(S_t)
- *       S_{t+1} = { e in S_t : |v_e - mu_t| <= k sigma_t }   (reject iff >, Eq. 19)
+ *       S_{t+1} = { e in S_t : |v_e - mu_t| <= k_t sigma_t }   (reject iff >, Eq. 19)
  *       stop as soon as S_{t+1} == S_t (nothing discarded)
+ * with k_t = k, or with chauvenet != 0 the cut-off of Eq. 20 for the current
+ * set's size n_t = |S_t|: k_t = sqrt(2 ln(n_t / sqrt(2 pi))); a set of two
+ * entries or fewer (ln <= 0) is not clipped (the loop stops).
  *   report moments(S_final) for the last set computed, and |S_final|.
  * Discarded entries never come back. Entries with weight 0 take part in no
  * sum and are not counted.
@@ -252,8 +255,8 @@ static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, con
  */
 int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, const int32_t* e_bin,
                           const double* e_c, int32_t nbins, const float* signal, const float* norm,
-                          int32_t n_iter, double k, double* mean, double* sigma, int32_t* count,
-                          int32_t* iters, double* band, uint8_t* keep_out) {
+                          int32_t n_iter, double k, int32_t chauvenet, double* mean, double* sigma,
+                          int32_t* count, int32_t* iters, double* band, uint8_t* keep_out) {
   double* v = (double*)malloc(sizeof(double) * (size_t)npix);
   double* nrm = (double*)malloc(sizeof(double) * (size_t)npix);
   int64_t* start = (int64_t*)calloc((size_t)nbins + 1, sizeof(int64_t));
@@ -284,7 +287,12 @@ int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, con
     int32_t steps = 0;
     for (int32_t it = 0; it < n_iter; ++it) {
       moments_t mo = moments(m, eb, kb, e_c, e_pix, v, nrm);
-      double lim = k * mo.sigma;
+      double kt = k;
+      if (chauvenet) {
+        if (mo.count <= 2) break;
+        kt = sqrt(2.0 * log((double)mo.count / sqrt(2.0 * M_PI)));
+      }
+      double lim = kt * mo.sigma;
       double scale = fabs(mo.mu) + lim;
       if (scale < DBL_MIN) scale = DBL_MIN;
       int changed = 0;
@@ -471,7 +479,7 @@ int oracle_process_frames(int32_t rows, int32_t cols, int64_t n_ent, const int32
       memcpy(sig, (const float*)frames + (int64_t)f * npix, sizeof(float) * (size_t)npix);
     double* mu = mean + (int64_t)f * nbins;
     double* sd = sigma + (int64_t)f * nbins;
-    if (oracle_integrate_clip(npix, n_ent, e_pix, e_bin, e_c, nbins, sig, norm, n_iter, k_clip, mu,
+    if (oracle_integrate_clip(npix, n_ent, e_pix, e_bin, e_c, nbins, sig, norm, n_iter, k_clip, 0, mu,
                               sd, NULL, NULL, NULL, NULL))
       err = 1;
     n_kept[f] = (int32_t)oracle_sparsify(npix, bin_of_pixel, sig, norm, mu, sd, k_pick, 0, NULL, NULL);
