@@ -113,8 +113,17 @@ typedef struct {
                                 (sep_csr_attach_model) and verify it in at most n
                                 passes, else run the plain loop for that bin;
                                 needs precision SEP_PREC_DWORD */
-  int32_t reserved[3];       /* must be 0 */
+  int32_t cutoff;            /* SEP_CUTOFF_FIXED: every step clips at k_clip;
+                                SEP_CUTOFF_CHAUVENET: the cut-off of each step is
+                                Eq. 20's for the current set's size n,
+                                sqrt(2 ln(n / sqrt(2 pi))), and a set of two
+                                entries or fewer is not clipped (k_clip unused);
+                                needs surrogate == 0 */
+  int32_t reserved[2];       /* must be 0 */
 } sep_params;
+
+#define SEP_CUTOFF_FIXED     0
+#define SEP_CUTOFF_CHAUVENET 1
 
 /* One peak (Section 4). y, x: centroid in pixel units (row, column axes,
  * pixel centres at idx + 0.5); I: background-subtracted sum over the kept

@@ -21,6 +21,7 @@ SEP_DEV_CAPACITY, SEP_DEV_TIMEOUT = 0x1, 0x2
 SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM = 0, 1, 2
 SEP_DTYPE_F32, SEP_DTYPE_U16_JF = 0, 1
 SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE, SEP_PREC_DWORD = 0, 1, 2, 3
+SEP_CUTOFF_FIXED, SEP_CUTOFF_CHAUVENET = 0, 1
 
 STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OOM", 4: "SEP_ERR_CAPACITY",
                 5: "SEP_ERR_TIMEOUT", 6: "SEP_ERR_CSR", 7: "SEP_ERR_STATE"}
@@ -53,7 +54,7 @@ class sep_geometry(C.Structure):
 class sep_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
                 ("min_count", C.c_int32), ("precision", C.c_int32), ("surrogate", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("cutoff", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class sep_train_cfg(C.Structure):
@@ -201,10 +202,12 @@ def make_geometry(rows, cols, pixel_m, dist_m, center_px, wavelength_m, unit, nb
     return g
 
 
-def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD, surrogate=0):
+def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD, surrogate=0,
+                cutoff=SEP_CUTOFF_FIXED):
     p = sep_params()
     p.n_iter, p.k_clip, p.k_pick, p.patch, p.min_count, p.precision = n_iter, k_clip, k_pick, patch, min_count, precision
     p.surrogate = surrogate
+    p.cutoff = cutoff
     return p
 
 

@@ -416,9 +416,16 @@ __device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)
 // the set, its moments are evaluated and the next interval is the
 // intersection with [mu - k sd, mu + k sd] (Eq. 19, cumulative).
 // (have_moments: st already holds the moments of S'.)
+// Chauvenet's cut-off for a set of n entries (Eq. 20): sqrt(2 ln(n / sqrt(2 pi))),
+// n > 2 (FP32 library logarithm and square root).
+__device__ __forceinline__ float chauvenet_k(float n) {
+  return sqrtf(2.0f * logf(n * 0.3989422804014327f));
+}
+
 template <int PREC>
 __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&h)[6], const float (&l)[6], float Kf,
-                                          float Ln, float Hn, int n_iter, float k, bool have_moments = false) {
+                                          float Ln, float Hn, int n_iter, float k, bool have_moments = false,
+                                          int cutoff = SEP_CUTOFF_FIXED) {
   if (st.steps >= 0 && n_set == st.n_cur) {
     st.done = 1;
     return;
@@ -428,10 +435,12 @@ __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&
   st.H = Hn;
   if (!have_moments) finalise<PREC>(Kf, h, l, st);
   st.steps += 1;
-  if (st.steps >= n_iter) {
+  // (Chauvenet: a set of two or fewer is not clipped, the loop ends here)
+  if (st.steps >= n_iter || (cutoff == SEP_CUTOFF_CHAUVENET && n_set <= 2.0f)) {
     st.done = 1;
     return;
   }
+  if (cutoff == SEP_CUTOFF_CHAUVENET) k = chauvenet_k(n_set);
   float L2 = Ln, H2 = Hn;
   clip_bounds<PREC>(st, k, L2, H2);
   st.Ln = L2;
@@ -600,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           }
           if (choose_shift(st.mu_hi, st.sd) == 0.0f) {
             // the shift 0 suits this set: this was the first pass
-            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true);
+            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true, a.cutoff);
           } else {
             // cancellation about 0 is too large: the first pass runs again about the mean
             st.Kf = st.mu_hi;
@@ -778,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         if (lane == 0) {
           float n_set, h[6], l[6];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip);
+          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff);
         }
       }
       __syncthreads();

@@ -107,7 +107,11 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
   if (p->surrogate < 0 || p->surrogate > 8) return fail(ctx, SEP_ERR_ARG, "surrogate must be in [0, 8]");
   if (p->surrogate > 0 && p->precision != SEP_PREC_DWORD)
     return fail(ctx, SEP_ERR_ARG, "the surrogate runs in precision SEP_PREC_DWORD only");
-  for (int i = 0; i < 3; ++i)
+  if (p->cutoff != SEP_CUTOFF_FIXED && p->cutoff != SEP_CUTOFF_CHAUVENET)
+    return fail(ctx, SEP_ERR_ARG, "cutoff must be SEP_CUTOFF_FIXED or SEP_CUTOFF_CHAUVENET");
+  if (p->cutoff == SEP_CUTOFF_CHAUVENET && p->surrogate > 0)
+    return fail(ctx, SEP_ERR_ARG, "the surrogate predicts fixed-cut-off clipping only");
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return fail(ctx, SEP_ERR_ARG, "reserved params must be 0");
   return SEP_OK;
 }
@@ -228,6 +232,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.cap = std::max(csr->h.max_row, 1);
   a.n_iter = pr->n_iter;
   a.k_clip = pr->k_clip;
+  a.cutoff = pr->cutoff;
   a.k_pick = pr->k_pick;
   a.mean = mean;
   a.sigma = sigma;

@@ -66,6 +66,7 @@ struct ClipArgs {
   int32_t nbins, n_frames, frames_per_cta, cap;
   int32_t n_iter;
   float k_clip, k_pick;
+  int32_t cutoff = 0;      // SEP_CUTOFF_*: fixed k_clip, or Eq. 20 for each set's size
   float* mean;
   float* sigma;
   int32_t* count;

@@ -13,8 +13,8 @@ from parity import Frame, check_clip, check_frame, check_kept, check_peaks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2411_09515_gb300 import (SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN,  # noqa: E402
-                                    Separator, peaks_to_numpy)
+from paper_2411_09515_gb300 import (SEP_CUTOFF_CHAUVENET, SEP_PREC_DWORD, SEP_PREC_FP64MERGE,  # noqa: E402
+                                    SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator, peaks_to_numpy)
 
 
 def run_batch(sep, frames_np, kcap, pcap, use_graph=True):
@@ -319,3 +319,37 @@ def test_process_host_pipeline_equals_device_batch(jf_small):
         assert np.array_equal(pageable["val"][f, :n].numpy(), o_dev["val"][f, :n])
         assert np.array_equal(pageable["peaks"][f, :p].numpy(), o_dev["peaks"][f, :p])
     assert sep.device_status() == 0
+
+
+@pytest.mark.parametrize("precision", [SEP_PREC_DWORD, SEP_PREC_PLAIN])
+def test_chauvenet_cutoff_parity(jf_small, precision):
+    """Eq. 20's cut-off for each set's size, against the oracle: raw split
+    frames (coefficient classes), float frames without splitting (unit
+    weights) and with a norm (per-entry weights), several iteration limits."""
+    det, mask, cal, fr, W = jf_small
+    sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)
+    sep.set_params(cutoff=SEP_CUTOFF_CHAUVENET)
+    kcap = det.npix // 4
+    for n_iter in (1, 5, 30):
+        sep.set_params(n_iter=n_iter)
+        o, dfr = run_batch(sep, fr[:3], kcap, 20000)
+        bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+        for f in range(3):
+            sig = oracle.jf_photons(fr[f], cal[0], cal[1])
+            check_frame(det, W, sig, o, f, n_iter=n_iter, kcap=kcap, bounds=bnd[f], chauvenet=True)
+    det1 = synth.det_config1()
+    W1 = oracle.weights(det1)
+    fr1 = synth.frames(det1, synth.spec_config1(7), 0, 2)[0].astype(np.float32)
+    rng = np.random.default_rng(8)
+    norm = rng.uniform(0.5, 2.0, det1.npix).astype(np.float32)
+    for nrm in (None, norm):
+        sep1 = Separator.from_detector(det1, norm=nrm, precision=precision)
+        sep1.set_params(cutoff=SEP_CUTOFF_CHAUVENET)
+        x = fr1 if nrm is None else (fr1 * nrm).astype(np.float32)
+        o, dfr = run_batch(sep1, x, 8192, 512)
+        bnd = sep1.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+        for f in range(2):
+            check_frame(det1, W1, x[f], o, f, kcap=8192, bounds=bnd[f], norm=nrm, chauvenet=True)
+    sep.set_params(surrogate=1)
+    with pytest.raises(Exception):   # the surrogate predicts fixed-cut-off clipping only
+        sep.integrate_clip(torch.from_numpy(fr[:1].view(np.int16)).cuda())
