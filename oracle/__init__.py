@@ -75,9 +75,10 @@ def lib():
         L.oracle_weights.argtypes = [C.POINTER(Geom), vp, C.c_int64, vp, vp, vp, vp, vp]
         L.oracle_weights.restype = C.c_int64
         L.oracle_integrate_clip.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, C.c_int32, vp, vp,
-                                            C.c_int32, C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp]
+                                            C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double,
+                                            vp, vp, vp, vp, vp, vp]
         L.oracle_integrate_clip.restype = C.c_int
-        L.oracle_moments_subset.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp]
+        L.oracle_moments_subset.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_int32, C.c_double, vp]
         L.oracle_moments_subset.restype = None
         L.oracle_sparsify.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int64, vp, vp]
         L.oracle_sparsify.restype = C.c_int64
@@ -158,9 +159,16 @@ def weights(det, mask=None) -> Weights:
     return Weights(pix[:n].copy(), b[:n].copy(), c[:n].copy(), bop, (rng[0], rng[1]), det.nbins, npix)
 
 
-def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=False, chauvenet=False):
+ERROR_AZIMUTHAL, ERROR_POISSON, ERROR_HYBRID = 0, 1, 2
+
+
+def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=False, chauvenet=False,
+                   model=ERROR_AZIMUTHAL, dark=0.0):
     """Integration (Eqs. 2, 8-13) and sigma-clipping (Eq. 19, Section 2.4) of one frame;
-    with ``chauvenet`` the cut-off of every step is Eq. 20's for the size of the set.
+    with ``chauvenet`` the cut-off of every step is Eq. 20's for the size of the set;
+    ``model``: the deviation that clips and is reported (Section 2.4.1: azimuthal
+    Eq. 13, Poisson Eqs. 3-4 with dark variance ``dark``, or hybrid: azimuthal
+    clipping, Poisson deviation of the final set).
 
     Returns dict(mean, sigma, count, iters, band[, keep]) per bin."""
     sig = _c(signal, np.float32).reshape(-1)
@@ -170,7 +178,8 @@ def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=Fal
            "iters": np.zeros(B, np.int32), "band": np.zeros(B)}
     keep = np.zeros(W.pix.size, np.uint8) if want_keep else None
     rc = lib().oracle_integrate_clip(W.npix, W.pix.size, _p(W.pix), _p(W.bin), _p(W.c), B, _p(sig),
-                                     _p(nrm), n_iter, k, int(bool(chauvenet)), _p(out["mean"]), _p(out["sigma"]),
+                                     _p(nrm), n_iter, k, int(bool(chauvenet)), int(model), float(dark),
+                                     _p(out["mean"]), _p(out["sigma"]),
                                      _p(out["count"]), _p(out["iters"]), _p(out["band"]), _p(keep))
     assert rc == 0
     if want_keep:
@@ -178,14 +187,15 @@ def integrate_clip(W: Weights, signal, norm=None, n_iter=5, k=3.0, want_keep=Fal
     return out
 
 
-def moments_subset(pix, c, sel, signal, norm=None):
-    """(mu, sigma, count) of an explicit set of entries (Eqs. 8-13)."""
+def moments_subset(pix, c, sel, signal, norm=None, model=ERROR_AZIMUTHAL, dark=0.0):
+    """(mu, sigma, count) of an explicit set of entries (Eqs. 8-13; sigma of
+    the error model, as integrate_clip reports it)."""
     pix = _c(pix, np.int32)
     c = _c(c, np.float64)
     sel = _c(sel, np.uint8)
     o = np.zeros(3)
     lib().oracle_moments_subset(pix.size, _p(pix), _p(c), _p(sel), _p(_c(signal, np.float32)),
-                                _p(_c(norm, np.float32)), _p(o))
+                                _p(_c(norm, np.float32)), int(model), float(dark), _p(o))
     return o[0], o[1], int(o[2])
 
 

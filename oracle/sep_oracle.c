@@ -198,12 +198,20 @@ int64_t oracle_weights(const oracle_geom* g_in, const uint8_t* mask, int64_t cap
  *   sigma   = sqrt(VV / OmegaOm)            (Eq. 13; the deviation of one pixel, "std")
  * An empty set (Omega = 0) has mu = 0, sigma = 0.
  */
-typedef struct { double mu, sigma, omega; int64_t count; } moments_t;
+/*
+ * sigma_p: the deviation of one pixel under the Poisson model (Eqs. 3 and 4
+ * of Section 2.2): every pixel's variance is its signal plus the dark
+ * variance, var_i = signal_i + dark (Eq. 3), propagated with squared
+ * coefficients (Eq. 4) and normalised like sigma (the deviation of one
+ * pixel, so that Eq. 5 turns it into the error of the mean):
+ * sigma_p^2 = sum c^2 var_i / sum c^2 norm^2.
+ */
+typedef struct { double mu, sigma, omega, sigma_p; int64_t count; } moments_t;
 
 static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, const double* ec,
-                         const int32_t* epix, const double* v, const double* nrm) {
-  moments_t r = {0.0, 0.0, 0.0, 0};
-  double Om = 0.0, V = 0.0, OO = 0.0, VV = 0.0;
+                         const int32_t* epix, const double* v, const double* nrm, double dark) {
+  moments_t r = {0.0, 0.0, 0.0, 0.0, 0};
+  double Om = 0.0, V = 0.0, OO = 0.0, VV = 0.0, VP = 0.0;
   for (int64_t t = 0; t < m; ++t) {
     if (!keep[t]) continue;
     int64_t e = ent[t];
@@ -223,9 +231,11 @@ static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, con
     double d = v[epix[e]] - mu;
     OO += w * w;
     VV += w * w * d * d;
+    VP += ec[e] * ec[e] * (v[epix[e]] * nrm[epix[e]] + dark);
   }
   r.mu = mu;
   r.sigma = sqrt(VV / OO);
+  r.sigma_p = VP > 0.0 ? sqrt(VP / OO) : 0.0;
   r.omega = Om;
   return r;
 }
@@ -241,6 +251,9 @@ static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, con
  * with k_t = k, or with chauvenet != 0 the cut-off of Eq. 20 for the current
  * set's size n_t = |S_t|: k_t = sqrt(2 ln(n_t / sqrt(2 pi))); a set of two
  * entries or fewer (ln <= 0) is not clipped (the loop stops).
+ * Error model (Section 2.4.1): 0 azimuthal (sigma_t, Eq. 13, clips and is
+ * reported), 1 Poisson (sigma_p clips and is reported), 2 hybrid (sigma
+ * clips, sigma_p of the final set is reported); dark: the dark variance.
  *   report moments(S_final) for the last set computed, and |S_final|.
  * Discarded entries never come back. Entries with weight 0 take part in no
  * sum and are not counted.
@@ -255,8 +268,9 @@ static moments_t moments(int64_t m, const int64_t* ent, const uint8_t* keep, con
  */
 int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, const int32_t* e_bin,
                           const double* e_c, int32_t nbins, const float* signal, const float* norm,
-                          int32_t n_iter, double k, int32_t chauvenet, double* mean, double* sigma,
-                          int32_t* count, int32_t* iters, double* band, uint8_t* keep_out) {
+                          int32_t n_iter, double k, int32_t chauvenet, int32_t model, double dark,
+                          double* mean, double* sigma, int32_t* count, int32_t* iters, double* band,
+                          uint8_t* keep_out) {
   double* v = (double*)malloc(sizeof(double) * (size_t)npix);
   double* nrm = (double*)malloc(sizeof(double) * (size_t)npix);
   int64_t* start = (int64_t*)calloc((size_t)nbins + 1, sizeof(int64_t));
@@ -286,13 +300,13 @@ int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, con
     double bmin = INFINITY;
     int32_t steps = 0;
     for (int32_t it = 0; it < n_iter; ++it) {
-      moments_t mo = moments(m, eb, kb, e_c, e_pix, v, nrm);
+      moments_t mo = moments(m, eb, kb, e_c, e_pix, v, nrm, dark);
       double kt = k;
       if (chauvenet) {
         if (mo.count <= 2) break;
         kt = sqrt(2.0 * log((double)mo.count / sqrt(2.0 * M_PI)));
       }
-      double lim = kt * mo.sigma;
+      double lim = kt * (model == 1 ? mo.sigma_p : mo.sigma);
       double scale = fabs(mo.mu) + lim;
       if (scale < DBL_MIN) scale = DBL_MIN;
       int changed = 0;
@@ -310,9 +324,9 @@ int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, con
       memcpy(kb, nb, (size_t)m);
       steps += 1;
     }
-    moments_t fin = moments(m, eb, kb, e_c, e_pix, v, nrm);
+    moments_t fin = moments(m, eb, kb, e_c, e_pix, v, nrm, dark);
     mean[b] = fin.mu;
-    sigma[b] = fin.sigma;
+    sigma[b] = model == 0 ? fin.sigma : fin.sigma_p;
     if (count) count[b] = (int32_t)fin.count;
     if (iters) iters[b] = steps;
     if (band) band[b] = bmin;
@@ -328,8 +342,8 @@ int oracle_integrate_clip(int64_t npix, int64_t n_ent, const int32_t* e_pix, con
  * set chosen elsewhere (same definitions as above).
  */
 void oracle_moments_subset(int64_t m, const int32_t* pix, const double* c, const uint8_t* sel,
-                           const float* signal, const float* norm, double* out3) {
-  double Om = 0, V = 0, OO = 0, VV = 0;
+                           const float* signal, const float* norm, int32_t model, double dark, double* out3) {
+  double Om = 0, V = 0, OO = 0, VV = 0, VP = 0;
   int64_t cnt = 0;
   for (int64_t t = 0; t < m; ++t) {
     if (!sel[t]) continue;
@@ -349,9 +363,10 @@ void oracle_moments_subset(int64_t m, const int32_t* pix, const double* c, const
     double d = (double)signal[pix[t]] / nr - mu;
     OO += w * w;
     VV += w * w * d * d;
+    VP += c[t] * c[t] * ((double)signal[pix[t]] + dark);
   }
   out3[0] = mu;
-  out3[1] = Om == 0.0 ? 0.0 : sqrt(VV / OO);
+  out3[1] = Om == 0.0 ? 0.0 : (model == 0 ? sqrt(VV / OO) : (VP > 0.0 ? sqrt(VP / OO) : 0.0));
   out3[2] = (double)(Om == 0.0 ? 0 : cnt);
 }
 
@@ -479,8 +494,8 @@ int oracle_process_frames(int32_t rows, int32_t cols, int64_t n_ent, const int32
       memcpy(sig, (const float*)frames + (int64_t)f * npix, sizeof(float) * (size_t)npix);
     double* mu = mean + (int64_t)f * nbins;
     double* sd = sigma + (int64_t)f * nbins;
-    if (oracle_integrate_clip(npix, n_ent, e_pix, e_bin, e_c, nbins, sig, norm, n_iter, k_clip, 0, mu,
-                              sd, NULL, NULL, NULL, NULL))
+    if (oracle_integrate_clip(npix, n_ent, e_pix, e_bin, e_c, nbins, sig, norm, n_iter, k_clip, 0, 0, 0.0,
+                              mu, sd, NULL, NULL, NULL, NULL))
       err = 1;
     n_kept[f] = (int32_t)oracle_sparsify(npix, bin_of_pixel, sig, norm, mu, sd, k_pick, 0, NULL, NULL);
     n_peaks[f] = (int32_t)oracle_peaks(rows, cols, bin_of_pixel, sig, norm, mu, sd, k_pick, patch,

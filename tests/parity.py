@@ -43,13 +43,15 @@ def close(a, b, rtol=RTOL, sd=None):
 class Frame:
     """Oracle view of one frame: values, clip results, thresholds."""
 
-    def __init__(self, W, signal, n_iter, k_clip, k_pick, norm=None, chauvenet=False):
+    def __init__(self, W, signal, n_iter, k_clip, k_pick, norm=None, chauvenet=False, model=0, dark=0.0):
         self.W = W
+        self.model, self.dark = model, dark
         self.sig = np.ascontiguousarray(signal, np.float32).reshape(-1)
         self.norm = norm
         self.v = self.sig.astype(np.float64) / (1.0 if norm is None else norm.astype(np.float64))
         self.k_clip, self.k_pick, self.n_iter = k_clip, k_pick, n_iter
-        self.ref = oracle.integrate_clip(W, self.sig, norm=norm, n_iter=n_iter, k=k_clip, chauvenet=chauvenet)
+        self.ref = oracle.integrate_clip(W, self.sig, norm=norm, n_iter=n_iter, k=k_clip, chauvenet=chauvenet,
+                                         model=model, dark=dark)
         self.order = np.argsort(W.bin, kind="stable")
         self.start = np.searchsorted(W.bin[self.order], np.arange(W.nbins + 1))
 
@@ -75,7 +77,7 @@ def check_clip(fr: Frame, mean, sigma, count, bounds):
         L, H = bounds[b]
         vv = fr.sig[pix]
         sel = (vv >= L) & (vv <= H)
-        mu, sd, n = oracle.moments_subset(pix, c, sel.astype(np.uint8), fr.sig, fr.norm)
+        mu, sd, n = oracle.moments_subset(pix, c, sel.astype(np.uint8), fr.sig, fr.norm, model=fr.model, dark=fr.dark)
         assert close(mean[b], mu, sd=np.array(sd)) and close(sigma[b], sd, sd=np.array(sd)) and count[b] == n, \
             (b, mean[b], mu, sigma[b], sd, count[b], n)
         moved.append((b, mu, sd))
@@ -160,11 +162,11 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3):
 
 
 def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None,
-                chauvenet=False):
+                chauvenet=False, model=0, dark=0.0):
     """Frame f of a batch's outputs `o` (numpy arrays as returned by the
     library) against the oracle on the frame's signal. Returns (banded bins,
     bins on another trajectory, excused pixels)."""
-    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm, chauvenet=chauvenet)
+    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm, chauvenet=chauvenet, model=model, dark=dark)
     if bounds is None:
         bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
     nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
