@@ -119,11 +119,24 @@ typedef struct {
                                 sqrt(2 ln(n / sqrt(2 pi))), and a set of two
                                 entries or fewer is not clipped (k_clip unused);
                                 needs surrogate == 0 */
-  int32_t reserved[2];       /* must be 0 */
+  int32_t error_model;       /* the deviation that clips and is reported
+                                (Section 2.4.1): SEP_ERROR_AZIMUTHAL, the spread
+                                of the bin's values (Eq. 13); SEP_ERROR_POISSON,
+                                each pixel's variance is its value plus dark_var
+                                (Eq. 3), propagated with squared coefficients
+                                (Eq. 4, normalised as Eq. 13: sigma^2 =
+                                sum c^2 (v + dark_var) / sum c^2); SEP_ERROR_HYBRID,
+                                azimuthal clipping, Poisson deviation of the
+                                final set. Poisson and hybrid: frames without a
+                                norm, surrogate == 0 */
+  float dark_var;            /* dark-noise variance sigma_dark^2 of Eq. 3, >= 0 */
 } sep_params;
 
 #define SEP_CUTOFF_FIXED     0
 #define SEP_CUTOFF_CHAUVENET 1
+#define SEP_ERROR_AZIMUTHAL  0
+#define SEP_ERROR_POISSON    1
+#define SEP_ERROR_HYBRID     2
 
 /* One peak (Section 4). y, x: centroid in pixel units (row, column axes,
  * pixel centres at idx + 0.5); I: background-subtracted sum over the kept

@@ -15,12 +15,14 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (PEAK_DTYPE, SEP_CUTOFF_CHAUVENET, SEP_CUTOFF_FIXED, SEP_DTYPE_F32, SEP_DTYPE_U16_JF,
+                       SEP_ERROR_AZIMUTHAL, SEP_ERROR_HYBRID, SEP_ERROR_POISSON,
                        SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, SEP_UNIT_2TH_DEG,
                        SEP_UNIT_Q_NM, SEP_UNIT_R_MM, SepError)
 
 __all__ = ["Context", "Separator", "Surrogate", "process_mixed", "SepError", "PEAK_DTYPE", "peaks_to_numpy", "SEP_DTYPE_F32", "SEP_DTYPE_U16_JF",
            "SEP_PREC_PLAIN", "SEP_PREC_KAHAN", "SEP_PREC_FP64MERGE", "SEP_PREC_DWORD", "SEP_UNIT_2TH_DEG", "SEP_UNIT_Q_NM",
-           "SEP_UNIT_R_MM", "SEP_CUTOFF_FIXED", "SEP_CUTOFF_CHAUVENET"]
+           "SEP_UNIT_R_MM", "SEP_CUTOFF_FIXED", "SEP_CUTOFF_CHAUVENET", "SEP_ERROR_AZIMUTHAL", "SEP_ERROR_POISSON",
+           "SEP_ERROR_HYBRID"]
 
 
 def peaks_to_numpy(peaks, n):

@@ -22,6 +22,7 @@ SEP_UNIT_2TH_DEG, SEP_UNIT_Q_NM, SEP_UNIT_R_MM = 0, 1, 2
 SEP_DTYPE_F32, SEP_DTYPE_U16_JF = 0, 1
 SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE, SEP_PREC_DWORD = 0, 1, 2, 3
 SEP_CUTOFF_FIXED, SEP_CUTOFF_CHAUVENET = 0, 1
+SEP_ERROR_AZIMUTHAL, SEP_ERROR_POISSON, SEP_ERROR_HYBRID = 0, 1, 2
 
 STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OOM", 4: "SEP_ERR_CAPACITY",
                 5: "SEP_ERR_TIMEOUT", 6: "SEP_ERR_CSR", 7: "SEP_ERR_STATE"}
@@ -54,7 +55,7 @@ class sep_geometry(C.Structure):
 class sep_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
                 ("min_count", C.c_int32), ("precision", C.c_int32), ("surrogate", C.c_int32),
-                ("cutoff", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("cutoff", C.c_int32), ("error_model", C.c_int32), ("dark_var", C.c_float)]
 
 
 class sep_train_cfg(C.Structure):

@@ -95,6 +95,8 @@ struct Bcast {
   float L, H;          // interval of the current set
   float n_cur;         // entries (weight != 0) in the current set
   int steps, done;
+  float sdP;           // Poisson deviation of the current set (error models 1, 2)
+  double sdP_d;        // FP64MERGE
 };
 
 // Error-free sum: a + b = s + e exactly.
@@ -416,6 +418,41 @@ __device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)
 // the set, its moments are evaluated and the next interval is the
 // intersection with [mu - k sd, mu + k sd] (Eq. 19, cumulative).
 // (have_moments: st already holds the moments of S'.)
+// Poisson deviation of a set (Eqs. 3-4, normalised as Eq. 13): each
+// value's variance is the value plus the dark variance, weighted by the
+// squared coefficients: sdP^2 = sum w^2 v / sum w^2 + dark = Kf + B1 / OO +
+// dark from the pass's sums about Kf (0 when negative or the set is empty).
+template <int PREC>
+__device__ __forceinline__ void poisson_sd(float Kf, const float (&hi)[6], const float (&lo)[6], float dark,
+                                           Bcast& st) {
+  // hi/lo layout: 0 Omega, 1 A1, 2 OO, 3 B1, 4 B2
+  if (hi[2] == 0.0f) {
+    st.sdP = 0.0f;
+    st.sdP_d = 0.0;
+    return;
+  }
+  if (PREC == SEP_PREC_FP64MERGE) {
+    const double OO = (double)hi[2] + lo[2], B1 = (double)hi[3] + lo[3];
+    const double var = (double)Kf + B1 / OO + (double)dark;
+    st.sdP_d = var > 0.0 ? sqrt(var) : 0.0;
+    st.sdP = (float)st.sdP_d;
+    return;
+  }
+  const float corr = __fdiv_rn(__fadd_rn(hi[3], lo[3]), __fadd_rn(hi[2], lo[2]));
+  float s, e;
+  two_sum(Kf, corr, s, e);
+  const float var = __fadd_rn(s, __fadd_rn(e, dark));
+  st.sdP = var > 0.0f ? __fsqrt_rn(var) : 0.0f;
+  st.sdP_d = st.sdP;
+}
+
+// The reported (and, for the Poisson model, clipping) deviation becomes the
+// Poisson one.
+__device__ __forceinline__ void use_poisson(Bcast& st) {
+  st.sd = st.sdP;
+  st.sd_d = st.sdP_d;
+}
+
 // Chauvenet's cut-off for a set of n entries (Eq. 20): sqrt(2 ln(n / sqrt(2 pi))),
 // n > 2 (FP32 library logarithm and square root).
 __device__ __forceinline__ float chauvenet_k(float n) {
@@ -425,8 +462,10 @@ __device__ __forceinline__ float chauvenet_k(float n) {
 template <int PREC>
 __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&h)[6], const float (&l)[6], float Kf,
                                           float Ln, float Hn, int n_iter, float k, bool have_moments = false,
-                                          int cutoff = SEP_CUTOFF_FIXED) {
+                                          int cutoff = SEP_CUTOFF_FIXED, int model = SEP_ERROR_AZIMUTHAL,
+                                          float dark = 0.0f) {
   if (st.steps >= 0 && n_set == st.n_cur) {
+    if (model == SEP_ERROR_HYBRID) use_poisson(st);   // the final set's Poisson deviation
     st.done = 1;
     return;
   }
@@ -434,9 +473,14 @@ __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&
   st.L = Ln;
   st.H = Hn;
   if (!have_moments) finalise<PREC>(Kf, h, l, st);
+  if (model != SEP_ERROR_AZIMUTHAL) {
+    poisson_sd<PREC>(Kf, h, l, dark, st);
+    if (model == SEP_ERROR_POISSON) use_poisson(st);
+  }
   st.steps += 1;
   // (Chauvenet: a set of two or fewer is not clipped, the loop ends here)
   if (st.steps >= n_iter || (cutoff == SEP_CUTOFF_CHAUVENET && n_set <= 2.0f)) {
+    if (model == SEP_ERROR_HYBRID) use_poisson(st);
     st.done = 1;
     return;
   }
@@ -609,7 +653,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
           }
           if (choose_shift(st.mu_hi, st.sd) == 0.0f) {
             // the shift 0 suits this set: this was the first pass
-            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true, a.cutoff);
+            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true, a.cutoff,
+                            a.error_model, a.dark_var);
           } else {
             // cancellation about 0 is too large: the first pass runs again about the mean
             st.Kf = st.mu_hi;
@@ -787,7 +832,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
         if (lane == 0) {
           float n_set, h[6], l[6];
           unpack_totals<MODE>(th, tl, n_set, h, l);
-          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff);
+          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model,
+                          a.dark_var);
         }
       }
       __syncthreads();

@@ -111,8 +111,12 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
     return fail(ctx, SEP_ERR_ARG, "cutoff must be SEP_CUTOFF_FIXED or SEP_CUTOFF_CHAUVENET");
   if (p->cutoff == SEP_CUTOFF_CHAUVENET && p->surrogate > 0)
     return fail(ctx, SEP_ERR_ARG, "the surrogate predicts fixed-cut-off clipping only");
-  for (int i = 0; i < 2; ++i)
-    if (p->reserved[i] != 0) return fail(ctx, SEP_ERR_ARG, "reserved params must be 0");
+  if (p->error_model != SEP_ERROR_AZIMUTHAL && p->error_model != SEP_ERROR_POISSON &&
+      p->error_model != SEP_ERROR_HYBRID)
+    return fail(ctx, SEP_ERR_ARG, "error_model must be SEP_ERROR_AZIMUTHAL, _POISSON or _HYBRID");
+  if (!(p->dark_var >= 0.0f) || !isfinite(p->dark_var)) return fail(ctx, SEP_ERR_ARG, "dark_var must be finite and >= 0");
+  if (p->error_model != SEP_ERROR_AZIMUTHAL && p->surrogate > 0)
+    return fail(ctx, SEP_ERR_ARG, "the surrogate predicts azimuthal-model clipping only");
   return SEP_OK;
 }
 
@@ -132,6 +136,8 @@ sep_status check_common(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
   }
   sep_status st = check_params(ctx, params);
   if (st != SEP_OK) return st;
+  if (params->error_model != SEP_ERROR_AZIMUTHAL && csr->has_norm)
+    return fail(ctx, SEP_ERR_ARG, "the Poisson and hybrid models take frames without a norm");
   if (params->surrogate > 0 && !csr->model) return fail(ctx, SEP_ERR_STATE, "surrogate requested but no model attached");
   if (params->surrogate > 0 && csr->model->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "model belongs to another context");
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -233,6 +239,8 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.n_iter = pr->n_iter;
   a.k_clip = pr->k_clip;
   a.cutoff = pr->cutoff;
+  a.error_model = pr->error_model;
+  a.dark_var = pr->dark_var;
   a.k_pick = pr->k_pick;
   a.mean = mean;
   a.sigma = sigma;

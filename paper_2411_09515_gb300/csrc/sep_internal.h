@@ -67,6 +67,8 @@ struct ClipArgs {
   int32_t n_iter;
   float k_clip, k_pick;
   int32_t cutoff = 0;      // SEP_CUTOFF_*: fixed k_clip, or Eq. 20 for each set's size
+  int32_t error_model = 0; // SEP_ERROR_*: azimuthal, Poisson or hybrid deviation
+  float dark_var = 0.0f;   // dark variance of the Poisson model (Eq. 3)
   float* mean;
   float* sigma;
   int32_t* count;

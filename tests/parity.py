@@ -118,10 +118,14 @@ def check_kept(fr: Frame, idx, val, n_kept, moved, capacity=None):
     return set(diff.tolist())
 
 
-def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3):
-    """Peak list against the oracle's, computed on the oracle's thresholds."""
+def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3, truncated=False):
+    """Peak list against the oracle's, computed on the oracle's thresholds
+    (truncated: the list filled its capacity, so it is compared up to its
+    last pixel)."""
     ref = oracle.peaks(det, fr.W, fr.sig, fr.ref["mean"], fr.ref["sigma"], k_pick=fr.k_pick, patch=patch,
                        min_count=min_count, norm=fr.norm)
+    if truncated and len(peaks):
+        ref = ref[ref["idx"] <= peaks["idx"][-1]]
     cols = det.cols
     h = patch // 2
 
@@ -171,8 +175,9 @@ def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, 
         bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
     nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
     excused = check_kept(fr, o["idx"][f], o["val"][f], o["n_kept"][f], moved, capacity=kcap)
+    pcap = o["peaks"].shape[1]
     peaks = o["peaks"][f][: int(o["n_peaks"][f])].copy().view(np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"),
                                                                       ("I", "<f4"), ("sigma", "<f4"),
                                                                       ("npix", "<i4")])).reshape(-1)
-    check_peaks(det, fr, peaks, excused)
+    check_peaks(det, fr, peaks, excused, truncated=int(o["n_peaks"][f]) > pcap)
     return nb, len(moved), len(excused)

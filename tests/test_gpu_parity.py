@@ -13,8 +13,9 @@ from parity import Frame, check_clip, check_frame, check_kept, check_peaks
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2411_09515_gb300 import (SEP_CUTOFF_CHAUVENET, SEP_PREC_DWORD, SEP_PREC_FP64MERGE,  # noqa: E402
-                                    SEP_PREC_KAHAN, SEP_PREC_PLAIN, Separator, peaks_to_numpy)
+from paper_2411_09515_gb300 import (SEP_CUTOFF_CHAUVENET, SEP_ERROR_HYBRID, SEP_ERROR_POISSON,  # noqa: E402
+                                    SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN, SEP_PREC_PLAIN, SepError,
+                                    Separator, peaks_to_numpy)
 
 
 def run_batch(sep, frames_np, kcap, pcap, use_graph=True):
@@ -353,3 +354,37 @@ def test_chauvenet_cutoff_parity(jf_small, precision):
     sep.set_params(surrogate=1)
     with pytest.raises(Exception):   # the surrogate predicts fixed-cut-off clipping only
         sep.integrate_clip(torch.from_numpy(fr[:1].view(np.int16)).cuda())
+
+
+@pytest.mark.parametrize("precision", [SEP_PREC_DWORD, SEP_PREC_FP64MERGE])
+def test_poisson_and_hybrid_error_models_parity(jf_small, precision):
+    """Section 2.4.1's Poisson and hybrid models (Eqs. 3-4) against the
+    oracle: raw split frames and float frames with unit coefficients, with and
+    without a dark variance, and with Chauvenet's cut-off."""
+    det, mask, cal, fr, W = jf_small
+    det1 = synth.det_config1()
+    W1 = oracle.weights(det1)
+    fr1 = synth.frames(det1, synth.spec_config1(5), 0, 2)[0].astype(np.float32)
+    for model in (SEP_ERROR_POISSON, SEP_ERROR_HYBRID):
+        for dark, chauv in ((0.0, False), (1.5, False), (0.0, True)):
+            cut = SEP_CUTOFF_CHAUVENET if chauv else 0
+            sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)
+            sep.set_params(error_model=model, dark_var=dark, cutoff=cut)
+            kcap = det.npix // 2
+            o, dfr = run_batch(sep, fr[:2], kcap, 100000)   # emptied bins keep every positive pixel
+            bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+            for f in range(2):
+                sig = oracle.jf_photons(fr[f], cal[0], cal[1])
+                check_frame(det, W, sig, o, f, kcap=kcap, bounds=bnd[f], chauvenet=chauv, model=model, dark=dark)
+            sep1 = Separator.from_detector(det1, precision=precision)
+            sep1.set_params(error_model=model, dark_var=dark, cutoff=cut)
+            o, dfr = run_batch(sep1, fr1, 16384, 512)
+            bnd = sep1.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+            for f in range(2):
+                check_frame(det1, W1, fr1[f], o, f, kcap=16384, bounds=bnd[f], chauvenet=chauv, model=model, dark=dark)
+    # a norm is refused (the Poisson variance is defined on unnormalised frames)
+    norm = np.full(det1.npix, 2.0, np.float32)
+    sepn = Separator.from_detector(det1, norm=norm)
+    sepn.set_params(error_model=SEP_ERROR_POISSON)
+    with pytest.raises(SepError):
+        sepn.integrate_clip(torch.from_numpy(fr1).cuda())
