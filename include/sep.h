@@ -275,6 +275,28 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
                        float* out_dev, sep_stream stream);
 
 /*
+ * Veto (Section 4, "Peak count as veto algorithm"): frame f passes when it
+ * has at least min_peaks peaks (n_peaks_dev[f] >= min_peaks; frames with fewer
+ * are discarded). Writes the passing frames' indices in ascending order to
+ * frame_list_dev [n_frames] (int32; the first *n_pass_dev entries are
+ * meaningful) and their count to n_pass_dev (int32 [1]). One CTA; n_frames
+ * <= 2^24. min_peaks >= 0.
+ */
+sep_status sep_veto(sep_ctx* ctx, int32_t n_frames, const int32_t* n_peaks_dev, int32_t min_peaks,
+                    int32_t* frame_list_dev, int32_t* n_pass_dev, sep_stream stream);
+
+/*
+ * Frame-drop compaction after sep_veto: row j of dst_dev becomes row
+ * frame_list_dev[j] of src_dev for j < *n_pass_dev (rows of row_bytes bytes,
+ * a multiple of 4; n_frames rows at most); rows of dst_dev past the count are
+ * left as they were. Works for any per-frame output array (mean, sigma,
+ * kept lists, peak records, ...). src and dst must not overlap.
+ */
+sep_status sep_compact_frames(sep_ctx* ctx, int32_t n_frames, const int32_t* frame_list_dev,
+                              const int32_t* n_pass_dev, int64_t row_bytes, const void* src_dev, void* dst_dev,
+                              sep_stream stream);
+
+/*
  * The whole path on a batch in one call: integrate + clip, sparsify and peak
  * picking, with the kept-pixel map passed between the steps on the device.
  * Outputs as in the three calls above. The launch sequence is captured once

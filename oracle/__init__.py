@@ -214,6 +214,12 @@ def sparsify(W: Weights, signal, mean, sigma, k_pick=3.0, norm=None):
     return idx, val
 
 
+def veto(n_peaks, min_peaks):
+    """Section 4 ("Peak count as veto algorithm"): the frames kept are those
+    with at least min_peaks peaks (fewer: discarded), in frame order."""
+    return [f for f, n in enumerate(n_peaks) if n >= min_peaks]
+
+
 def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan):
     """Decompression of Section 3 ("Densification / Decompression"): the
     background of every pixel with a radial bin is its bin's mean level, with

@@ -226,6 +226,25 @@ class Separator:
         B.sep_densify(self.ctx, self.csr, F, mean, sigma, idx, val, kcap, n_kept, noise, fill, out, stream)
         return out
 
+    def veto(self, n_peaks, min_peaks, stream=None):
+        """Frames with at least ``min_peaks`` peaks (Section 4's veto):
+        (ascending frame list [F], count [1]) on the device."""
+        t = self.torch
+        F = int(n_peaks.shape[0])
+        frame_list = t.empty(F, dtype=t.int32, device=n_peaks.device)
+        n_pass = t.empty(1, dtype=t.int32, device=n_peaks.device)
+        B.sep_veto(self.ctx, F, n_peaks, min_peaks, frame_list, n_pass, stream)
+        return frame_list, n_pass
+
+    def compact_frames(self, frame_list, n_pass, src, out=None, stream=None):
+        """Rows of the passing frames of a per-frame output, moved to the
+        front (row j = row frame_list[j]); rows past the count are untouched."""
+        if out is None:
+            out = self.torch.empty_like(src)
+        F = int(src.shape[0])
+        B.sep_compact_frames(self.ctx, F, frame_list, n_pass, src[0].numel() * src.element_size(), src, out, stream)
+        return out
+
     def alloc_outputs(self, F, kept_capacity, peak_capacity, device=None):
         t = self.torch
         dev = device if device is not None else t.device("cuda", self.device)

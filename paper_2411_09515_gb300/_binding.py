@@ -35,7 +35,7 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
            "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct",
-           "sep_process_host", "sep_densify"]
+           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 
@@ -112,6 +112,8 @@ def lib():
                                     _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
     L.sep_peakfind.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp, _vp,
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
+    L.sep_veto.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
+    L.sep_compact_frames.argtypes = [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp, _vp, _vp]
     L.sep_densify.argtypes = [_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
                                     _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
@@ -326,6 +328,16 @@ def sep_peakfind(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, 
     _check(ctx, lib().sep_peakfind(ctx, csr, calib, _ptr(frames), dtype, n_frames, C.byref(params), _ptr(mean),
                                    _ptr(sigma), _ptr(idx), _ptr(n_kept), kept_capacity, _ptr(peaks), capacity,
                                    _ptr(n_peaks), _stream(stream)))
+
+
+def sep_veto(ctx, n_frames, n_peaks, min_peaks, frame_list, n_pass, stream=None):
+    _check(ctx, lib().sep_veto(ctx, n_frames, _ptr(n_peaks), int(min_peaks), _ptr(frame_list), _ptr(n_pass),
+                               _stream(stream)))
+
+
+def sep_compact_frames(ctx, n_frames, frame_list, n_pass, row_bytes, src, dst, stream=None):
+    _check(ctx, lib().sep_compact_frames(ctx, n_frames, _ptr(frame_list), _ptr(n_pass), int(row_bytes), _ptr(src),
+                                         _ptr(dst), _stream(stream)))
 
 
 def sep_densify(ctx, csr, n_frames, mean, sigma, idx, val, kept_capacity, n_kept, noise, fill, out, stream=None):

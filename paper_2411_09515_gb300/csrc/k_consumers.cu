@@ -233,6 +233,45 @@ __global__ void __launch_bounds__(256) k_dense_scatter(const int32_t* idx, const
   }
 }
 
+// Veto (Section 4): the frames with at least min_peaks peaks, ascending, by
+// one CTA scanning the counts in tiles of its size.
+__global__ void __launch_bounds__(1024) k_veto(int32_t n_frames, const int32_t* n_peaks, int32_t min_peaks,
+                                               int32_t* list, int32_t* n_pass) {
+  __shared__ int sh[32];
+  int base = 0;
+  for (int f0 = 0; f0 < n_frames; f0 += 1024) {
+    const int f = f0 + threadIdx.x;
+    const int pass = f < n_frames && n_peaks[f] >= min_peaks;
+    int total;
+    const int pos = base + block_exclusive_scan<1024>(pass, &total, sh);
+    if (pass) list[pos] = f;
+    base += total;
+  }
+  if (threadIdx.x == 0) *n_pass = base;
+}
+
+// Row j of dst = row list[j] of src for j < *n_pass (32-bit words; 16-byte
+// vectors when rows and bases allow).
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_compact_rows(const int32_t* list, const int32_t* n_pass, int64_t row_words,
+                                                      const uint32_t* src, uint32_t* dst) {
+  const int64_t j = blockIdx.y;
+  if (j >= *n_pass) return;
+  const int64_t r = list[j];
+  if (r < 0 || r >= gridDim.y) return;   // (a caller's list is not trusted)
+  const uint32_t* s = src + r * row_words;
+  uint32_t* d = dst + j * row_words;
+  if (VEC) {
+    const int64_t n4 = row_words >> 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x)
+      reinterpret_cast<uint4*>(d)[q] = __ldg(reinterpret_cast<const uint4*>(s) + q);
+  } else {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < row_words;
+         q += (int64_t)gridDim.x * blockDim.x)
+      d[q] = __ldg(s + q);
+  }
+}
+
 // Indices outside the detector are ignored (a caller's list is not trusted).
 __global__ void k_scatter_list(const int32_t* idx, const int32_t* n_kept, int64_t kcap, int64_t npix,
                                uint32_t* bitmap, int64_t words) {
@@ -459,6 +498,28 @@ cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int3
     dim3 g2((unsigned)std::min<int64_t>((cap + 255) / 256, 64), (unsigned)n_frames);
     k_dense_scatter<<<g2, 256, 0, s>>>(idx, val, cap, n_kept, npix, out);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_veto(int32_t n_frames, const int32_t* n_peaks, int32_t min_peaks, int32_t* list, int32_t* n_pass,
+                        cudaStream_t s) {
+  k_veto<<<1, 1024, 0, s>>>(n_frames, n_peaks, min_peaks, list, n_pass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_rows(int32_t n_frames, const int32_t* list, const int32_t* n_pass, int64_t row_bytes,
+                                const void* src, void* dst, cudaStream_t s) {
+  if (n_frames <= 0 || row_bytes <= 0) return cudaSuccess;
+  const int64_t words = row_bytes / 4;
+  const bool vec = words % 4 == 0 && (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0;
+  const int64_t per = vec ? words / 4 : words;
+  dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>((per + 255) / 256, 1), 64), (unsigned)n_frames);
+  if (vec)
+    k_compact_rows<true><<<grid, 256, 0, s>>>(list, n_pass, words, static_cast<const uint32_t*>(src),
+                                               static_cast<uint32_t*>(dst));
+  else
+    k_compact_rows<false><<<grid, 256, 0, s>>>(list, n_pass, words, static_cast<const uint32_t*>(src),
+                                                static_cast<uint32_t*>(dst));
   return cudaGetLastError();
 }
 

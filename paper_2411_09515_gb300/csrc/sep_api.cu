@@ -695,6 +695,34 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
   return SEP_OK;
 }
 
+sep_status sep_veto(sep_ctx* ctx, int32_t n_frames, const int32_t* n_peaks_dev, int32_t min_peaks,
+                    int32_t* frame_list_dev, int32_t* n_pass_dev, sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (n_frames < 0 || n_frames > (1 << 24) || min_peaks < 0) return fail(ctx, SEP_ERR_ARG, "n_frames or min_peaks");
+  if (!n_pass_dev || (n_frames > 0 && (!n_peaks_dev || !frame_list_dev))) return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaError_t e = sep::launch_veto(n_frames, n_peaks_dev, min_peaks, frame_list_dev, n_pass_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "veto launch");
+  return SEP_OK;
+}
+
+sep_status sep_compact_frames(sep_ctx* ctx, int32_t n_frames, const int32_t* frame_list_dev,
+                              const int32_t* n_pass_dev, int64_t row_bytes, const void* src_dev, void* dst_dev,
+                              sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (n_frames < 0 || row_bytes < 0 || row_bytes % 4) return fail(ctx, SEP_ERR_ARG, "n_frames or row_bytes");
+  if (n_frames == 0 || row_bytes == 0) return SEP_OK;
+  if (!frame_list_dev || !n_pass_dev || !src_dev || !dst_dev) return fail(ctx, SEP_ERR_ARG, "NULL argument");
+  const char *s0 = static_cast<const char*>(src_dev), *d0 = static_cast<const char*>(dst_dev);
+  const int64_t span = row_bytes * n_frames;
+  if (s0 < d0 + span && d0 < s0 + span) return fail(ctx, SEP_ERR_ARG, "src and dst overlap");
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaError_t e = sep::launch_compact_rows(n_frames, frame_list_dev, n_pass_dev, row_bytes, src_dev, dst_dev,
+                                           (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "compact launch");
+  return SEP_OK;
+}
+
 sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                              int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                              float* sigma_dev, int32_t* count_dev, int32_t* idx_dev, float* val_dev,

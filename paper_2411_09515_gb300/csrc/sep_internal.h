@@ -142,6 +142,12 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
 cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,
                            const float* sigma, const int32_t* idx, const float* val, int64_t cap,
                            const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s);
+// Veto (Section 4): ascending list of the frames with >= min_peaks peaks.
+cudaError_t launch_veto(int32_t n_frames, const int32_t* n_peaks, int32_t min_peaks, int32_t* list, int32_t* n_pass,
+                        cudaStream_t s);
+// Rows list[j] of src to rows j of dst, j < *n_pass (row_bytes a multiple of 4).
+cudaError_t launch_compact_rows(int32_t n_frames, const int32_t* list, const int32_t* n_pass, int64_t row_bytes,
+                                const void* src, void* dst, cudaStream_t s);
 // Staged values back to image order (NaN where a pixel has no position).
 cudaError_t launch_unstage(const float* stage, int64_t stride, const int32_t* pos_of, int64_t npix, int32_t n_frames,
                            float* out, cudaStream_t s);
