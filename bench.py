@@ -245,6 +245,8 @@ def run_ours(args):
 
     # densification (Section 3) of the batch's sparse output, timed alone
     dens = densify_eval(sep, out, F, stream, args)
+    # the clip variants of Section 2.4 on the same batch, and the veto
+    variants = variants_eval(sep, dev, out, kcap, pcap, stream, args)
 
     # the learned surrogate against the plain loop on the same batch
     sur = None
@@ -283,6 +285,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "surrogate": sur,
             "densify": dens,
+            "variants": variants,
             "device_status": status,
             "mean_kept_per_frame": float(n_kept.mean()), "mean_peaks_per_frame": float(n_peaks.mean()),
             "setup_s": round(t_gen, 1),
@@ -290,6 +293,50 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def variants_eval(sep, dev, out, kcap, pcap, stream, args):
+    """Whole-path frames/s with Chauvenet's cut-off (Eq. 20) and with the
+    Poisson and hybrid error models (Section 2.4.1) on the benchmark batch,
+    and the time of the veto (Section 4) with the compaction of the kept lists
+    and peak records of the passing frames."""
+    import torch
+    from paper_2411_09515_gb300 import SEP_CUTOFF_CHAUVENET, SEP_ERROR_HYBRID, SEP_ERROR_POISSON
+    F = dev.shape[0]
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    base = (sep.params.cutoff, sep.params.error_model)
+    for name, kw in (("chauvenet", {"cutoff": SEP_CUTOFF_CHAUVENET}), ("poisson", {"error_model": SEP_ERROR_POISSON}),
+                     ("hybrid", {"error_model": SEP_ERROR_HYBRID})):
+        sep.set_params(**kw)
+        ms = timed(lambda: sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream), 3)
+        res[name] = {"frames_s": round(F / (ms * 1e-3), 1), "ms_per_step": round(ms, 3)}
+        sep.set_params(cutoff=base[0], error_model=base[1])
+    sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)   # the plain outputs again
+    dst = {k: torch.empty_like(out[k]) for k in ("idx", "val", "peaks", "n_kept", "n_peaks")}
+    thr = 20
+
+    def veto_step():
+        lst, n = sep.veto(out["n_peaks"], thr, stream=stream)
+        for k in dst:
+            sep.compact_frames(lst, n, out[k], out=dst[k], stream=stream)
+        return n
+
+    ms = timed(veto_step, 5)
+    n = int(veto_step().item())
+    res["veto"] = {"min_peaks": thr, "frames_passed": n, "frames": F, "ms": round(ms, 3)}
+    return res
 
 
 def densify_eval(sep, out, F, stream, args):
