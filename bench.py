@@ -98,6 +98,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest value of x over the ranks of the process group (x itself
+    with one process): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(frames_per_rank, steps, world, ms):
+    """Frames per second of the whole job: every rank processes its own
+    frames_per_rank frames per step (weak scaling), in ms for all steps."""
+    return frames_per_rank * steps * world / (ms * 1e-3)
+
+
 def setup_workload(F, rank, seed=2024):
     import synth
     det = synth.det_jf4m(split=2, nbins=1000)
@@ -194,11 +212,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), device=f"cuda:{local}")
     status = sep.device_status()
     n_kept = out["n_kept"].cpu().numpy()
     n_peaks = out["n_peaks"].cpu().numpy()
@@ -237,11 +251,7 @@ def run_ours(args):
         sep.process_host(host, host_out, kcap, pcap, chunk_frames=args.chunk_frames, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), device=f"cuda:{local}")
 
     # densification (Section 3) of the batch's sparse output, timed alone
     dens = densify_eval(sep, out, F, stream, args)
@@ -263,7 +273,7 @@ def run_ours(args):
         nvalid = int((mask == 0).sum())
         alg = algorithmic_bytes_clip(F, det.npix, nvalid, info["nnz"], info["nbins"])
         achieved = alg / (k_ms * 1e-3) / 1e9
-        value = F * args.steps * world / (ms * 1e-3)
+        value = whole_job_rate(F, args.steps, world, ms)
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -278,7 +288,7 @@ def run_ours(args):
                          "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": measured_traffic(F),
                          "peak_source": src, "kernel_ms": round(k_ms, 4),
                          "algorithmic_bytes_per_launch": alg},
-            "e2e": {"value": round(F * args.steps * world / (e2e_ms * 1e-3), 2), "unit": UNIT,
+            "e2e": {"value": round(whole_job_rate(F, args.steps, world, e2e_ms), 2), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "chunk_frames": args.chunk_frames},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
