@@ -93,7 +93,11 @@ typedef struct {
   double wavelength_m;       /* metres (used by SEP_UNIT_Q_NM) */
   int32_t unit;              /* SEP_UNIT_* radial unit of the bins */
   int32_t nbins;             /* number of radial bins, 1 .. SEP_MAX_BINS */
-  int32_t split;             /* 1: no splitting; 2: 2 x 2 sub-pixel centres */
+  int32_t split;             /* 1: no splitting; 2: 2 x 2 sub-pixel centres;
+                                0: exact area fractions (the area of the pixel
+                                between the bin's two circles on the detector
+                                plane over the pixel's area; per-entry weights,
+                                a pixel may span at most 15 bins) */
   double range[2];           /* [lo, hi] in the unit; NaN = automatic (min/max over valid sub-pixel centres) */
 } sep_geometry;
 

@@ -144,6 +144,121 @@ class Weights:
         self.bin_of_pixel, self.range, self.nbins, self.npix = bin_of_pixel, rng, nbins, npix
 
 
+def _radius_of(det, x):
+    """Detector-plane radius (m) of the radial value x in det's unit (R9 inverted)."""
+    x = float(x)
+    if det.unit == 2:                                   # r in mm
+        R = x * 1e-3
+    else:
+        if det.unit == 0:                               # 2theta in degrees
+            tth = math.radians(x)
+        else:                                           # q in nm^-1
+            sarg = x * det.wavelength_m * 1e9 / (4 * math.pi)
+            tth = math.pi if sarg >= 1 else 2 * math.asin(sarg)
+        R = math.inf if tth >= math.pi / 2 else det.dist_m * math.tan(tth)
+    return max(R, 0.0)
+
+
+def _unit_of(det, R):
+    if det.unit == 2:
+        return R * 1e3
+    tth = math.atan2(R, det.dist_m)
+    if det.unit == 0:
+        return tth * (180 / math.pi)
+    return 4 * math.pi * math.sin(0.5 * tth) / (det.wavelength_m * 1e9)
+
+
+def _rect_in_disc(x0, x1, y0, y1, R):
+    """Area of [x0, x1] x [y0, y1] inside the disc of radius R about the
+    origin: the integral over x of the chord of the rectangle's column inside
+    the circle, split where the circle crosses the rectangle's top and bottom."""
+    if R <= 0:
+        return 0.0
+    if math.isinf(R):
+        return (x1 - x0) * (y1 - y0)
+    a, b = max(x0, -R), min(x1, R)
+    if a >= b:
+        return 0.0
+
+    def S(t):   # integral of sqrt(R^2 - u^2) from 0 to t
+        t = min(max(t, -R), R)
+        return 0.5 * (t * math.sqrt(max(R * R - t * t, 0.0)) + R * R * math.asin(t / R))
+
+    cuts = [a, b]
+    for y in (y0, y1):
+        if abs(y) < R:
+            u = math.sqrt(R * R - y * y)
+            cuts += [u, -u]
+    cuts = sorted(c for c in set(cuts) if a <= c <= b)
+    area = 0.0
+    for u, v in zip(cuts[:-1], cuts[1:]):
+        m = 0.5 * (u + v)
+        h = math.sqrt(max(R * R - m * m, 0.0))
+        top_is_circle, bot_is_circle = h < y1, -h > y0
+        top = h if top_is_circle else y1
+        bot = -h if bot_is_circle else y0
+        if top <= bot:
+            continue
+        seg = 0.0
+        seg += (S(v) - S(u)) if top_is_circle else y1 * (v - u)
+        seg -= -(S(v) - S(u)) if bot_is_circle else y0 * (v - u)
+        area += seg
+    return area
+
+
+def weights_exact(det, mask=None) -> Weights:
+    """c_{i,r} of Section 2.2 as the exact fraction of pixel i's area falling
+    into radial bin r: the bin's edges (in det's unit) are circles on the
+    detector plane, and c is the pixel's area between them over the pixel's
+    area. The range is det.range, or (NaN) the span of the valid pixels'
+    nearest and farthest points. The threshold bin of a pixel is the bin of
+    its centre (R10). Plain Python, for small detectors."""
+    rows, cols = det.rows, det.cols
+    py, px = det.pixel_m
+    cx, cy = det.center_px
+    m = np.zeros(rows * cols, np.uint8) if mask is None else np.asarray(mask, np.uint8).reshape(-1)
+    lo, hi = det.range
+
+    def extent(r, c):
+        x0, x1 = (c - cx) * px, (c + 1 - cx) * px
+        y0, y1 = (r - cy) * py, (r + 1 - cy) * py
+        nx = x0 if x0 > 0 else (x1 if x1 < 0 else 0.0)
+        ny = y0 if y0 > 0 else (y1 if y1 < 0 else 0.0)
+        fx, fy = max(abs(x0), abs(x1)), max(abs(y0), abs(y1))
+        return (x0, x1, y0, y1), _unit_of(det, math.hypot(nx, ny)), _unit_of(det, math.hypot(fx, fy))
+
+    if math.isnan(lo) or math.isnan(hi):
+        ex = [extent(r, c)[1:] for r in range(rows) for c in range(cols) if not m[r * cols + c]]
+        lo = min(e[0] for e in ex) if math.isnan(lo) else lo
+        hi = max(e[1] for e in ex) if math.isnan(hi) else hi
+    B = det.nbins
+    edges_R = [_radius_of(det, lo + (hi - lo) * k / B) for k in range(B + 1)]
+    pix, bins, cs = [], [], []
+    for r in range(rows):
+        for c in range(cols):
+            i = r * cols + c
+            if m[i]:
+                continue
+            (x0, x1, y0, y1), umin, umax = extent(r, c)
+            if umax < lo or umin > hi:
+                continue
+            t0 = (max(umin, lo) - lo) / (hi - lo) * B
+            t1 = (min(umax, hi) - lo) / (hi - lo) * B
+            for b in range(max(int(math.floor(t0)), 0), min(int(math.floor(t1)), B - 1) + 1):
+                f = (_rect_in_disc(x0, x1, y0, y1, edges_R[b + 1]) - _rect_in_disc(x0, x1, y0, y1, edges_R[b])) / (px * py)
+                if f > 1e-12:
+                    pix.append(i)
+                    bins.append(b)
+                    cs.append(min(f, 1.0))
+    # threshold bins: the pixel centres' bins on the same range (the C oracle's R9 sequence)
+    import copy
+    d1 = copy.copy(det)
+    d1.split, d1.range = 1, (lo, hi)
+    bop = weights(d1, mask).bin_of_pixel
+    return Weights(np.asarray(pix, np.int32), np.asarray(bins, np.int32), np.asarray(cs, np.float64), bop, (lo, hi),
+                   B, rows * cols)
+
+
 def weights(det, mask=None) -> Weights:
     g = geom_of(det)
     m = _c(mask, np.uint8)

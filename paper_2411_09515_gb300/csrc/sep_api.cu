@@ -161,7 +161,7 @@ sep::PixArgs pix_args(const sep_csr* csr, const sep_calib* calib, const void* fr
 sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
   int optin = 0;
   SEP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->has_norm) + 1024;  // + static shared memory
+  const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->weighted) + 1024;  // + static shared memory
   if (need > (size_t)optin) {
     char buf[160];
     snprintf(buf, sizeof buf, "largest bin (%d entries) needs %zu bytes of shared memory, device allows %d",
@@ -291,7 +291,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
   if (csr->plan.empty()) {
     a.bin_list = nullptr;
     a.cap = std::max(csr->h.max_row, 4);
-    return sep::launch_integrate_clip(a, csr->h.nbins, 256, split, csr->has_norm, precision, mode, s);
+    return sep::launch_integrate_clip(a, csr->h.nbins, 256, split, csr->weighted, precision, mode, s);
   }
   const int nc = (int)csr->plan.size();
   if (nc == 1 || mode == 1 || !allow_fork) {
@@ -299,7 +299,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
       a.bin_list = k.d_bins;
       a.cap = k.cap;
       a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
-      cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->has_norm, precision, mode, s);
+      cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->weighted, precision, mode, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -313,7 +313,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
     a.cap = k.cap;
     a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
     if (e == cudaSuccess)
-      e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->has_norm, precision, mode, si);
+      e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->weighted, precision, mode, si);
     if (e == cudaSuccess && i > 0) e = cudaEventRecord(ctx->ev_join[i], si);
   }
   for (int i = 1; i < nc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, ctx->ev_join[i], 0);
@@ -421,6 +421,7 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
   c->npix = (int64_t)c->h.rows * c->h.cols;
   c->nnz = (int64_t)c->h.ent.size();
   c->has_norm = norm_host != nullptr;
+  c->weighted = c->has_norm || c->h.split == 0;
   if (!ctx) {  // host-only matrix: inspection only
     *out = c;
     return SEP_OK;
@@ -439,7 +440,7 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
       (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
-      (c->has_norm && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
+      (c->weighted && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
       (c->has_norm && (st = upload(ctx, &c->d_norm, norm_host, (size_t)c->npix)) != SEP_OK)) {
     sep_csr_destroy(c);
     return st;

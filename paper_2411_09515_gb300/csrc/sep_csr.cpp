@@ -2,7 +2,10 @@
 //
 // The coefficient c_{i,r} is the fraction of pixel i falling into radial bin
 // r; it is measured with split x split sub-pixel centres, so c = k / split^2
-// with k the number of centres of pixel i inside bin r. The radial value of a
+// with k the number of centres of pixel i inside bin r, or (split 0) as the
+// exact area fraction: the bin's edges map to detector radii and c is the
+// area of the pixel between the two circles over the pixel's area
+// (rectangle-disc intersections in closed form, binary64). The radial value of a
 // point and its bin follow one fixed sequence of binary64 operations (the
 // definition the tests compare against):
 //   dy = (row + fy - cy) * pixel_y,  dx = (col + fx - cx) * pixel_x,
@@ -38,6 +41,55 @@ inline double radial(const Geo& g, int64_t row, int64_t col, double fy, double f
   return 4.0 * M_PI * sin(0.5 * tth) / (g.lam * 1.0e9);
 }
 
+// Detector-plane radius (metres) of a radial value and back (the unit's
+// function of r in radial(), inverted); radii below 0 clamp to 0.
+inline double radius_of(const Geo& g, double x) {
+  double R;
+  if (g.unit == SEP_UNIT_R_MM) {
+    R = x * 1.0e-3;
+  } else {
+    double tth;
+    if (g.unit == SEP_UNIT_2TH_DEG) {
+      tth = x * (M_PI / 180.0);
+    } else {
+      const double sarg = x * g.lam * 1.0e9 / (4.0 * M_PI);
+      tth = sarg >= 1.0 ? M_PI : 2.0 * asin(sarg);
+    }
+    R = tth >= 0.5 * M_PI ? std::numeric_limits<double>::infinity() : g.dist * tan(tth);
+  }
+  return R > 0.0 ? R : 0.0;
+}
+inline double unit_of(const Geo& g, double R) {
+  if (g.unit == SEP_UNIT_R_MM) return R * 1.0e3;
+  const double tth = atan2(R, g.dist);
+  if (g.unit == SEP_UNIT_2TH_DEG) return tth * (180.0 / M_PI);
+  return 4.0 * M_PI * sin(0.5 * tth) / (g.lam * 1.0e9);
+}
+
+// Area of the disc of radius R about the origin inside the quadrant
+// rectangle [0, x] x [0, y] (x, y >= 0): the column under the circle,
+// G(t) = integral_0^t sqrt(R^2 - u^2) du = (t sqrt(R^2 - t^2) + R^2 asin(t / R)) / 2.
+inline double quadrant_area(double x, double y, double R) {
+  if (R <= 0.0 || x <= 0.0 || y <= 0.0) return 0.0;
+  auto G = [R](double t) { return 0.5 * (t * sqrt(std::max(R * R - t * t, 0.0)) + R * R * asin(std::min(t / R, 1.0))); };
+  const double xc = std::min(x, R);
+  if (y >= R) return G(xc);
+  const double us = sqrt(R * R - y * y);   // where the circle leaves the top edge y
+  if (xc <= us) return xc * y;
+  return us * y + G(xc) - G(us);
+}
+// signed: the area in [0, x] x [0, y] with orientation sign(x) sign(y)
+inline double corner_area(double x, double y, double R) {
+  const double a = quadrant_area(fabs(x), fabs(y), R);
+  return (x < 0) != (y < 0) ? -a : a;
+}
+// Area of the rectangle [x0, x1] x [y0, y1] inside the disc of radius R.
+inline double rect_disc_area(double x0, double x1, double y0, double y1, double R) {
+  if (!(R > 0.0)) return 0.0;
+  if (isinf(R)) return (x1 - x0) * (y1 - y0);
+  return corner_area(x1, y1, R) - corner_area(x0, y1, R) - corner_area(x1, y0, R) + corner_area(x0, y0, R);
+}
+
 inline int32_t bin_index(double x, double lo, double hi, int32_t B) {
   if (!(x >= lo && x <= hi)) return -1;
   double t = (x - lo) / (hi - lo) * (double)B;
@@ -55,12 +107,14 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   if (rows <= 0 || cols <= 0) return "rows and cols must be positive";
   if (rows * cols > (int64_t)SEP_MAX_PIXELS) return "rows * cols exceeds SEP_MAX_PIXELS";
   if (gm.nbins < 1 || gm.nbins > SEP_MAX_BINS) return "nbins out of range";
-  if (gm.split != 1 && gm.split != 2) return "split must be 1 or 2";
+  if (gm.split != 0 && gm.split != 1 && gm.split != 2) return "split must be 0 (exact area), 1 or 2";
   if (gm.unit < 0 || gm.unit > 2) return "unknown unit";
   if (!(gm.dist_m > 0) || !(gm.pixel_m[0] > 0) || !(gm.pixel_m[1] > 0)) return "distance and pixel size must be > 0";
   if (gm.unit == SEP_UNIT_Q_NM && !(gm.wavelength_m > 0)) return "wavelength must be > 0 for q";
   const int64_t npix = rows * cols;
-  const int s = gm.split;
+  // exact: area fractions (one weighted class); else s x s sub-pixel centres
+  const bool exact = gm.split == 0;
+  const int s = exact ? 1 : gm.split;
   Geo g{gm.pixel_m[0], gm.pixel_m[1], gm.dist_m, gm.center_px[0], gm.center_px[1], gm.wavelength_m, gm.unit};
   double off[2];
   for (int a = 0; a < s; ++a) off[a] = ((double)a + 0.5) / (double)s;
@@ -78,6 +132,16 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     for (int64_t row = 0; row < rows; ++row)
       for (int64_t col = 0; col < cols; ++col) {
         if (mask && mask[row * cols + col]) continue;
+        if (exact) {   // the whole pixel: its nearest and farthest points
+          const double x0 = ((double)col - g.cx) * g.px, x1 = x0 + g.px;
+          const double y0 = ((double)row - g.cy) * g.py, y1 = y0 + g.py;
+          const double nx = x0 > 0 ? x0 : (x1 < 0 ? x1 : 0.0), ny = y0 > 0 ? y0 : (y1 < 0 ? y1 : 0.0);
+          const double fx = std::max(fabs(x0), fabs(x1)), fy = std::max(fabs(y0), fabs(y1));
+          const double a = unit_of(g, sqrt(nx * nx + ny * ny)), b = unit_of(g, sqrt(fx * fx + fy * fy));
+          mn = a < mn ? a : mn;
+          mx = b > mx ? b : mx;
+          continue;
+        }
         for (int a = 0; a < s; ++a)
           for (int b = 0; b < s; ++b) {
             double x = radial(g, row, col, off[a], off[b]);
@@ -91,10 +155,14 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   if (!(hi > lo)) return "empty radial range (no valid pixel, or lo >= hi)";
   const int32_t B = gm.nbins;
 
-  // per pixel: up to s*s (bin, k) pairs + centre bin
-  const int maxe = s * s + 1;
+  // per pixel: up to s*s (bin, k) pairs + centre bin (exact: up to kMaxExact
+  // bins with their area fractions in pc, k = 1; a carrier has k = 0)
+  constexpr int kMaxExact = 15;
+  const int maxe = exact ? kMaxExact + 1 : s * s + 1;
   std::vector<int32_t> pb((size_t)npix * maxe, -1);
   std::vector<uint8_t> pk((size_t)npix * maxe, 0);
+  std::vector<double> pc(exact ? (size_t)npix * maxe : 0, 0.0);
+  int too_many = 0;
   std::vector<uint8_t> pn((size_t)npix, 0);
   std::vector<int32_t> bop((size_t)npix, -1);
   std::vector<float> xcen((size_t)npix, 0.0f);   // radial value of the pixel centre (staging order)
@@ -108,6 +176,53 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       int32_t bc = xc < lo ? 0 : (xc > hi ? B - 1 : bin_index(xc, lo, hi, B));
       bop[i] = bc;
       xcen[i] = (float)xc;
+      if (exact) {
+        int32_t* eb = &pb[(size_t)i * maxe];
+        uint8_t* ek = &pk[(size_t)i * maxe];
+        double* ec = &pc[(size_t)i * maxe];
+        const double x0 = ((double)col - g.cx) * g.px, x1 = x0 + g.px;
+        const double y0 = ((double)row - g.cy) * g.py, y1 = y0 + g.py;
+        const double nx = x0 > 0 ? x0 : (x1 < 0 ? x1 : 0.0), ny = y0 > 0 ? y0 : (y1 < 0 ? y1 : 0.0);
+        const double fx = std::max(fabs(x0), fabs(x1)), fy = std::max(fabs(y0), fabs(y1));
+        const double umin = unit_of(g, sqrt(nx * nx + ny * ny)), umax = unit_of(g, sqrt(fx * fx + fy * fy));
+        int n = 0;
+        bool has_centre = false;
+        if (umax >= lo && umin <= hi) {
+          const int32_t b0 = bin_index(std::max(umin, lo), lo, hi, B), b1 = bin_index(std::min(umax, hi), lo, hi, B);
+          const double area = g.px * g.py;
+          for (int32_t b = b0; b <= b1 && b >= 0; ++b) {
+            const double elo = lo + (hi - lo) * (double)b / (double)B;
+            const double ehi = lo + (hi - lo) * (double)(b + 1) / (double)B;
+            const double c = (rect_disc_area(x0, x1, y0, y1, radius_of(g, ehi)) -
+                              rect_disc_area(x0, x1, y0, y1, radius_of(g, elo))) / area;
+            if (!(c > 1e-12)) continue;
+            if (n == kMaxExact) {
+              too_many = 1;
+              break;
+            }
+            eb[n] = b;
+            ek[n] = 1;
+            ec[n] = std::min(c, 1.0);
+            ++n;
+            if (b == bc) has_centre = true;
+          }
+        }
+        if (!has_centre) {   // threshold carrier of zero weight, kept in bin order
+          int p = n;
+          while (p > 0 && eb[p - 1] > bc) {
+            eb[p] = eb[p - 1];
+            ek[p] = ek[p - 1];
+            ec[p] = ec[p - 1];
+            --p;
+          }
+          eb[p] = bc;
+          ek[p] = 0;
+          ec[p] = 0.0;
+          ++n;
+        }
+        pn[i] = (uint8_t)n;
+        continue;
+      }
       int32_t sb[4];
       int m = 0;
       for (int a = 0; a < s; ++a)
@@ -142,6 +257,8 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       pn[i] = (uint8_t)n;
     }
   }
+
+  if (too_many) return "exact area fractions: a pixel spans more than 15 bins (bins far narrower than pixels)";
 
   // Row layout (one row per bin): entries grouped by coefficient class,
   // largest coefficient first (class c holds k = s*s - c sub-pixels, c = 0 ..
@@ -178,7 +295,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   const int64_t nnz = pos;
   out->ent.assign((size_t)nnz, kPad);
   out->coef.assign((size_t)nnz, 0.0f);
-  if (norm) out->w.assign((size_t)nnz, 0.0f);
+  if (norm || exact) out->w.assign((size_t)nnz, 0.0f);   // per-entry weights c * norm
   const double inv = 1.0 / (double)(s * s);
   for (int64_t i = 0; i < npix; ++i) {
     for (int t = 0; t < pn[i]; ++t) {
@@ -191,9 +308,9 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       else u |= (uint32_t)(k - 1) << kKShift;
       if (b == bop[i]) u |= kCentre;
       out->ent[e] = u;
-      const double cf = (double)k * inv;
+      const double cf = exact ? pc[(size_t)i * maxe + t] : (double)k * inv;
       out->coef[e] = (float)cf;
-      if (norm) out->w[e] = (float)(cf * (double)norm[i]);
+      if (norm || exact) out->w[e] = (float)(cf * (norm ? (double)norm[i] : 1.0));
     }
   }
   // Staging order of the pixel values. The clip kernel gathers each bin's
@@ -266,12 +383,12 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
           const int64_t e = grp_e[k].second;
           ent2[k] = (out->ent[e] & ~kColMask) | grp_e[k].first;
           coef2[k] = out->coef[e];
-          if (norm) w2[k] = out->w[e];
+          if (!out->w.empty()) w2[k] = out->w[e];
         }
         for (size_t k = 0; k < grp_e.size(); ++k) {
           out->ent[g0 + (int64_t)k] = ent2[k];
           out->coef[g0 + (int64_t)k] = coef2[k];
-          if (norm) out->w[g0 + (int64_t)k] = w2[k];
+          if (!out->w.empty()) out->w[g0 + (int64_t)k] = w2[k];
         }
       }
     }
@@ -287,7 +404,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   out->rows = gm.rows;
   out->cols = gm.cols;
   out->nbins = B;
-  out->split = s;
+  out->split = gm.split;   // 0: exact area fractions
   out->lo = lo;
   out->hi = hi;
   out->max_row = max_row;

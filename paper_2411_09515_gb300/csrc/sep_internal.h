@@ -227,7 +227,8 @@ struct sep_csr {
   std::vector<sep_clip_class> plan;   // empty = one class of every bin at 256 threads
   uint64_t plan_version = 0;
   int64_t npix = 0, nnz = 0;
-  bool has_norm = false;
+  bool has_norm = false;   // values are divided by a norm (Eq. 1)
+  bool weighted = false;   // per-entry weights c * norm (a norm, or exact area fractions)
   int32_t* d_rowptr = nullptr;
   uint32_t* d_ent = nullptr;
   int32_t* d_cpix = nullptr;          // pixel of each centre entry, else -1

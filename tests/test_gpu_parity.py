@@ -388,3 +388,22 @@ def test_poisson_and_hybrid_error_models_parity(jf_small, precision):
     sepn.set_params(error_model=SEP_ERROR_POISSON)
     with pytest.raises(SepError):
         sepn.integrate_clip(torch.from_numpy(fr1).cuda())
+
+
+@pytest.mark.parametrize("precision", [SEP_PREC_DWORD, SEP_PREC_FP64MERGE])
+def test_exact_area_coefficients_parity(precision):
+    """Exact area fractions (split 0: per-entry weights) against the oracle's
+    own fractions, plain clipping and the Poisson model, with a mask."""
+    det = synth.Detector("exact", 96, 110, dist_m=0.05, center_px=(40.3, 50.7), nbins=40, split=0,
+                         unit=synth.UNIT_2TH_DEG)
+    mask = np.zeros(det.npix, np.uint8)
+    mask[::29] = 1
+    W = oracle.weights_exact(det, mask)
+    fr = synth.frames(det, synth.spec_config1(9), 0, 3, mask=mask)[0].astype(np.float32)
+    for model in (0, SEP_ERROR_POISSON):
+        sep = Separator.from_detector(det, mask=mask, precision=precision)
+        sep.set_params(error_model=model)
+        o, dfr = run_batch(sep, fr, det.npix, 4000)
+        bnd = sep.integrate_clip(dfr, bounds=True)["bounds"].cpu().numpy()
+        for f in range(3):
+            check_frame(det, W, fr[f], o, f, kcap=det.npix, bounds=bnd[f], model=model)
