@@ -352,18 +352,19 @@ def variants_eval(sep, dev, out, kcap, pcap, stream, args):
 def densify_eval(sep, out, F, stream, args):
     """Dense frames rebuilt from the batch's per-bin levels and kept lists,
     without and with a noisy background (normal deviates drawn once, outside
-    the timed region). Algorithmic bytes per frame: the dense frame written
-    (4N), the kept list read (8 per kept pixel), mean and sigma (8B), and the
-    deviates read (4N) with noise."""
+    the timed region), and with the radially interpolated profile.
+    Algorithmic bytes per frame: the dense frame written (4N), the kept list
+    read (8 per kept pixel), mean and sigma (8B), and the deviates read (4N)
+    with noise; the interpolation table (8N) once per launch."""
     import torch
     N = sep.npix
     dense = torch.empty((F, N), dtype=torch.float32, device=out["mean"].device)
     z = torch.randn((F, N), dtype=torch.float32, device=out["mean"].device)
     kept = int(out["n_kept"].clamp(max=out["idx"].shape[1]).sum().item())
     res = {}
-    for name, noise in (("plain", None), ("noise", z)):
+    for name, noise, smooth in (("plain", None, False), ("noise", z, False), ("smooth_noise", z, True)):
         run = lambda: sep.densify(out["mean"], out["sigma"], out["idx"], out["val"], out["n_kept"], noise=noise,
-                                  out=dense, stream=stream)
+                                  out=dense, interpolate=smooth, stream=stream)
         for _ in range(2):
             run()
         torch.cuda.synchronize()
@@ -374,7 +375,8 @@ def densify_eval(sep, out, F, stream, args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        nbytes = 4 * N * F + 8 * kept + 8 * sep.nbins * F + (4 * N * F if noise is not None else 0)
+        nbytes = 4 * N * F + 8 * kept + 8 * sep.nbins * F + (4 * N * F if noise is not None else 0) + \
+            (8 * N if smooth else 0)
         gbs = nbytes / (ms * 1e-3) / 1e9
         res[name] = {"frames_s": round(F / (ms * 1e-3), 1), "ms": round(ms, 3), "achieved_gbs": round(gbs, 1),
                      "frac_of_hbm": round(gbs / peaks_file()[0]["hbm_gbs"], 4), "peak_source": peaks_file()[1]}

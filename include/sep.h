@@ -263,10 +263,15 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
 /*
  * Densification (Section 3, "Densification / Decompression"): rebuild dense
  * frames from their sparse form. Every pixel with a centre bin b gets the
- * bin's background level mean_dev[f][b]; when noise_dev is given (standard
- * normal deviates z, float32 [n_frames][npix], drawn by the caller) it gets
- * RN32(mean_b + RN32(sigma_b * z_i)) instead (the noisy background some
- * reduction programs need); then the first min(n_kept[f], kept_capacity)
+ * bin's background level m_i = mean_dev[f][b] (s_i = sigma_dev[f][b]), or with
+ * interpolate != 0 the smooth profile: the linear interpolation of the bins'
+ * levels at the pixel centre's radial value between the two nearest bin
+ * centres (end bins' levels beyond the outer centres), in binary32:
+ * m_i = RN(RN(RN(1 - t_i) mean_a) + RN(t_i mean_(a+1))), s_i likewise;
+ * when noise_dev is given (standard normal deviates z, float32
+ * [n_frames][npix], drawn by the caller) the pixel gets RN32(m_i + RN32(s_i *
+ * z_i)) instead (the noisy background some reduction programs need); then
+ * the first min(n_kept[f], kept_capacity)
  * kept pixels of the frame (idx_dev / val_dev [n_frames][kept_capacity], as
  * sep_sparsify writes them; indices outside the detector are skipped) get
  * their recorded values back. Pixels without a bin (masked) get `fill`.
@@ -276,7 +281,7 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
 sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const float* mean_dev,
                        const float* sigma_dev, const int32_t* idx_dev, const float* val_dev,
                        int64_t kept_capacity, const int32_t* n_kept_dev, const float* noise_dev, float fill,
-                       float* out_dev, sep_stream stream);
+                       int32_t interpolate, float* out_dev, sep_stream stream);
 
 /*
  * Veto (Section 4, "Peak count as veto algorithm"): frame f passes when it

@@ -78,6 +78,8 @@ def lib():
                                             C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double,
                                             vp, vp, vp, vp, vp, vp]
         L.oracle_integrate_clip.restype = C.c_int
+        L.oracle_pixel_unit.argtypes = [C.POINTER(Geom), vp]
+        L.oracle_pixel_unit.restype = None
         L.oracle_moments_subset.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_int32, C.c_double, vp]
         L.oracle_moments_subset.restype = None
         L.oracle_sparsify.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int64, vp, vp]
@@ -335,23 +337,57 @@ def veto(n_peaks, min_peaks):
     return [f for f, n in enumerate(n_peaks) if n >= min_peaks]
 
 
-def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan):
+def pixel_unit(det):
+    """Radial value (det's unit) of every pixel centre, the R9 sequence."""
+    out = np.empty(det.rows * det.cols, np.float64)
+    lib().oracle_pixel_unit(C.byref(geom_of(det)), _p(out))
+    return out
+
+
+def interpolation(det, W: Weights):
+    """Lower bin a and weight t (binary32) of the linear interpolation of a
+    per-bin profile at every pixel centre's radial value, between the two
+    bin centres around it (lo + (b + 1/2)(hi - lo)/B); the end bins' levels
+    beyond the outer centres."""
+    lo, hi = W.range
+    B = W.nbins
+    u = (pixel_unit(det) - lo) / (hi - lo) * B - 0.5
+    a = np.floor(u)
+    t = (u - a).astype(np.float32)
+    low, high = ~(u > 0), u >= B - 1
+    a = np.where(low, 0, np.where(high, B - 1, a)).astype(np.int64)
+    t = np.where(low | high, np.float32(0), t)
+    return a, t
+
+
+def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan, interp=None):
     """Decompression of Section 3 ("Densification / Decompression"): the
-    background of every pixel with a radial bin is its bin's mean level, with
-    noise of the bin's deviation when standard normal deviates z are given
-    (binary32, one rounding per operation: mean_b + (sigma_b * z_i)); the
-    pixels that were kept get their recorded values back; pixels without a
-    bin get `fill`. Plain numpy statement (no arithmetic in the C library)."""
+    background of every pixel with a radial bin is its bin's mean level (with
+    ``interp`` = interpolation(det, W): the smooth profile, (1 - t) m_a + t
+    m_(a+1), each product and the sum rounded to binary32), with noise of the
+    bin's (interpolated) deviation when standard normal deviates z are given
+    (binary32, one rounding per operation: m + (s * z_i)); the pixels that were
+    kept get their recorded values back; pixels without a bin get `fill`.
+    Plain numpy statement (no arithmetic in the C library)."""
     bop = np.asarray(W.bin_of_pixel)
     out = np.full(W.npix, fill, np.float32)
     has = bop >= 0
-    mu = np.asarray(mean, np.float32)[bop[has]]
+    mean = np.asarray(mean, np.float32)
+    sigma = None if sigma is None else np.asarray(sigma, np.float32)
+
+    def level(p):
+        if interp is None:
+            return p[bop[has]]
+        a, t = interp[0][has], interp[1][has]
+        upper = np.where(a + 1 < W.nbins, p[np.minimum(a + 1, W.nbins - 1)], np.float32(0))
+        return (np.float32(1) - t) * p[a] + t * upper      # binary32 throughout
+
+    mu = level(mean)
     if noise is None:
         out[has] = mu
     else:
-        sd = np.asarray(sigma, np.float32)[bop[has]]
         z = np.asarray(noise, np.float32).reshape(-1)[has]
-        out[has] = mu + sd * z          # float32 operands: each operation rounds to binary32
+        out[has] = mu + level(sigma) * z   # float32 operands: each operation rounds to binary32
     idx = np.asarray(idx, np.int64)
     ok = (idx >= 0) & (idx < W.npix)
     out[idx[ok]] = np.asarray(val, np.float32)[ok]

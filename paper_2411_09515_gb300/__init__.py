@@ -213,17 +213,20 @@ class Separator:
                        n_kept, idx.shape[1], peaks, capacity, n_peaks, stream)
         return {"peaks": peaks, "n_peaks": n_peaks}
 
-    def densify(self, mean, sigma, idx, val, n_kept, noise=None, fill=float("nan"), out=None, stream=None):
+    def densify(self, mean, sigma, idx, val, n_kept, noise=None, fill=float("nan"), out=None, interpolate=False,
+                stream=None):
         """Dense frames from their sparse form (Section 3): each binned pixel
-        gets its bin's mean (plus sigma * noise with caller-drawn standard
-        normal deviates), kept pixels their recorded values, pixels without
-        a bin `fill`."""
+        gets its bin's mean (or, with ``interpolate``, the profile linearly
+        interpolated at the pixel's radial value), plus sigma * noise with
+        caller-drawn standard normal deviates; kept pixels their recorded
+        values; pixels without a bin `fill`."""
         t = self.torch
         F = mean.shape[0]
         if out is None:
             out = t.empty((F, self.npix), dtype=t.float32, device=mean.device)
         kcap = idx.shape[1] if idx is not None else 0
-        B.sep_densify(self.ctx, self.csr, F, mean, sigma, idx, val, kcap, n_kept, noise, fill, out, stream)
+        B.sep_densify(self.ctx, self.csr, F, mean, sigma, idx, val, kcap, n_kept, noise, fill, out, int(interpolate),
+                      stream)
         return out
 
     def veto(self, n_peaks, min_peaks, stream=None):

@@ -114,7 +114,8 @@ def lib():
                                C.c_int64, _vp, C.c_int64, _vp, _vp]
     L.sep_veto.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
     L.sep_compact_frames.argtypes = [_vp, C.c_int32, _vp, _vp, C.c_int64, _vp, _vp, _vp]
-    L.sep_densify.argtypes = [_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, _vp, _vp]
+    L.sep_densify.argtypes = [_vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_float, C.c_int32,
+                              _vp, _vp]
     L.sep_process_batch.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(sep_params), _vp, _vp, _vp,
                                     _vp, _vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int32, _vp]
     L.sep_model_create.argtypes = [_vp, C.c_uint64, C.POINTER(_vp)]
@@ -340,9 +341,11 @@ def sep_compact_frames(ctx, n_frames, frame_list, n_pass, row_bytes, src, dst, s
                                          _ptr(dst), _stream(stream)))
 
 
-def sep_densify(ctx, csr, n_frames, mean, sigma, idx, val, kept_capacity, n_kept, noise, fill, out, stream=None):
+def sep_densify(ctx, csr, n_frames, mean, sigma, idx, val, kept_capacity, n_kept, noise, fill, out, interpolate=0,
+                stream=None):
     _check(ctx, lib().sep_densify(ctx, csr, n_frames, _ptr(mean), _ptr(sigma), _ptr(idx), _ptr(val), kept_capacity,
-                                  _ptr(n_kept), _ptr(noise), C.c_float(fill), _ptr(out), _stream(stream)))
+                                  _ptr(n_kept), _ptr(noise), C.c_float(fill), int(interpolate), _ptr(out),
+                                  _stream(stream)))
 
 
 def sep_process_batch(ctx, csr, calib, frames, dtype, n_frames, params, mean, sigma, count, idx, val, kept_capacity,

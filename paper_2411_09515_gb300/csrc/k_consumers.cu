@@ -178,17 +178,30 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
 // Densification (Section 3): the background level of every binned pixel
 // (its bin's mean, or RN(mean + RN(sigma z)) with the caller's deviates z),
 // fill where a pixel has no bin; one thread per pixel.
+// Level of pixel i in a per-bin profile p (bin level, or the radial
+// interpolation between the bins a and a + 1 with weight t on the upper).
+__device__ __forceinline__ float profile_at(const float* p, int32_t b, const int32_t* ia, const float* it, int64_t i,
+                                            int32_t nbins) {
+  if (!ia) return __ldg(p + b);
+  const int32_t a = __ldg(ia + i);
+  const float t = __ldg(it + i);
+  const float hi = a + 1 < nbins ? __ldg(p + a + 1) : 0.0f;
+  return __fadd_rn(__fmul_rn(__fsub_rn(1.0f, t), __ldg(p + a)), __fmul_rn(t, hi));
+}
+
 __global__ void __launch_bounds__(256) k_dense_background(const int32_t* bop, int64_t npix, int32_t nbins,
                                                           const float* mean, const float* sigma,
-                                                          const float* noise, float fill, float* out) {
+                                                          const float* noise, float fill, const int32_t* ia,
+                                                          const float* it, float* out) {
   const int64_t f = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npix) return;
   const int32_t b = __ldg(bop + i);
   float x = fill;
   if (b >= 0) {
-    x = __ldg(mean + f * nbins + b);
-    if (noise) x = __fadd_rn(x, __fmul_rn(__ldg(sigma + f * nbins + b), __ldg(noise + f * npix + i)));
+    x = profile_at(mean + f * nbins, b, ia, it, i, nbins);
+    if (noise)
+      x = __fadd_rn(x, __fmul_rn(profile_at(sigma + f * nbins, b, ia, it, i, nbins), __ldg(noise + f * npix + i)));
   }
   out[f * npix + i] = x;
 }
@@ -197,7 +210,8 @@ __global__ void __launch_bounds__(256) k_dense_background(const int32_t* bop, in
 // pixel count is a multiple of 4 and the rows are 16-byte aligned).
 __global__ void __launch_bounds__(256) k_dense_background4(const int32_t* bop, int64_t npix, int32_t nbins,
                                                            const float* mean, const float* sigma,
-                                                           const float* noise, float fill, float* out) {
+                                                           const float* noise, float fill, const int32_t* ia,
+                                                           const float* it, float* out) {
   const int64_t f = blockIdx.y;
   const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= npix) return;
@@ -214,8 +228,8 @@ __global__ void __launch_bounds__(256) k_dense_background4(const int32_t* bop, i
   for (int k = 0; k < 4; ++k) {
     x[k] = fill;
     if (bb[k] >= 0) {
-      x[k] = __ldg(mu + bb[k]);
-      if (noise) x[k] = __fadd_rn(x[k], __fmul_rn(__ldg(sigma + f * nbins + bb[k]), z[k]));
+      x[k] = profile_at(mu, bb[k], ia, it, i + k, nbins);
+      if (noise) x[k] = __fadd_rn(x[k], __fmul_rn(profile_at(sigma + f * nbins, bb[k], ia, it, i + k, nbins), z[k]));
     }
   }
   *reinterpret_cast<float4*>(out + f * npix + i) = make_float4(x[0], x[1], x[2], x[3]);
@@ -483,16 +497,17 @@ cudaError_t launch_compact(const PixArgs& p, int32_t n_frames, const uint32_t* b
 
 cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,
                            const float* sigma, const int32_t* idx, const float* val, int64_t cap,
-                           const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s) {
+                           const int32_t* n_kept, const float* noise, float fill, const int32_t* interp_a,
+                           const float* interp_t, float* out, cudaStream_t s) {
   if (n_frames <= 0 || npix <= 0) return cudaSuccess;
   const bool vec = npix % 4 == 0 && (uintptr_t)out % 16 == 0 && (!noise || (uintptr_t)noise % 16 == 0) &&
                    (uintptr_t)bop % 16 == 0;
   if (vec) {
     dim3 g1((unsigned)((npix / 4 + 255) / 256), (unsigned)n_frames);
-    k_dense_background4<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+    k_dense_background4<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, interp_a, interp_t, out);
   } else {
     dim3 g1((unsigned)((npix + 255) / 256), (unsigned)n_frames);
-    k_dense_background<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, out);
+    k_dense_background<<<g1, 256, 0, s>>>(bop, npix, nbins, mean, sigma, noise, fill, interp_a, interp_t, out);
   }
   if (cap > 0) {
     dim3 g2((unsigned)std::min<int64_t>((cap + 255) / 256, 64), (unsigned)n_frames);

@@ -435,6 +435,8 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
   if ((st = upload(ctx, &c->d_rowptr, c->h.rowptr.data(), c->h.rowptr.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_ent, c->h.ent.data(), c->h.ent.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_cpix, c->h.cpix.data(), c->h.cpix.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_interp_a, c->h.interp_a.data(), c->h.interp_a.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_interp_t, c->h.interp_t.data(), c->h.interp_t.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
@@ -460,6 +462,8 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_rowptr);
   cudaFree(csr->d_ent);
   cudaFree(csr->d_cpix);
+  cudaFree(csr->d_interp_a);
+  cudaFree(csr->d_interp_t);
   cudaFree(csr->d_w);
   cudaFree(csr->d_norm);
   cudaFree(csr->d_bop);
@@ -679,7 +683,7 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
 sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const float* mean_dev,
                        const float* sigma_dev, const int32_t* idx_dev, const float* val_dev,
                        int64_t kept_capacity, const int32_t* n_kept_dev, const float* noise_dev, float fill,
-                       float* out_dev, sep_stream stream) {
+                       int32_t interpolate, float* out_dev, sep_stream stream) {
   if (!ctx) return SEP_ERR_ARG;
   if (!csr) return fail(ctx, SEP_ERR_ARG, "NULL matrix");
   if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "matrix belongs to another context");
@@ -690,8 +694,9 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
     return fail(ctx, SEP_ERR_ARG, "NULL argument");
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaError_t e = sep::launch_densify(csr->d_bop, csr->npix, csr->h.nbins, n_frames, mean_dev, sigma_dev, idx_dev,
-                                      val_dev, kept_capacity, n_kept_dev, noise_dev, fill, out_dev,
-                                      (cudaStream_t)stream);
+                                      val_dev, kept_capacity, n_kept_dev, noise_dev, fill,
+                                      interpolate ? csr->d_interp_a : nullptr,
+                                      interpolate ? csr->d_interp_t : nullptr, out_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify launch");
   return SEP_OK;
 }

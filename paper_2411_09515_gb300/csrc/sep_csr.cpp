@@ -166,6 +166,8 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   std::vector<uint8_t> pn((size_t)npix, 0);
   std::vector<int32_t> bop((size_t)npix, -1);
   std::vector<float> xcen((size_t)npix, 0.0f);   // radial value of the pixel centre (staging order)
+  out->interp_a.assign((size_t)npix, 0);
+  out->interp_t.assign((size_t)npix, 0.0f);
 #pragma omp parallel for schedule(static)
   for (int64_t row = 0; row < rows; ++row) {
     for (int64_t col = 0; col < cols; ++col) {
@@ -176,6 +178,21 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       int32_t bc = xc < lo ? 0 : (xc > hi ? B - 1 : bin_index(xc, lo, hi, B));
       bop[i] = bc;
       xcen[i] = (float)xc;
+      {
+        // smooth profile: between the two bin centres around the pixel centre
+        const double u = (xc - lo) / (hi - lo) * (double)B - 0.5;
+        if (!(u > 0.0)) {
+          out->interp_a[i] = 0;
+          out->interp_t[i] = 0.0f;
+        } else if (u >= (double)(B - 1)) {
+          out->interp_a[i] = B - 1;
+          out->interp_t[i] = 0.0f;
+        } else {
+          const double a = floor(u);
+          out->interp_a[i] = (int32_t)a;
+          out->interp_t[i] = (float)(u - a);
+        }
+      }
       if (exact) {
         int32_t* eb = &pb[(size_t)i * maxe];
         uint8_t* ek = &pk[(size_t)i * maxe];

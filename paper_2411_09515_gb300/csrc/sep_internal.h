@@ -36,6 +36,8 @@ struct HostCsr {
   std::vector<uint32_t> ent;     // [nnz] packed
   std::vector<float> coef;       // [nnz] c_{i,r} (0 for centre-only entries)
   std::vector<int32_t> cpix;     // [nnz] pixel of a centre entry (it carries its pixel's centre bin), else -1
+  std::vector<int32_t> interp_a; // [npix] lower bin of the pixel centre's interpolation (densification)
+  std::vector<float> interp_t;   // [npix] its weight on the upper bin, in [0, 1)
   std::vector<float> w;          // [nnz] c * norm (only with a norm)
   std::vector<int32_t> bop;      // [npix] centre bin, -1 masked
   std::vector<float> centers;    // [nbins]
@@ -141,7 +143,8 @@ cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pic
 // the kept pixels' values.
 cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,
                            const float* sigma, const int32_t* idx, const float* val, int64_t cap,
-                           const int32_t* n_kept, const float* noise, float fill, float* out, cudaStream_t s);
+                           const int32_t* n_kept, const float* noise, float fill, const int32_t* interp_a,
+                           const float* interp_t, float* out, cudaStream_t s);
 // Veto (Section 4): ascending list of the frames with >= min_peaks peaks.
 cudaError_t launch_veto(int32_t n_frames, const int32_t* n_peaks, int32_t min_peaks, int32_t* list, int32_t* n_pass,
                         cudaStream_t s);
@@ -232,6 +235,8 @@ struct sep_csr {
   int32_t* d_rowptr = nullptr;
   uint32_t* d_ent = nullptr;
   int32_t* d_cpix = nullptr;          // pixel of each centre entry, else -1
+  int32_t* d_interp_a = nullptr;      // radial interpolation of the background (densification)
+  float* d_interp_t = nullptr;
   float* d_w = nullptr;
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;

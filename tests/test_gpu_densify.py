@@ -89,8 +89,29 @@ def test_odd_pixel_count_takes_the_scalar_kernel():
     n_kept = np.array([cap, 7], np.int32)
     z = rng.standard_normal((F, det.npix)).astype(np.float32)
     t = [torch.from_numpy(a).cuda() for a in (mean, sigma, idx, val, n_kept, z)]
-    out = sep.densify(t[0], t[1], t[2], t[3], t[4], noise=t[5], fill=0.5).cpu().numpy()
-    for f in range(F):
-        k = int(n_kept[f])
-        want = oracle.densify(W, mean[f], sigma[f], idx[f, :k], val[f, :k], noise=z[f], fill=0.5)
-        assert np.array_equal(out[f].view(np.uint32), want.view(np.uint32)), f
+    interp = oracle.interpolation(det, W)
+    for smooth in (False, True):
+        out = sep.densify(t[0], t[1], t[2], t[3], t[4], noise=t[5], fill=0.5, interpolate=smooth).cpu().numpy()
+        for f in range(F):
+            k = int(n_kept[f])
+            want = oracle.densify(W, mean[f], sigma[f], idx[f, :k], val[f, :k], noise=z[f], fill=0.5,
+                                  interp=interp if smooth else None)
+            assert np.array_equal(out[f].view(np.uint32), want.view(np.uint32)), (f, smooth)
+
+
+def test_interpolated_background_bit_exact(small):
+    det, mask, cal, fr, W = small
+    sep = Separator.from_detector(det, mask=mask, calib=cal)
+    d = torch.from_numpy(fr.view(np.int16)).cuda()
+    o = sep.process_batch(d, det.npix // 4, 2000)
+    z = torch.from_numpy(np.random.default_rng(5).standard_normal((fr.shape[0], det.npix)).astype(np.float32)).cuda()
+    interp = oracle.interpolation(det, W)
+    for noise in (None, z):
+        got = sep.densify(o["mean"], o["sigma"], o["idx"], o["val"], o["n_kept"], noise=noise,
+                          interpolate=True).cpu().numpy()
+        for f in range(fr.shape[0]):
+            n = int(o["n_kept"][f])
+            want = oracle.densify(W, o["mean"][f].cpu().numpy(), o["sigma"][f].cpu().numpy(),
+                                  o["idx"][f, :n].cpu().numpy(), o["val"][f, :n].cpu().numpy(),
+                                  noise=None if noise is None else z[f].cpu().numpy(), interp=interp)
+            assert np.array_equal(got[f].view(np.uint32), want.view(np.uint32)), (f, noise is None)

@@ -69,3 +69,28 @@ def test_kept_share_of_normal_data_is_the_normal_tail():
         p = 0.5 * math.erfc(k / math.sqrt(2))          # the normal tail above k deviations
         assert abs(idx.size - n * p) < 5 * math.sqrt(n * p * (1 - p))
         assert abs(p - printed) / printed < 0.05          # the values the paper prints
+
+
+def test_interpolated_background_reproduces_a_linear_profile():
+    # the smooth background of Section 3: a profile linear in the radial
+    # value is reproduced at every pixel between the outer bin centres
+    det = synth.det_config1()
+    W = oracle.weights(det)
+    lo, hi = W.range
+    B = W.nbins
+    centres = lo + (np.arange(B) + 0.5) * (hi - lo) / B
+    alpha, beta = 3.0, 0.7
+    mean = (alpha + beta * centres).astype(np.float32)
+    interp = oracle.interpolation(det, W)
+    out = oracle.densify(W, mean, None, np.empty(0, np.int32), np.empty(0, np.float32), interp=interp)
+    x = oracle.pixel_unit(det)
+    inner = (x > centres[0]) & (x < centres[-1]) & (W.bin_of_pixel >= 0)
+    assert np.allclose(out[inner], alpha + beta * x[inner], rtol=2e-6, atol=1e-5)
+    # beyond the outer centres: the end bins' levels
+    below = (x <= centres[0]) & (W.bin_of_pixel >= 0)
+    above = (x >= centres[-1]) & (W.bin_of_pixel >= 0)
+    assert below.any() and np.all(out[below] == mean[0])
+    assert above.any() and np.all(out[above] == mean[-1])
+    # the weights: in [0, 1), and the lower bin within one of the centre bin
+    a, t = interp
+    assert np.all((t >= 0) & (t < 1)) and np.all(np.abs(a - W.bin_of_pixel) <= 1)
