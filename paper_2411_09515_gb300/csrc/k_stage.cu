@@ -4,8 +4,9 @@
 //
 // One CTA per staging tile (kTileH x kTileW pixels of the image) and group
 // of frames. Threads read tile rows: each thread four consecutive pixels
-// (one vector load where the row is aligned), two frames per step; the
-// tile's values are placed in shared memory at their rank inside the tile,
+// (one vector load where the row is aligned), two frames per step (four in
+// the ring kernel); the tile's values are placed in shared memory at their
+// rank inside the tile,
 // then written out as one contiguous run. Each value is the same IEEE sequence as pixel_value():
 // RN32(RN32(adc - pedestal) / gain), then RN32(. / norm).
 #include <cuda_runtime.h>
@@ -131,11 +132,12 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
 // into its own slots of a ring in shared memory (cp.async, no registers
 // held), kRing frames ahead, and reads them back when their frame comes.
 // A thread reads only what it copied itself, so the ring needs no barrier.
+// Four frames per step share the two barriers around the write-out.
 template <int DT, bool NORM>
 __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   constexpr int kVec = DT == SEP_DTYPE_U16_JF ? 8 : 16;   // bytes of 4 raw words
-  constexpr int kRing = 6;   // frames ahead (even; 10 measured no faster)
-  __shared__ float tv[2][kTilePix];
+  constexpr int kRing = 8;   // frames ahead (a multiple of the 4 frames of a step)
+  __shared__ float tv[4][kTilePix];
   __shared__ __align__(16) unsigned char ring[kRing][kStageThreads * kVec];
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
@@ -191,13 +193,13 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   };
 #pragma unroll
   for (int j = 0; j < kRing; ++j) issue(j);
-  for (int j = 0; j < nfr; j += 2) {
-    const int nf = min(2, nfr - j);
-    // groups 0 .. j + kRing - 1 issued: frames j and j + 1 have landed
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 2) : "memory");
-    uint32_t w[2][4];
+  for (int j = 0; j < nfr; j += 4) {
+    const int nf = min(4, nfr - j);
+    // groups 0 .. j + kRing - 1 issued: frames j .. j + 3 have landed
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 4) : "memory");
+    uint32_t w[4][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       const unsigned char* sl = &ring[(j + h) % kRing][tid * kVec];
       if (DT == SEP_DTYPE_U16_JF) {
         const uint2 v = *reinterpret_cast<const uint2*>(sl);
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       if (h >= nf) continue;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -244,6 +246,8 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
     // the two slots just read are refilled (this thread's own words, already in registers)
     issue(j + kRing);
     issue(j + kRing + 1);
+    issue(j + kRing + 2);
+    issue(j + kRing + 3);
     __syncthreads();
     for (int h = 0; h < nf; ++h) {
       float* out = a.stage + (int64_t)(f0 + j + h) * a.npos + base;
