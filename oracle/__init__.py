@@ -5,10 +5,12 @@ computes. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import this package. It shares no code with
 ``paper_2411_09515_gb300`` and never imports it.
 
-The arithmetic lives in ``sep_oracle.c`` (compiled to
-``oracle/_build/liboracle.so``); this module only marshals numpy arrays.
-Every function's docstring names the passage of the paper it follows; the
-C source states the definitions in full.
+The arithmetic of correction, coefficients, moments, clipping,
+sparsification and peaks lives in ``sep_oracle.c`` (compiled to
+``oracle/_build/liboracle.so``), for which this module marshals numpy
+arrays; densification, the veto, the exact area fractions and the radial
+interpolation are plain Python / numpy statements here. Every function's
+docstring names the passage of the paper it follows.
 """
 from __future__ import annotations
 
