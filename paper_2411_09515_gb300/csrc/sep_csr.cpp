@@ -214,6 +214,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
                               rect_disc_area(x0, x1, y0, y1, radius_of(g, elo))) / area;
             if (!(c > 1e-12)) continue;
             if (n == kMaxExact) {
+#pragma omp atomic write
               too_many = 1;
               break;
             }
