@@ -101,3 +101,12 @@ def test_library_matrix_matches_the_oracle(unit):
     assert set(got) == set(want)
     for k in want:
         assert got[k] == pytest.approx(want[k], rel=2e-7, abs=1e-12)   # binary32 coefficients
+
+
+def test_library_refuses_bins_far_narrower_than_pixels():
+    det = _det(synth.UNIT_R_MM, nbins=4000)
+    geo = B.make_geometry(det.rows, det.cols, det.pixel_m, det.dist_m, det.center_px, det.wavelength_m, det.unit,
+                          det.nbins, det.split, det.range)
+    with pytest.raises(B.SepError) as e:
+        B.sep_build_csr(None, geo, None)
+    assert e.value.status == B.SEP_ERR_ARG
