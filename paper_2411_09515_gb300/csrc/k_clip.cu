@@ -863,15 +863,22 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
       // kept pixels of this bin: its centre entries (one per pixel whose
       // centre bin this is) whose value exceeds the threshold; the values
       // are still in shared memory, only kept pixels touch global memory
-      // (consecutive threads read consecutive values: no bank conflicts;
+      // (consecutive threads read consecutive groups: no bank conflicts;
       // the entry's pixel is looked up only for values above the threshold)
       uint32_t* bm = a.bitmap + (int64_t)f * a.words;
       int np = 0;
       int32_t g[kMarkAhead];
 #pragma unroll
       for (int k = 0; k < kMarkAhead; ++k) g[k] = -1;
-      for (int e = tid; e < n; e += kThreads) {
-        if (vals[e] > thr) {
+      // (four values per load: rows are padded to multiples of 4 with NaN,
+      // never above a threshold)
+      for (int q = tid; q < nq; q += kThreads) {
+        const float4 v4 = vals4[q];
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (!(xs[j] > thr)) continue;
+          const int e = 4 * q + j;
           if (np < kMarkAhead) {   // kept for later (a shift register: static indexing)
 #pragma unroll
             for (int k = kMarkAhead - 1; k > 0; --k) g[k] = g[k - 1];
