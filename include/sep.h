@@ -166,8 +166,9 @@ sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* statu
 /* ---- integration matrix (Section 2.2) ------------------------------------ */
 /*
  * Build the CSR matrix of coefficients c_{i,r} (the fraction of pixel i in
- * radial bin r, Section 2.2, measured by split x split sub-pixel centres)
- * on the host and upload it to the context's device.
+ * radial bin r, Section 2.2, measured by split x split sub-pixel centres, or
+ * with split 0 the exact area fraction) on the host and upload it to the
+ * context's device.
  *  mask_host: rows*cols bytes, nonzero = masked pixel (never used); may be NULL.
  *  norm_host: rows*cols floats, the normalisation of Eq. 1 (denominator);
  *             may be NULL (= 1 everywhere). Must be > 0 on valid pixels.
