@@ -149,7 +149,8 @@ class Weights:
 
 
 def _radius_of(det, x):
-    """Detector-plane radius (m) of the radial value x in det's unit (R9 inverted)."""
+    """Detector-plane radius (m) of the radial value x in det's unit (the
+    inverse of the radius -> 2theta / q / r mapping of the flat detector)."""
     x = float(x)
     if det.unit == 2:                                   # r in mm
         R = x * 1e-3
@@ -216,7 +217,7 @@ def weights_exact(det, mask=None) -> Weights:
     detector plane, and c is the pixel's area between them over the pixel's
     area. The range is det.range, or (NaN) the span of the valid pixels'
     nearest and farthest points. The threshold bin of a pixel is the bin of
-    its centre (R10). Plain Python, for small detectors."""
+    its centre (clamped into the range). Plain Python, for small detectors."""
     rows, cols = det.rows, det.cols
     py, px = det.pixel_m
     cx, cy = det.center_px
@@ -254,7 +255,7 @@ def weights_exact(det, mask=None) -> Weights:
                     pix.append(i)
                     bins.append(b)
                     cs.append(min(f, 1.0))
-    # threshold bins: the pixel centres' bins on the same range (the C oracle's R9 sequence)
+    # threshold bins: the pixel centres' bins on the same range (the C oracle's radial values)
     import copy
     d1 = copy.copy(det)
     d1.split, d1.range = 1, (lo, hi)
@@ -340,7 +341,8 @@ def veto(n_peaks, min_peaks):
 
 
 def pixel_unit(det):
-    """Radial value (det's unit) of every pixel centre, the R9 sequence."""
+    """Radial value (det's unit) of every pixel centre, by the C oracle's
+    binary64 sequence (radius, then 2theta / q / r)."""
     out = np.empty(det.rows * det.cols, np.float64)
     lib().oracle_pixel_unit(C.byref(geom_of(det)), _p(out))
     return out

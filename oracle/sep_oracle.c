@@ -120,7 +120,8 @@ void oracle_unit_range(const oracle_geom* g, const uint8_t* mask, double* lo, do
   *hi = mx;
 }
 
-/* Radial value of every pixel centre (R9 sequence), masked ones included. */
+/* Radial value of every pixel centre (unit_value at offset 0.5, 0.5), masked
+ * ones included. */
 void oracle_pixel_unit(const oracle_geom* g, double* out) {
   for (int64_t row = 0; row < g->rows; ++row)
     for (int64_t col = 0; col < g->cols; ++col) out[row * g->cols + col] = unit_value(g, row, col, 0.5, 0.5);
