@@ -9,7 +9,9 @@ The arithmetic of correction, coefficients, moments, clipping,
 sparsification and peaks lives in ``sep_oracle.c`` (compiled to
 ``oracle/_build/liboracle.so``), for which this module marshals numpy
 arrays; densification, the veto, the exact area fractions and the radial
-interpolation are plain Python / numpy statements here. Every function's
+interpolation (of the densified background and of the sparsification
+threshold, fed to the C routines as one "bin" per pixel) are plain Python /
+numpy statements here. Every function's
 docstring names the passage of the paper it follows.
 """
 from __future__ import annotations
@@ -319,18 +321,40 @@ def moments_subset(pix, c, sel, signal, norm=None, model=ERROR_AZIMUTHAL, dark=0
     return o[0], o[1], int(o[2])
 
 
-def sparsify(W: Weights, signal, mean, sigma, k_pick=3.0, norm=None):
-    """Pixels above mu + k_pick sigma of their radial bin (Section 3), ascending."""
+def per_pixel_background(W: Weights, mean, sigma, interp):
+    """The background of every pixel as its own "bin": (bins, mean, sigma)
+    with bins[i] = i for a pixel with a radial bin (-1 otherwise) and
+    mean / sigma the per-bin profile interpolated in binary64 at the pixel
+    centre's radial value (``interp`` = interpolation(det, W, exact=True)).
+    Fed to the per-bin sparsification and peak routines it makes their
+    threshold mu(x_i) + k_pick sigma(x_i) and their background mu(x_j)."""
+    bop = np.asarray(W.bin_of_pixel)
+    has = bop >= 0
+    bins = np.where(has, np.arange(W.npix), -1).astype(np.int32)
+    mu = np.zeros(W.npix)
+    sd = np.zeros(W.npix)
+    mu[has] = profile_at(interp, mean, W.nbins)[has]
+    sd[has] = profile_at(interp, sigma, W.nbins)[has]
+    return bins, mu, sd
+
+
+def sparsify(W: Weights, signal, mean, sigma, k_pick=3.0, norm=None, interp=None):
+    """Pixels above mu + k_pick sigma of their radial bin (Section 3),
+    ascending; with ``interp`` (interpolation(det, W, exact=True)) the
+    background at the pixel centre's radial value instead: the smooth
+    profile of Section 3, interpolated between bin centres."""
     sig = _c(signal, np.float32).reshape(-1)
+    bop = W.bin_of_pixel
+    if interp is not None:
+        bop, mean, sigma = per_pixel_background(W, mean, sigma, interp)
+    bop = _c(bop, np.int32)
     mean = _c(mean, np.float64)
     sigma = _c(sigma, np.float64)
     nrm = _c(norm, np.float32)
-    n = lib().oracle_sparsify(W.npix, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick,
-                              0, None, None)
+    n = lib().oracle_sparsify(W.npix, _p(bop), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, 0, None, None)
     idx = np.empty(n, np.int32)
     val = np.empty(n, np.float64)
-    lib().oracle_sparsify(W.npix, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, n,
-                          _p(idx), _p(val))
+    lib().oracle_sparsify(W.npix, _p(bop), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, n, _p(idx), _p(val))
     return idx, val
 
 
@@ -348,20 +372,31 @@ def pixel_unit(det):
     return out
 
 
-def interpolation(det, W: Weights):
-    """Lower bin a and weight t (binary32) of the linear interpolation of a
-    per-bin profile at every pixel centre's radial value, between the two
-    bin centres around it (lo + (b + 1/2)(hi - lo)/B); the end bins' levels
-    beyond the outer centres."""
+def interpolation(det, W: Weights, exact=False):
+    """Lower bin a and weight t (binary32; binary64 with ``exact``) of the
+    linear interpolation of a per-bin profile at every pixel centre's radial
+    value, between the two bin centres around it (lo + (b + 1/2)(hi - lo)/B);
+    the end bins' levels beyond the outer centres."""
     lo, hi = W.range
     B = W.nbins
     u = (pixel_unit(det) - lo) / (hi - lo) * B - 0.5
     a = np.floor(u)
-    t = (u - a).astype(np.float32)
+    t = u - a if exact else (u - a).astype(np.float32)
     low, high = ~(u > 0), u >= B - 1
     a = np.where(low, 0, np.where(high, B - 1, a)).astype(np.int64)
-    t = np.where(low | high, np.float32(0), t)
+    t = np.where(low | high, t.dtype.type(0), t)
     return a, t
+
+
+def profile_at(interp, profile, nbins):
+    """A per-bin profile at every pixel centre, in binary64:
+    (1 - t) p_a + t p_(a+1) (the upper term is 0 where a is the last bin,
+    where t is 0 too)."""
+    a, t = interp
+    p = np.asarray(profile, np.float64)
+    t = np.asarray(t, np.float64)
+    upper = np.where(a + 1 < nbins, p[np.minimum(a + 1, nbins - 1)], 0.0)
+    return (1.0 - t) * p[a] + t * upper
 
 
 def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan, interp=None):
@@ -398,14 +433,19 @@ def densify(W: Weights, mean, sigma, idx, val, noise=None, fill=np.nan, interp=N
     return out
 
 
-def peaks(det, W: Weights, signal, mean, sigma, k_pick=3.0, patch=3, min_count=3, norm=None):
-    """Peak picking of Section 4 over the kept pixels; structured array."""
+def peaks(det, W: Weights, signal, mean, sigma, k_pick=3.0, patch=3, min_count=3, norm=None, interp=None):
+    """Peak picking of Section 4 over the kept pixels; structured array.
+    With ``interp`` the kept test and the background of the records use the
+    profile interpolated at each pixel centre (as ``sparsify``)."""
     sig = _c(signal, np.float32).reshape(-1)
+    bop = W.bin_of_pixel
+    if interp is not None:
+        bop, mean, sigma = per_pixel_background(W, mean, sigma, interp)
+    bop = _c(bop, np.int32)
     mean = _c(mean, np.float64)
     sigma = _c(sigma, np.float64)
     nrm = _c(norm, np.float32)
-    args = (det.rows, det.cols, _p(W.bin_of_pixel), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, patch,
-            min_count)
+    args = (det.rows, det.cols, _p(bop), _p(sig), _p(nrm), _p(mean), _p(sigma), k_pick, patch, min_count)
     n = lib().oracle_peaks(*args, 0, None)
     out = np.zeros(n, PEAK_DTYPE)
     lib().oracle_peaks(*args, n, _p(out))
