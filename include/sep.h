@@ -134,6 +134,18 @@ typedef struct {
                                 final set. Poisson and hybrid: frames without a
                                 norm, surrogate == 0 */
   float dark_var;            /* dark-noise variance sigma_dark^2 of Eq. 3, >= 0 */
+  int32_t interpolate;       /* background of the two consumers (Sections 3, 4):
+                                0: the pixel centre's bin, a pixel is kept iff
+                                v > mu_b + k_pick sigma_b and peak records
+                                subtract mu_b; 1: the smooth profile at the
+                                pixel centre's radial value x (mean and
+                                deviation interpolated linearly between the two
+                                bin centres around x, the end bins' levels
+                                beyond the outer centres, binary32), kept iff
+                                v > mu(x) + k_pick sigma(x), and peak records
+                                subtract mu(x) and propagate sigma(x). With 1
+                                the batch calls mark kept pixels in a pass
+                                after clipping instead of inside it */
 } sep_params;
 
 #define SEP_CUTOFF_FIXED     0

@@ -55,7 +55,8 @@ class sep_geometry(C.Structure):
 class sep_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("k_clip", C.c_float), ("k_pick", C.c_float), ("patch", C.c_int32),
                 ("min_count", C.c_int32), ("precision", C.c_int32), ("surrogate", C.c_int32),
-                ("cutoff", C.c_int32), ("error_model", C.c_int32), ("dark_var", C.c_float)]
+                ("cutoff", C.c_int32), ("error_model", C.c_int32), ("dark_var", C.c_float),
+                ("interpolate", C.c_int32)]
 
 
 class sep_train_cfg(C.Structure):
@@ -207,11 +208,12 @@ def make_geometry(rows, cols, pixel_m, dist_m, center_px, wavelength_m, unit, nb
 
 
 def make_params(n_iter=5, k_clip=3.0, k_pick=3.0, patch=3, min_count=3, precision=SEP_PREC_DWORD, surrogate=0,
-                cutoff=SEP_CUTOFF_FIXED):
+                cutoff=SEP_CUTOFF_FIXED, interpolate=0):
     p = sep_params()
     p.n_iter, p.k_clip, p.k_pick, p.patch, p.min_count, p.precision = n_iter, k_clip, k_pick, patch, min_count, precision
     p.surrogate = surrogate
     p.cutoff = cutoff
+    p.interpolate = interpolate
     return p
 
 

@@ -235,6 +235,31 @@ __global__ void __launch_bounds__(256) k_dense_background4(const int32_t* bop, i
   *reinterpret_cast<float4*>(out + f * npix + i) = make_float4(x[0], x[1], x[2], x[3]);
 }
 
+// Kept pixels against the smooth background (Section 3): the threshold of
+// pixel i is RD(mu(x_i) + k_pick sigma(x_i)) with the frame's profile
+// interpolated at the pixel centre. One thread per pixel, one warp per
+// bitmap word: every word is written.
+template <int DT, bool NORM>
+__global__ void __launch_bounds__(256) k_mark_interp(PixArgs p, int32_t nbins, const float* mean, const float* sigma,
+                                                     float k_pick, uint32_t* bitmap, int64_t words) {
+  const int64_t f = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = false;
+  if (i < p.npix) {
+    const int32_t b = __ldg(p.bop + i);
+    if (b >= 0) {
+      const int64_t row = p.orow ? p.orow[f] : f * (int64_t)nbins;
+      const float m = profile_at(mean + row, b, p.ia, p.it, i, nbins);
+      const float sd = profile_at(sigma + row, b, p.ia, p.it, i, nbins);
+      const void* frame = p.fptr ? (const void*)p.fptr[f] : frame_ptr<DT>(p.frames, f, p.npix);
+      const float v = value_of<DT, NORM>(p, frame, f, i);
+      keep = v > __double2float_rd((double)m + (double)k_pick * (double)sd);
+    }
+  }
+  const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+  if ((threadIdx.x & 31) == 0 && (i >> 5) < words) bitmap[f * words + (i >> 5)] = mk;
+}
+
 // ... then the recorded values of the kept pixels.
 __global__ void __launch_bounds__(256) k_dense_scatter(const int32_t* idx, const float* val, int64_t cap,
                                                        const int32_t* n_kept, int64_t npix, float* out) {
@@ -358,7 +383,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_flags(PixArgs p, const ui
 // Phase 2 (one CTA per frame): prefix over chunk counts, then every flagged
 // entry writes its record at its rank: ascending pixel order, since the
 // kept list ascends.
-template <int DT, bool NORM>
+template <int DT, bool NORM, bool INTERP>
 __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, const float* mean, const float* sigma,
                                                     const uint32_t* bitmap, int64_t words, const int32_t* idx,
                                                     const int32_t* n_kept, int64_t kcap, int32_t patch,
@@ -417,8 +442,9 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
               if (!is_kept(bm, j)) continue;
               const int32_t bj = __ldg(p.bop + j);
               const float vj = value_of<DT, NORM>(p, frame, f, j);
-              const float w = vj - __ldg(mu + bj);
-              const float s = __ldg(sd + bj);
+              // background of the pixel's bin, or the profile at its centre
+              const float w = vj - (INTERP ? profile_at(mu, bj, p.ia, p.it, j, nbins) : __ldg(mu + bj));
+              const float s = INTERP ? profile_at(sd, bj, p.ia, p.it, j, nbins) : __ldg(sd + bj);
               ++nk;
               I += w;
               sy += w * ((float)r + 0.5f);
@@ -469,6 +495,23 @@ cudaError_t launch_mark(const PixArgs& p, int32_t n_frames, int32_t nbins, const
     if (nrm) k_mark<SEP_DTYPE_F32, true><<<grid, 256, 0, s>>>(p, nbins, thr, bitmap, words);
     else k_mark<SEP_DTYPE_F32, false><<<grid, 256, 0, s>>>(p, nbins, thr, bitmap, words);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_interp(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* mean,
+                               const float* sigma, float k_pick, uint32_t* bitmap, int64_t words, cudaStream_t s) {
+  if (n_frames <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((words * 32 + 255) / 256), (unsigned)n_frames);
+  const bool nrm = p.norm != nullptr;
+#define SEP_MARK_ARGS p, nbins, mean, sigma, k_pick, bitmap, words
+  if (p.dtype == SEP_DTYPE_U16_JF) {
+    if (nrm) k_mark_interp<SEP_DTYPE_U16_JF, true><<<grid, 256, 0, s>>>(SEP_MARK_ARGS);
+    else k_mark_interp<SEP_DTYPE_U16_JF, false><<<grid, 256, 0, s>>>(SEP_MARK_ARGS);
+  } else {
+    if (nrm) k_mark_interp<SEP_DTYPE_F32, true><<<grid, 256, 0, s>>>(SEP_MARK_ARGS);
+    else k_mark_interp<SEP_DTYPE_F32, false><<<grid, 256, 0, s>>>(SEP_MARK_ARGS);
+  }
+#undef SEP_MARK_ARGS
   return cudaGetLastError();
 }
 
@@ -556,25 +599,30 @@ cudaError_t launch_peaks(const PixArgs& p, int32_t n_frames, int32_t nbins, cons
   int32_t* cnt = scratch + (int64_t)n_frames * nch * 8;
   dim3 g1((unsigned)std::min<int32_t>(std::max<int32_t>(nch, 1), kPeakCtasPerFrame), (unsigned)n_frames);
   const bool nrm = p.norm != nullptr;
+  const bool itp = p.ia != nullptr && p.it != nullptr;
 #define SEP_FLAG_ARGS p, bitmap, words, idx, n_kept, kcap, patch, min_count, flags, cnt, nch
 #define SEP_PEMIT_ARGS p, nbins, mean, sigma, bitmap, words, idx, n_kept, kcap, patch, flags, cnt, nch, peaks, pcap, n_peaks, status
+#define SEP_PEMIT(DT, NR)                                                              \
+  if (itp) k_peak_emit<DT, NR, true><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);      \
+  else k_peak_emit<DT, NR, false><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS)
   if (p.dtype == SEP_DTYPE_U16_JF) {
     if (nrm) {
       k_peak_flags<SEP_DTYPE_U16_JF, true><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
-      k_peak_emit<SEP_DTYPE_U16_JF, true><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+      SEP_PEMIT(SEP_DTYPE_U16_JF, true);
     } else {
       k_peak_flags<SEP_DTYPE_U16_JF, false><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
-      k_peak_emit<SEP_DTYPE_U16_JF, false><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+      SEP_PEMIT(SEP_DTYPE_U16_JF, false);
     }
   } else {
     if (nrm) {
       k_peak_flags<SEP_DTYPE_F32, true><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
-      k_peak_emit<SEP_DTYPE_F32, true><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+      SEP_PEMIT(SEP_DTYPE_F32, true);
     } else {
       k_peak_flags<SEP_DTYPE_F32, false><<<g1, kPeakThreads, 0, s>>>(SEP_FLAG_ARGS);
-      k_peak_emit<SEP_DTYPE_F32, false><<<n_frames, 1024, 0, s>>>(SEP_PEMIT_ARGS);
+      SEP_PEMIT(SEP_DTYPE_F32, false);
     }
   }
+#undef SEP_PEMIT
 #undef SEP_FLAG_ARGS
 #undef SEP_PEMIT_ARGS
   return cudaGetLastError();

@@ -117,6 +117,7 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
   if (!(p->dark_var >= 0.0f) || !isfinite(p->dark_var)) return fail(ctx, SEP_ERR_ARG, "dark_var must be finite and >= 0");
   if (p->error_model != SEP_ERROR_AZIMUTHAL && p->surrogate > 0)
     return fail(ctx, SEP_ERR_ARG, "the surrogate predicts azimuthal-model clipping only");
+  if (p->interpolate != 0 && p->interpolate != 1) return fail(ctx, SEP_ERR_ARG, "interpolate must be 0 or 1");
   return SEP_OK;
 }
 
@@ -156,6 +157,14 @@ sep::PixArgs pix_args(const sep_csr* csr, const sep_calib* calib, const void* fr
   p.norm = csr->d_norm;
   p.bop = csr->d_bop;
   return p;
+}
+
+// The consumers' background at the pixel centre (params->interpolate).
+void set_interp(sep::PixArgs& p, const sep_csr* csr, const sep_params* params) {
+  if (params->interpolate) {
+    p.ia = csr->d_interp_a;
+    p.it = csr->d_interp_t;
+  }
 }
 
 sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
@@ -642,9 +651,15 @@ sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
     return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
-  cudaError_t e = sep::launch_thresholds(mean_dev, sigma_dev, params->k_pick, (int64_t)n_frames * csr->h.nbins,
-                                         ctx->d_thr, s);
-  if (e == cudaSuccess) e = sep::launch_mark(p, n_frames, csr->h.nbins, ctx->d_thr, ctx->d_bitmap, words, s);
+  cudaError_t e = cudaSuccess;
+  if (params->interpolate) {
+    set_interp(p, csr, params);
+    e = sep::launch_mark_interp(p, n_frames, csr->h.nbins, mean_dev, sigma_dev, params->k_pick, ctx->d_bitmap, words,
+                                s);
+  } else {
+    e = sep::launch_thresholds(mean_dev, sigma_dev, params->k_pick, (int64_t)n_frames * csr->h.nbins, ctx->d_thr, s);
+    if (e == cudaSuccess) e = sep::launch_mark(p, n_frames, csr->h.nbins, ctx->d_thr, ctx->d_bitmap, words, s);
+  }
   if (e == cudaSuccess)
     e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, capacity, n_kept_dev, ctx->d_aux,
                             ctx->d_status, s);
@@ -670,6 +685,7 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
     return st;
   cudaStream_t s = (cudaStream_t)stream;
   sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
+  set_interp(p, csr, params);
   cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
   if (e == cudaSuccess)
     e = sep::launch_scatter_list(n_frames, idx_dev, n_kept_dev, kept_capacity, csr->npix, ctx->d_bitmap, words, s);
@@ -751,19 +767,24 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
   cudaStream_t s = (cudaStream_t)stream;
 
   auto enqueue = [&](int mode) -> cudaError_t {
-    // the clip kernel marks the kept pixels as each bin's threshold is known
+    // the clip kernel marks the kept pixels as each bin's threshold is known;
+    // thresholds interpolated between bins wait for every bin of the frame
     sep::ClipArgs a = clip_args(ctx, csr, ctx->d_stage, n_frames, params, mean_dev, sigma_dev, count_dev, nullptr,
                                 nullptr, nullptr);
-    a.bitmap = ctx->d_bitmap;
+    a.bitmap = params->interpolate ? nullptr : ctx->d_bitmap;
     a.words = words;
     sep::PixArgs p = pix_args(csr, calib, frames_dev, dtype);
     p.stage = ctx->d_stage;
     p.pos_of = csr->d_pos_of;
     p.npos = stage_stride(csr);
+    set_interp(p, csr, params);
     cudaError_t e = cudaMemsetAsync(ctx->d_bitmap, 0, (size_t)(words * n_frames) * 4, s);
     if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, frames_dev, nullptr, dtype, n_frames, ctx->d_stage, s);
     if (e == cudaSuccess)
       e = enqueue_clip(ctx, csr, a, params->precision, mode, s);
+    if (e == cudaSuccess && params->interpolate)
+      e = sep::launch_mark_interp(p, n_frames, csr->h.nbins, mean_dev, sigma_dev, params->k_pick, ctx->d_bitmap,
+                                  words, s);
     if (e == cudaSuccess)
       e = sep::launch_compact(p, n_frames, ctx->d_bitmap, words, idx_dev, val_dev, kept_capacity, n_kept_dev,
                               ctx->d_aux, ctx->d_status, s);
@@ -1181,7 +1202,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       sep::ClipArgs ca = clip_args(ctx, csr, stage, m, params, mean_dev, sigma_dev, count_dev, nullptr, nullptr,
                                    nullptr);
       ca.orow = orow;
-      ca.bitmap = bm;   // kept pixels are marked by the clip kernel
+      ca.bitmap = params->interpolate ? nullptr : bm;   // kept pixels are marked by the clip kernel
       ca.words = words[d];
       if (mode == 1) {
         e = enqueue_clip(ctx, csr, ca, params->precision, 1, sd, false);
@@ -1194,9 +1215,12 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
       pa.stage = stage;
       pa.pos_of = csr->d_pos_of;
       pa.npos = stage_stride(csr);
+      set_interp(pa, csr, params);
       if (e == cudaSuccess) e = cudaMemsetAsync(bm, 0, (size_t)(words[d] * m) * 4, sd);
       if (e == cudaSuccess) e = enqueue_stage(ctx, csr, calib, nullptr, fptr, dtype, m, stage, sd);
       if (e == cudaSuccess) e = enqueue_clip(ctx, csr, ca, params->precision, mode, sd, false);
+      if (e == cudaSuccess && params->interpolate)
+        e = sep::launch_mark_interp(pa, m, csr->h.nbins, mean_dev, sigma_dev, params->k_pick, bm, words[d], sd);
       if (e == cudaSuccess)
         e = sep::launch_compact(pa, m, bm, words[d], idx_dev, val_dev, kept_capacity, n_kept_dev, aux, ctx->d_status,
                                 sd);

@@ -129,6 +129,10 @@ struct PixArgs {           // what the consumers need to recompute a pixel value
   const float* stage = nullptr;
   const int32_t* pos_of = nullptr;   // [npix] staging position, -1 if not staged
   int64_t npos = 0;
+  // background at the pixel centre interpolated between bin centres (lower
+  // bin, weight on the upper bin, per pixel); null: the centre bin's level
+  const int32_t* ia = nullptr;
+  const float* it = nullptr;
 };
 
 // mode 0: set the kernel's shared-memory attribute and launch; 1: attribute
@@ -139,6 +143,11 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
 size_t clip_smem_bytes(int32_t cap, bool weighted);
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
+// Kept-pixel bitmap with each pixel's threshold taken from the profile
+// interpolated at its centre (p.ia, p.it); every word of the n_frames rows
+// is written. Profile rows: p.orow[f] when set, else f * nbins.
+cudaError_t launch_mark_interp(const PixArgs& p, int32_t n_frames, int32_t nbins, const float* mean,
+                               const float* sigma, float k_pick, uint32_t* bitmap, int64_t words, cudaStream_t s);
 // Dense frames from their sparse form (Section 3): background by bin, then
 // the kept pixels' values.
 cudaError_t launch_densify(const int32_t* bop, int64_t npix, int32_t nbins, int32_t n_frames, const float* mean,

@@ -58,7 +58,9 @@ extern "C" sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, con
   } else if (dtype != SEP_DTYPE_F32) {
     return fail(SEP_ERR_ARG, "unknown dtype");
   }
-  if (!params || !(params->k_pick >= 0.0f) || !isfinite(params->k_pick)) return fail(SEP_ERR_ARG, "bad params");
+  if (!params || !(params->k_pick >= 0.0f) || !isfinite(params->k_pick) ||
+      (params->interpolate != 0 && params->interpolate != 1))
+    return fail(SEP_ERR_ARG, "bad params");
   if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(SEP_ERR_ARG, "device index too large");
   if (n_frames == 0) return SEP_OK;
 
@@ -106,8 +108,14 @@ extern "C" sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, con
   cudaStream_t s = (cudaStream_t)stream;
   // the mark kernel writes every bitmap word and the count kernel every tile
   // count, so no scratch word is read before this call writes it
-  e = sep::launch_thresholds(mean_dev, sigma_dev, params->k_pick, (int64_t)n_frames * csr->h.nbins, thr, s);
-  if (e == cudaSuccess) e = sep::launch_mark(p, n_frames, csr->h.nbins, thr, bitmap, words, s);
+  if (params->interpolate) {
+    p.ia = csr->d_interp_a;
+    p.it = csr->d_interp_t;
+    e = sep::launch_mark_interp(p, n_frames, csr->h.nbins, mean_dev, sigma_dev, params->k_pick, bitmap, words, s);
+  } else {
+    e = sep::launch_thresholds(mean_dev, sigma_dev, params->k_pick, (int64_t)n_frames * csr->h.nbins, thr, s);
+    if (e == cudaSuccess) e = sep::launch_mark(p, n_frames, csr->h.nbins, thr, bitmap, words, s);
+  }
   if (e == cudaSuccess)
     e = sep::launch_compact(p, n_frames, bitmap, words, idx_dev, val_dev, capacity, n_kept_dev, aux, ctx->d_status, s);
   if (e != cudaSuccess) return fail(SEP_ERR_CUDA, std::string("sparsify (static scratch): ") + cudaGetErrorString(e));

@@ -9,6 +9,10 @@ A local maximum between two pixels whose values are equal up to one FP32
 rounding of signal / norm may be either pixel (the library compares the FP32
 values, the oracle the FP64 quotients).
 
+With thresholds interpolated between bin centres (``interp``, the oracle's
+binary64 interpolation table) every pixel has its own threshold; the same
+band applies to it.
+
 A clip decision taken within a relative 1e-5 of a boundary ("banded" bin in
 the oracle's log) may legitimately go either way in FP32 on the GPU and then
 change the rest of that bin's trajectory. For such bins the GPU's own final
@@ -43,8 +47,10 @@ def close(a, b, rtol=RTOL, sd=None):
 class Frame:
     """Oracle view of one frame: values, clip results, thresholds."""
 
-    def __init__(self, W, signal, n_iter, k_clip, k_pick, norm=None, chauvenet=False, model=0, dark=0.0):
+    def __init__(self, W, signal, n_iter, k_clip, k_pick, norm=None, chauvenet=False, model=0, dark=0.0,
+                 interp=None):
         self.W = W
+        self.interp = interp
         self.model, self.dark = model, dark
         self.sig = np.ascontiguousarray(signal, np.float32).reshape(-1)
         self.norm = norm
@@ -85,11 +91,20 @@ def check_clip(fr: Frame, mean, sigma, count, bounds):
 
 
 def thresholds(fr: Frame, moved):
-    thr = fr.ref["mean"] + fr.k_pick * fr.ref["sigma"]
-    thr_alt = thr.copy()
+    """Per-pixel thresholds from the oracle's profile, and from the profile
+    with the bins of another trajectory replaced by the GPU's own sets."""
+    mean, sigma = fr.ref["mean"], fr.ref["sigma"]
+    mean_alt, sigma_alt = mean.copy(), sigma.copy()
     for b, mu, sd in moved:
-        thr_alt[b] = mu + fr.k_pick * sd
-    return thr, thr_alt
+        mean_alt[b], sigma_alt[b] = mu, sd
+    bop = fr.W.bin_of_pixel
+    b = np.where(bop >= 0, bop, 0)
+    if fr.interp is None:
+        return (mean + fr.k_pick * sigma)[b], (mean_alt + fr.k_pick * sigma_alt)[b]
+    nb = fr.W.nbins
+    at = oracle.profile_at
+    return (at(fr.interp, mean, nb) + fr.k_pick * at(fr.interp, sigma, nb),
+            at(fr.interp, mean_alt, nb) + fr.k_pick * at(fr.interp, sigma_alt, nb))
 
 
 def check_kept(fr: Frame, idx, val, n_kept, moved, capacity=None):
@@ -97,10 +112,9 @@ def check_kept(fr: Frame, idx, val, n_kept, moved, capacity=None):
     bop = fr.W.bin_of_pixel
     thr, thr_alt = thresholds(fr, moved)
     valid = bop >= 0
-    b = np.where(valid, bop, 0)
     v = fr.v
-    want = np.flatnonzero(valid & (v > thr[b]))
-    want_alt = np.flatnonzero(valid & (v > thr_alt[b]))
+    want = np.flatnonzero(valid & (v > thr))
+    want_alt = np.flatnonzero(valid & (v > thr_alt))
     n = int(n_kept)
     got = np.asarray(idx[: min(n, capacity if capacity is not None else n)])
     assert np.all(np.diff(got) > 0), "kept pixels not ascending"
@@ -108,11 +122,11 @@ def check_kept(fr: Frame, idx, val, n_kept, moved, capacity=None):
     want_val = fr.sig[got] if fr.norm is None else fr.sig[got] / fr.norm[got].astype(np.float32)
     assert np.array_equal(np.asarray(val[: got.size], np.float32), want_val.astype(np.float32))
     diff = np.setxor1d(got, want)
-    near = np.abs(v[diff] - thr[b[diff]]) <= BAND * np.abs(thr[b[diff]])
+    near = np.abs(v[diff] - thr[diff]) <= BAND * np.abs(thr[diff])
     alt = np.isin(diff, want_alt) == np.isin(diff, got)
     excused = near | alt
     assert np.all(excused), (f"{(~excused).sum()} kept pixels differ beyond the band, e.g. pixel "
-                             f"{diff[~excused][0]} v={v[diff[~excused][0]]} thr={thr[b[diff[~excused][0]]]}")
+                             f"{diff[~excused][0]} v={v[diff[~excused][0]]} thr={thr[diff[~excused][0]]}")
     if capacity is None or n <= capacity:
         assert abs(n - want.size) <= diff.size
     return set(diff.tolist())
@@ -123,7 +137,7 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3, truncated=
     (truncated: the list filled its capacity, so it is compared up to its
     last pixel)."""
     ref = oracle.peaks(det, fr.W, fr.sig, fr.ref["mean"], fr.ref["sigma"], k_pick=fr.k_pick, patch=patch,
-                       min_count=min_count, norm=fr.norm)
+                       min_count=min_count, norm=fr.norm, interp=fr.interp)
     if truncated and len(peaks):
         ref = ref[ref["idx"] <= peaks["idx"][-1]]
     cols = det.cols
@@ -166,11 +180,12 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3, truncated=
 
 
 def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None,
-                chauvenet=False, model=0, dark=0.0):
+                chauvenet=False, model=0, dark=0.0, interp=None):
     """Frame f of a batch's outputs `o` (numpy arrays as returned by the
     library) against the oracle on the frame's signal. Returns (banded bins,
     bins on another trajectory, excused pixels)."""
-    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm, chauvenet=chauvenet, model=model, dark=dark)
+    fr = Frame(W, sig, n_iter, k_clip, k_pick, norm=norm, chauvenet=chauvenet, model=model, dark=dark,
+               interp=interp)
     if bounds is None:
         bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
     nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)

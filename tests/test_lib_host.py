@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     import ctypes as C
     assert C.sizeof(B.sep_geometry) == 4 * 2 + 8 * 2 + 8 + 8 * 2 + 8 + 4 * 3 + 4 + 8 * 2  # padded before range
-    assert C.sizeof(B.sep_params) == 40
+    assert C.sizeof(B.sep_params) == 44
     assert B.PEAK_DTYPE.itemsize == B.PEAK_BYTES == 24
 
 
