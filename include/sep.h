@@ -103,6 +103,11 @@ typedef struct {
 
 #define SEP_MAX_PIXELS (1 << 25)
 #define SEP_MAX_BINS   32767
+/* Frames per call of every call that takes device-resident frames or
+ * per-frame device rows (their launches have one grid row per frame); a
+ * larger n_frames returns SEP_ERR_ARG before any launch. sep_process_host
+ * takes any count (its chunks must respect the limit), sep_veto up to 2^24. */
+#define SEP_MAX_FRAMES 65535
 
 /* Parameters of clipping and of the two consumers (Sections 2.4, 3, 4). */
 typedef struct {

@@ -23,6 +23,7 @@ SEP_DTYPE_F32, SEP_DTYPE_U16_JF = 0, 1
 SEP_PREC_PLAIN, SEP_PREC_KAHAN, SEP_PREC_FP64MERGE, SEP_PREC_DWORD = 0, 1, 2, 3
 SEP_CUTOFF_FIXED, SEP_CUTOFF_CHAUVENET = 0, 1
 SEP_ERROR_AZIMUTHAL, SEP_ERROR_POISSON, SEP_ERROR_HYBRID = 0, 1, 2
+SEP_MAX_PIXELS, SEP_MAX_BINS, SEP_MAX_FRAMES = 1 << 25, 32767, 65535
 
 STATUS_NAMES = {0: "SEP_OK", 1: "SEP_ERR_ARG", 2: "SEP_ERR_CUDA", 3: "SEP_ERR_OOM", 4: "SEP_ERR_CAPACITY",
                 5: "SEP_ERR_TIMEOUT", 6: "SEP_ERR_CSR", 7: "SEP_ERR_STATE"}

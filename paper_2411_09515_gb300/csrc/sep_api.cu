@@ -122,11 +122,12 @@ sep_status check_params(sep_ctx* ctx, const sep_params* p) {
 }
 
 sep_status check_common(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames, int32_t dtype,
-                        int32_t n_frames, const sep_params* params) {
+                        int32_t n_frames, const sep_params* params, bool chunked = false) {
   if (!ctx) return SEP_ERR_ARG;
   if (!csr) return fail(ctx, SEP_ERR_ARG, "csr is NULL");
   if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr belongs to another context");
   if (n_frames < 0) return fail(ctx, SEP_ERR_ARG, "n_frames < 0");
+  if (n_frames > SEP_MAX_FRAMES && !chunked) return fail(ctx, SEP_ERR_ARG, "n_frames above SEP_MAX_FRAMES");
   if (n_frames > 0 && !frames) return fail(ctx, SEP_ERR_ARG, "frames is NULL");
   if (dtype == SEP_DTYPE_U16_JF) {
     if (!calib) return fail(ctx, SEP_ERR_ARG, "raw Jungfrau frames need a calibration");
@@ -705,6 +706,7 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
   if (!csr) return fail(ctx, SEP_ERR_ARG, "NULL matrix");
   if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "matrix belongs to another context");
   if (n_frames < 0 || kept_capacity < 0) return fail(ctx, SEP_ERR_ARG, "negative size");
+  if (n_frames > SEP_MAX_FRAMES) return fail(ctx, SEP_ERR_ARG, "n_frames above SEP_MAX_FRAMES");
   if (n_frames == 0) return SEP_OK;
   if (!mean_dev || !out_dev || (noise_dev && !sigma_dev) ||
       (kept_capacity > 0 && (!idx_dev || !val_dev || !n_kept_dev)))
@@ -733,7 +735,8 @@ sep_status sep_compact_frames(sep_ctx* ctx, int32_t n_frames, const int32_t* fra
                               const int32_t* n_pass_dev, int64_t row_bytes, const void* src_dev, void* dst_dev,
                               sep_stream stream) {
   if (!ctx) return SEP_ERR_ARG;
-  if (n_frames < 0 || row_bytes < 0 || row_bytes % 4) return fail(ctx, SEP_ERR_ARG, "n_frames or row_bytes");
+  if (n_frames < 0 || n_frames > SEP_MAX_FRAMES || row_bytes < 0 || row_bytes % 4)
+    return fail(ctx, SEP_ERR_ARG, "n_frames or row_bytes");
   if (n_frames == 0 || row_bytes == 0) return SEP_OK;
   if (!frame_list_dev || !n_pass_dev || !src_dev || !dst_dev) return fail(ctx, SEP_ERR_ARG, "NULL argument");
   const char *s0 = static_cast<const char*>(src_dev), *d0 = static_cast<const char*>(dst_dev);
@@ -858,10 +861,11 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
                             float* sigma_host, int32_t* count_host, int32_t* idx_host, float* val_host,
                             int64_t kept_capacity, int32_t* n_kept_host, sep_peak* peaks_host,
                             int64_t peak_capacity, int32_t* n_peaks_host, int32_t chunk_frames, sep_stream stream) {
-  sep_status st = check_common(ctx, csr, calib, frames_host, dtype, n_frames, params);
+  sep_status st = check_common(ctx, csr, calib, frames_host, dtype, n_frames, params, true);
   if (st != SEP_OK) return st;
   if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
-  if (chunk_frames < 0) return fail(ctx, SEP_ERR_ARG, "chunk_frames < 0");
+  if (chunk_frames < 0 || chunk_frames > SEP_MAX_FRAMES)
+    return fail(ctx, SEP_ERR_ARG, "chunk_frames outside [0, SEP_MAX_FRAMES]");
   if (n_frames > 0 && (!mean_host || !sigma_host || !count_host || !n_kept_host || !n_peaks_host ||
                        (kept_capacity > 0 && (!idx_host || !val_host)) || (peak_capacity > 0 && !peaks_host)))
     return fail(ctx, SEP_ERR_ARG, "NULL argument");
@@ -1101,7 +1105,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
                              sep_stream stream) {
   if (!ctx) return SEP_ERR_ARG;
   if (n_det < 1 || n_det > 4 || !csrs) return fail(ctx, SEP_ERR_ARG, "1 to 4 detectors");
-  if (n_frames < 0 || (n_frames > 0 && !frames)) return fail(ctx, SEP_ERR_ARG, "bad frame list");
+  if (n_frames < 0 || n_frames > SEP_MAX_FRAMES || (n_frames > 0 && !frames))
+    return fail(ctx, SEP_ERR_ARG, "bad frame list");
   if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
   sep_status st = check_params(ctx, params);
   if (st != SEP_OK) return st;
@@ -1111,6 +1116,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
   for (int d = 0; d < n_det; ++d) {
     if (!csrs[d] || csrs[d]->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr missing or from another context");
     if ((st = check_bin_fits(ctx, csrs[d])) != SEP_OK) return st;
+    if (params->error_model != SEP_ERROR_AZIMUTHAL && csrs[d]->has_norm)
+      return fail(ctx, SEP_ERR_ARG, "the Poisson and hybrid models take frames without a norm");
     if (params->surrogate > 0 && (!csrs[d]->model || csrs[d]->model->ctx != ctx))
       return fail(ctx, SEP_ERR_STATE, "surrogate requested but a detector has no model of this context");
   }

@@ -50,6 +50,7 @@ extern "C" sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, con
   };
   if (!csr || csr->ctx != ctx) return fail(csr ? SEP_ERR_STATE : SEP_ERR_ARG, "csr missing or from another context");
   if (n_frames < 0 || capacity < 0) return fail(SEP_ERR_ARG, "n_frames and capacity must be >= 0");
+  if (n_frames > SEP_MAX_FRAMES) return fail(SEP_ERR_ARG, "n_frames above SEP_MAX_FRAMES");
   if (n_frames > 0 && (!frames_dev || !mean_dev || !sigma_dev || !n_kept_dev || (capacity > 0 && (!idx_dev || !val_dev))))
     return fail(SEP_ERR_ARG, "NULL argument");
   if (dtype == SEP_DTYPE_U16_JF) {

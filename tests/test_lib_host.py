@@ -36,6 +36,20 @@ def test_library_exports_every_declared_symbol():
     assert "sm_103a" in B.sep_version()
 
 
+def test_constants_match_header():
+    """Every numeric #define of the header has the same value in the binding."""
+    src = open(os.path.join(ROOT, "include", "sep.h")).read()
+    found = 0
+    for name, val in re.findall(r"^#define[ \t]+(SEP_[A-Z_0-9]+)[ \t]+([^/\n]+)", src, flags=re.M):
+        val = val.strip()
+        if not val:
+            continue
+        assert hasattr(B, name), name
+        assert getattr(B, name) == eval(val.replace("<<", " << "), {}), name
+        found += 1
+    assert found >= 30
+
+
 def test_struct_layouts_match_header():
     import ctypes as C
     assert C.sizeof(B.sep_geometry) == 4 * 2 + 8 * 2 + 8 + 8 * 2 + 8 + 4 * 3 + 4 + 8 * 2  # padded before range
