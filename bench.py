@@ -215,18 +215,19 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # one event between consecutive steps: the total and each step's time
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), device=f"cuda:{local}")
+    ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), device=f"cuda:{local}")
+    per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
     status = sep.device_status()
     n_kept = out["n_kept"].cpu().numpy()
     n_peaks = out["n_peaks"].cpu().numpy()
@@ -297,6 +298,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "step_ms": ({"median": round(per_step[len(per_step) // 2], 4), "min": round(per_step[0], 4),
+                         "max": round(per_step[-1], 4)} if per_step else None),
             "scaling": "weak", "vs_baseline": None, "dtype": "u16->f32",
             "data": "synthetic (seeded Jungfrau-4M-shaped raw frames; no dataset)",
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "nnz": info["nnz"], "max_row": info["max_row"],
