@@ -50,6 +50,45 @@ def test_constants_match_header():
     assert found >= 30
 
 
+def header_structs():
+    """{name: [(field, c type, array length or 0), ...]} of the header's
+    plain structs, in declaration order."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sep.h")).read(), flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const )?\w+\s*\*?)\s*(.*)", decl)
+            ctype = m.group(1).replace(" ", "")
+            for item in m.group(2).split(","):
+                item = item.strip()
+                if item.startswith("*"):
+                    ctype, item = ctype + "*", item[1:]
+                a = re.match(r"(\w+)(?:\[(\d+)\])?$", item)
+                fields.append((a.group(1), ctype, int(a.group(2) or 0)))
+        out[name] = fields
+    return out
+
+
+def test_struct_fields_match_header():
+    """Field names, order and types of every ctypes struct equal the header's."""
+    import ctypes as C
+    cmap = {"int32_t": C.c_int32, "float": C.c_float, "double": C.c_double, "uint64_t": C.c_uint64,
+            "constvoid*": C.c_void_p}
+    hs = header_structs()
+    for cls in (B.sep_geometry, B.sep_params, B.sep_train_cfg, B.sep_frame_desc):
+        want = hs[cls.__name__]
+        got = cls._fields_
+        assert [f[0] for f in got] == [w[0] for w in want], cls.__name__
+        for (name, ct), (_, htype, n) in zip(got, want):
+            base = cmap[htype]
+            assert ct == (base * n if n else base), (cls.__name__, name)
+    assert list(B.PEAK_DTYPE.names) == [w[0] for w in hs["sep_peak"]]
+
+
 def test_struct_layouts_match_header():
     import ctypes as C
     assert C.sizeof(B.sep_geometry) == 4 * 2 + 8 * 2 + 8 + 8 * 2 + 8 + 4 * 3 + 4 + 8 * 2  # padded before range
