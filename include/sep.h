@@ -252,7 +252,9 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
 
 /*
  * Sparsify (Section 3): keep valid pixel i when value_i > mean_b + k_pick sigma_b,
- * b = centre bin of i. Writes, per frame, the first `capacity` kept pixels in
+ * b = centre bin of i (with params->interpolate: the profile interpolated at
+ * the pixel centre, mean(x_i) + k_pick sigma(x_i); the threshold is that sum
+ * rounded down to binary32). Writes, per frame, the first `capacity` kept pixels in
  * ascending index order: idx_dev [n_frames][capacity] (int32) and val_dev
  * [n_frames][capacity] (float32 value), and the true count n_kept_dev
  * [n_frames]. A count above capacity sets SEP_DEV_CAPACITY.
@@ -267,9 +269,13 @@ sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
  * Peak picking (Section 4) over the kept pixels given by a previous
  * sep_sparsify (idx_dev, n_kept_dev, kept_capacity). A kept pixel is a peak
  * when it is the maximum of its patch (ties: the lowest index wins) and at
- * least min_count patch pixels are kept. Writes the first `capacity` peaks
- * per frame in ascending index order to peaks_dev [n_frames][capacity] and
- * the true count to n_peaks_dev [n_frames].
+ * least min_count patch pixels are kept. Its record: I = sum of
+ * (value_j - background_j) over the kept patch pixels j, the centroid of
+ * those weights, sigma = sqrt(sum of deviation_j^2), with background and
+ * deviation the pixel's bin levels (params->interpolate: the profile at the
+ * pixel centre). Writes the first `capacity` peaks per frame in ascending
+ * index order to peaks_dev [n_frames][capacity] and the true count to
+ * n_peaks_dev [n_frames].
  */
 sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
                         const void* frames_dev, int32_t dtype, int32_t n_frames,
