@@ -214,6 +214,15 @@ sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64
  * radius of the pixel centre, then pixel index. perm_inv [npos] receives the
  * pixel of each position (may be NULL); *npos the number of positions. */
 sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos);
+/* Interpolation table of the smooth background (Section 3; densification
+ * and the consumers with interpolate): per pixel, the lower bin a [npix]
+ * and the weight t [npix] (binary32, in [0, 1)) of the upper bin, so that
+ * a profile p at the pixel centre is (1 - t) p[a] + t p[a+1]: u = (x - lo) /
+ * (hi - lo) * nbins - 1/2 for the centre's radial value x, a = floor(u),
+ * t = u - a rounded once; u <= 0 gives (0, 0) and u >= nbins - 1 gives
+ * (nbins - 1, 0) (the end bins' levels). Masked pixels get (0, 0). Host
+ * copies; either pointer may be NULL. */
+sep_status sep_csr_interp(const sep_csr* csr, int32_t* lower_bin, float* weight);
 /* Host copies for inspection (any pointer may be NULL):
  * rowptr [nbins+1], col [nnz] (-1 for padding), coef [nnz] (c_{i,r}; 0 for
  * padding and centre-only entries),

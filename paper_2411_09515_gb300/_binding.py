@@ -36,7 +36,7 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
            "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct",
-           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames"]
+           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames", "sep_csr_interp"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 
@@ -446,6 +446,21 @@ def sep_csr_staging(csr):
     out = np.zeros(max(n.value, 1), np.int32)
     lib().sep_csr_staging(csr, _ptr(out), C.byref(n))
     return out[: n.value]
+
+
+def sep_csr_interp(csr):
+    """Interpolation table of the smooth background: lower bin (int32 [npix])
+    and weight of the upper bin (float32 [npix])."""
+    npix = C.c_int64()
+    st = lib().sep_csr_info(csr, C.byref(npix), None, None, None, None)
+    if st != SEP_OK:
+        raise SepError(st, "sep_csr_info")
+    a = np.zeros(npix.value, np.int32)
+    t = np.zeros(npix.value, np.float32)
+    st = lib().sep_csr_interp(csr, _ptr(a), _ptr(t))
+    if st != SEP_OK:
+        raise SepError(st, "sep_csr_interp")
+    return a, t
 
 
 def sep_correct(ctx, csr, calib, frames, dtype, n_frames, out, stream=None):

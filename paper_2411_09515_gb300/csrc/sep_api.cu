@@ -506,6 +506,15 @@ sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos)
   return SEP_OK;
 }
 
+sep_status sep_csr_interp(const sep_csr* csr, int32_t* lower_bin, float* weight) {
+  if (!csr) return SEP_ERR_ARG;
+  const size_t n = (size_t)csr->npix;
+  if (csr->h.interp_a.size() != n || csr->h.interp_t.size() != n) return SEP_ERR_CSR;
+  if (lower_bin) memcpy(lower_bin, csr->h.interp_a.data(), n * sizeof(int32_t));
+  if (weight) memcpy(weight, csr->h.interp_t.data(), n * sizeof(float));
+  return SEP_OK;
+}
+
 sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, float* coef, int32_t* bin_of_pixel,
                           float* bin_centers) {
   if (!csr) return SEP_ERR_ARG;

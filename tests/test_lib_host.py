@@ -195,3 +195,42 @@ def test_csr_explicit_range_drops_outside():
     det.range = (1.0, 5.0)
     det.nbins = 20
     compare_with_oracle(det)
+
+
+@pytest.mark.parametrize("case", ["config1", "jf_mask_split2", "r_mm_user_range", "exact"])
+def test_interpolation_table_matches_the_oracle(case):
+    """The host-built table of the smooth background (lower bin, binary32
+    weight) equals the oracle's, bit for bit, in three units, with a mask,
+    a user range that leaves pixels beyond the outer bin centres, and exact
+    area fractions (whose automatic range spans the pixels' extents)."""
+    mask = None
+    if case == "config1":
+        det = synth.det_config1()
+    elif case == "jf_mask_split2":
+        det = synth.det_small_jf(split=2, nbins=120, rows=300, cols=260)
+        det.layout = None
+        mask = np.zeros(det.npix, np.uint8)
+        mask[::13] = 1
+    elif case == "r_mm_user_range":
+        det = synth.Detector("r", 60, 70, dist_m=0.05, center_px=(30.3, 25.7), nbins=25, split=1,
+                             unit=synth.UNIT_R_MM, range=(0.5, 2.0))
+    else:
+        det = synth.Detector("x", 40, 44, dist_m=0.05, center_px=(20.3, 18.7), nbins=16, split=0,
+                             unit=synth.UNIT_2TH_DEG)
+    csr = B.sep_build_csr(None, geom_of(det), mask)
+    try:
+        a, t = B.sep_csr_interp(csr)
+    finally:
+        B.sep_csr_destroy(csr)
+    W = oracle.weights_exact(det, mask) if det.split == 0 else oracle.weights(det, mask)
+    oa, ot = oracle.interpolation(det, W)
+    valid = W.bin_of_pixel >= 0
+    assert np.array_equal(a[valid], oa[valid])
+    assert np.array_equal(t[valid].view(np.uint32), np.asarray(ot, np.float32)[valid].view(np.uint32))
+    assert np.all(a[~valid] == 0) and np.all(t[~valid] == 0)
+    assert np.all((t >= 0) & (t < 1)) and np.all((a >= 0) & (a < det.nbins))
+    lo, hi = W.range
+    x = oracle.pixel_unit(det)
+    u = (x - lo) / (hi - lo) * det.nbins - 0.5
+    assert np.any(valid & (u <= 0)) or case != "r_mm_user_range"
+    assert np.all(t[valid & ((u <= 0) | (u >= det.nbins - 1))] == 0)
