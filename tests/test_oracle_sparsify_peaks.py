@@ -100,6 +100,26 @@ def test_hand_built_peak():
     assert p["sigma"] == pytest.approx(1.0, rel=1e-15)        # sqrt(4 * 0.5^2)
 
 
+def test_peak_across_two_bins_uses_each_pixel_bin():
+    # columns >= 4 belong to bin 1 (mean 2, deviation 1, threshold 4);
+    # the rest to bin 0 (mean 1, deviation 0.5, threshold 2)
+    det, W, v = patch_case({(3, 3): 10, (3, 4): 6, (2, 3): 4, (2, 4): 3.5, (3, 2): 3})
+    W.bin_of_pixel[np.arange(det.npix) % det.cols >= 4] = 1
+    mu, sd = np.array([1.0, 2.0]), np.array([0.5, 1.0])
+    pk = oracle.peaks(det, W, v, mu, sd, k_pick=KP, patch=3, min_count=3)
+    assert pk.size == 1
+    p = pk[0]
+    # kept: (3,3) w 9, (3,4) w 4 (bin 1), (2,3) w 3, (3,2) w 2; (2,4) = 3.5 is
+    # below bin 1's threshold although above bin 0's
+    assert p["idx"] == 24 and p["npix"] == 4
+    assert p["I"] == pytest.approx(18.0, rel=1e-15)
+    assert p["y"] == pytest.approx((9 * 3.5 + 4 * 3.5 + 3 * 2.5 + 2 * 3.5) / 18.0, rel=1e-14)
+    assert p["x"] == pytest.approx((9 * 3.5 + 4 * 4.5 + 3 * 3.5 + 2 * 2.5) / 18.0, rel=1e-14)
+    assert p["sigma"] == pytest.approx(math.sqrt(3 * 0.25 + 1.0), rel=1e-15)
+    idx, _ = oracle.sparsify(W, v, mu, sd, k_pick=KP)
+    assert idx.tolist() == [17, 23, 24, 25]
+
+
 def test_plateau_gives_one_peak_lowest_index():
     det, W, v = patch_case({(3, 3): 10, (3, 4): 10, (2, 3): 5})
     pk = oracle.peaks(det, W, v, MU, SD, k_pick=KP, patch=3, min_count=3)
