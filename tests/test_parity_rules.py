@@ -72,3 +72,21 @@ def test_the_rules_separate_the_two_threshold_readings(config1):
     o = _outputs(det, W, frames[:1], interp=interp)
     with pytest.raises(AssertionError):
         check_frame(det, W, frames[0], o, 0, kcap=8192)
+
+
+def test_rules_on_masked_split_raw_frames():
+    """The same on two raw Jungfrau-shaped frames with a mask and 2 x 2
+    splitting, interpolated thresholds."""
+    det = synth.det_small_jf(split=2, nbins=300)
+    mask = det.mask()
+    cal = synth.jf_calib(det.npix, seed=7)
+    spec = synth.spec_jf_serial(11)
+    spec.hit_rate = 0.5
+    fr = synth.frames(det, spec, 0, 2, calib=cal, mask=mask)[0]
+    W = oracle.weights(det, mask)
+    ip = oracle.interpolation(det, W, exact=True)
+    sigs = [oracle.jf_photons(fr[f], cal[0], cal[1]) for f in range(2)]
+    kcap = det.npix // 4
+    o = _outputs(det, W, sigs, interp=ip, kcap=kcap, pcap=20000)
+    for f in range(2):
+        check_frame(det, W, sigs[f], o, f, kcap=kcap, interp=ip)
