@@ -90,3 +90,29 @@ def test_rules_on_masked_split_raw_frames():
     o = _outputs(det, W, sigs, interp=ip, kcap=kcap, pcap=20000)
     for f in range(2):
         check_frame(det, W, sigs[f], o, f, kcap=kcap, interp=ip)
+
+
+def test_band_covers_a_binary32_interpolated_threshold(config1):
+    """The arithmetic the header states for interpolated thresholds (binary32
+    profile at the pixel from binary32 levels and weight, the sum rounded
+    down to binary32), evaluated here in numpy on the oracle's levels, keeps
+    a set the rules accept against the oracle's binary64 thresholds."""
+    det, W, frames, interp = config1
+    a, t = oracle.interpolation(det, W)                       # the library's binary32 table
+    B = W.nbins
+    for sig in frames:
+        o = _outputs(det, W, [sig], interp=interp)
+        m32, s32 = o["mean"][0], o["sigma"][0]
+
+        def prof(p):
+            up = np.where(a + 1 < B, p[np.minimum(a + 1, B - 1)], np.float32(0))
+            return (np.float32(1) - t) * p[a] + t * up           # binary32 operations
+
+        exact = prof(m32).astype(np.float64) + 3.0 * prof(s32).astype(np.float64)
+        thr = exact.astype(np.float32)
+        above = thr.astype(np.float64) > exact
+        thr[above] = np.nextafter(thr[above], np.float32(-np.inf))
+        idx = np.flatnonzero((W.bin_of_pixel >= 0) & (sig > thr)).astype(np.int32)
+        o["idx"][0, :] = -1
+        o["idx"][0, :idx.size], o["val"][0, :idx.size], o["n_kept"][0] = idx, sig[idx], idx.size
+        check_frame(det, W, sig, o, 0, kcap=8192, interp=interp)
