@@ -528,6 +528,22 @@ sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const floa
 sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
                                sep_stream stream);
 
+/* Counters of the clip kernel's tail replay (diagnostics; the method is
+ * unchanged by them). With collection enabled, every later integrate-clip,
+ * batch and mixed call adds to SEP_CLIP_STATS counters held by the context:
+ *   [0] bin-frame items, [1] core scans (pass B), [2] items whose tail slots
+ *   overflowed (their remaining steps ran as full passes), [3] replay steps,
+ *   [4] tail entries listed (summed over core scans), [5] items whose
+ *   kept-pixel marks came from the tail alone, [6] full passes,
+ *   [7] reserved (0).
+ * enable: 1 collect, 0 stop, -1 leave as is (collection costs a few atomics
+ * per block). counts: NULL or SEP_CLIP_STATS values written on return.
+ * reset: nonzero zeroes the counters after reading. Synchronises `stream`
+ * when counts or reset are requested. SEP_ERR_ARG for a NULL context or
+ * enable outside {-1, 0, 1}. */
+#define SEP_CLIP_STATS 8
+sep_status sep_clip_stats(sep_ctx* ctx, int32_t enable, uint64_t* counts, int32_t reset, sep_stream stream);
+
 /* Checkpoint: one JSON header line, then float32 parameters, normalisation,
  * Adam moments. */
 sep_status sep_model_save(const sep_model* model, const char* path);

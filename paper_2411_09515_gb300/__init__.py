@@ -301,6 +301,10 @@ class Separator:
     def device_status(self, stream=None):
         return B.sep_get_device_status(self.ctx, stream)
 
+    def clip_stats(self, enable=-1, read=True, reset=False, stream=None):
+        """Tail-replay counters of the clip kernel (see sep_clip_stats)."""
+        return B.sep_clip_stats(self.ctx, enable, read, reset, stream)
+
 
 class Surrogate:
     """The clip surrogate's network (20 -> 64 -> 64 -> 2, GELU), trained on

@@ -36,9 +36,10 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
            "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct",
-           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames", "sep_csr_interp"]
+           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames", "sep_csr_interp", "sep_clip_stats"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
+SEP_CLIP_STATS = 8
 
 
 class SepError(RuntimeError):
@@ -139,6 +140,7 @@ def lib():
                                        _vp, _vp, _vp, _vp]
     L.sep_surrogate_prepare.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, C.POINTER(C.c_int64), _vp]
     L.sep_surrogate_stats.argtypes = [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int32, _vp]
+    L.sep_clip_stats.argtypes = [_vp, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, _vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("sep_version", "sep_last_error", "sep_ctx_destroy", "sep_csr_destroy", "sep_calib_destroy",
@@ -435,6 +437,18 @@ def sep_surrogate_stats(ctx, reset=False, stream=None):
     a, b = C.c_uint64(0), C.c_uint64(0)
     _check(ctx, lib().sep_surrogate_stats(ctx, C.byref(a), C.byref(b), int(reset), _stream(stream)))
     return a.value, b.value
+
+
+CLIP_STATS_NAMES = ("items", "core_scans", "overflows", "replay_steps", "tail_entries", "tail_marked",
+                    "full_passes", "reserved")
+
+
+def sep_clip_stats(ctx, enable=-1, read=True, reset=False, stream=None):
+    """Tail-replay counters of the clip kernel (a dict when read, else None);
+    enable 1 / 0 switches collection for later calls, -1 leaves it."""
+    buf = (C.c_uint64 * SEP_CLIP_STATS)()
+    _check(ctx, lib().sep_clip_stats(ctx, int(enable), buf if read else None, int(reset), _stream(stream)))
+    return dict(zip(CLIP_STATS_NAMES, (int(x) for x in buf))) if read else None
 
 
 def sep_csr_staging(csr):

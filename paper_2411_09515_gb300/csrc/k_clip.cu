@@ -38,6 +38,8 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sep_device.cuh"
 #include "sep_internal.h"
 #include "sep_mlp.cuh"
@@ -287,12 +289,13 @@ struct Ext {
 
 // One pass: shifted sums about Kf over the entries of weight != 0 whose value
 // lies in [Ln, Hn], and the extremes around the interval (Ext).
+// (tid: the thread's index among the kThreads that share the row)
 template <int MODE, bool KAHAN, int EXT, int kThreads>
 __device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts, const int (&ge)[4], float Ln,
                                           float Hn, float Kf, Ext<EXT>& ex, float (&ss)[Sums<MODE>::NF],
-                                          float (&cc)[Sums<MODE>::NF], uint32_t (&ci)[Sums<MODE>::NI]) {
+                                          float (&cc)[Sums<MODE>::NF], uint32_t (&ci)[Sums<MODE>::NI],
+                                          int tid = threadIdx.x) {
   constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
-  const int tid = threadIdx.x;
 #pragma unroll
   for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
 #pragma unroll
@@ -566,7 +569,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
   int ge[4];   // end of coefficient class 0..3 in the row; weight-0 carriers follow
 #pragma unroll
   for (int c = 0; c < 4; ++c) ge[c] = __ldg(a.grp + 4 * b + c);
-  const uint4* ent4 = reinterpret_cast<const uint4*>(a.ent + r0);
   float4* vals4 = reinterpret_cast<float4*>(vals);
   const int nq = n >> 2;
 
@@ -594,31 +596,16 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
     uint32_t ci0[NI];
     Ext<0> ex0;
     {
-      // Stage the row's packed entries into the value slots (16-byte
-      // cp.async copies); then every thread replaces each of its entries by
-      // the staged value it addresses with a 4-byte cp.async: all of a
-      // thread's loads are in flight at once and land in shared memory
-      // without passing through registers. Consecutive threads take
-      // consecutive entries, which ascend in staging position inside a
-      // coefficient group, so a warp's loads fall on short contiguous runs.
-      // Slot e is read (entry) and then overwritten (value) by one thread.
+      // the row's values are contiguous in the staged frame (slot = entry):
+      // 16-byte copies into shared memory (padding slots hold NaN)
       const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
+      const float4* src4 = reinterpret_cast<const float4*>(vf + r0);
       for (int q = tid; q < nq; q += kThreads)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(ent4 + q)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(src4 + q)
                      : "memory");
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       if (mk_bm) mark_flush(mk_bm, mk_px);   // the previous frame's marks
       mk_bm = nullptr;
-      __syncthreads();
-      // (padding entries address the row's NaN slot, outside every interval)
-      const uint32_t* ents = reinterpret_cast<const uint32_t*>(vals);
-      for (int e = tid; e < n; e += kThreads) {
-        const uint32_t u = ents[e];
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + 4u * (unsigned)e),
-                     "l"(vf + (u & kColMask))
-                     : "memory");
-      }
-      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
       pass_sums<MODE, KAHAN, 0, kThreads>(vals4, wts, ge, -FLT_MAX, FLT_MAX, 0.0f, ex0, ss0, cc0, ci0);
     }
@@ -899,6 +886,622 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(Cl
   if (mk_bm) mark_flush(mk_bm, mk_px);
 }
 
+// ---------------------------------------------------------------------------
+// Clip by tail replay, one warp per bin and frame (the default kernel; the
+// surrogate variants above keep full passes of a whole CTA over a copy of
+// the row's values in shared memory).
+//
+// Every set of the clip loop is a value interval and the intervals are
+// nested (Eq. 19 is cumulative). An interval C = [cLo, cHi] that lies inside
+// every interval the loop has still to visit contributes the same entries,
+// hence the same sums, to each remaining step; only the entries outside C
+// (the tail) need to be tested again. Per bin and frame:
+//   pass A  plain FP32 moments of the full set, used only to place C
+//           kCoreMargin deviations inside the first clip interval;
+//   pass B  one scan of the row: core entries are summed (in the call's
+//           precision, about a shift K), every other valid entry is listed
+//           in its lane's tail slots (value, entry index and class);
+//   replay  the loop of Eq. 19 from the full set: the sums of a step are the
+//           core sums plus a pass over the tail, finalised exactly as a full
+//           pass would be (same set, sums in another order). When a new
+//           interval no longer contains C, C is placed inside it and pass B
+//           runs again; when a lane's tail slots overflow, the remaining
+//           steps run as full passes.
+// The kept-pixel marks come from the tail alone when the threshold lies at
+// or above C (no core entry can exceed it), else from a scan of the row.
+//
+// A warp owns its item from the first load to the marks. The row is read
+// straight from the staged frame (slot = entry, so a bin's values are one
+// contiguous run: 16-byte loads, several in flight per lane); only the tail
+// lives in shared memory, so many items fit an SM. Every total is a warp
+// butterfly, which leaves bit-identical totals on all lanes (addition, and
+// the error-free pair sum, are commutative), so every lane evaluates each
+// clip step itself: no lane waits for another and the CTA never
+// synchronises (its warps take other frames of the same bin).
+constexpr float kCoreMargin = 1.0f;   // core margin inside the clip interval, in deviations
+constexpr int kLoadsAhead = 4;        // 16-byte loads in flight per lane in a scan of the row
+
+// One item's row: entry e's staged value at v4[e / 4] (padding slots NaN).
+struct Row {
+  const float4* v4;
+};
+
+// Scan of every step-th 16-byte group of [q0, q1) of a row by one lane of a
+// warp: fn(v, q) for each of the lane's groups, kLoadsAhead loads issued
+// before their use (groups past q1 are not loaded; fn is not called for
+// them).
+template <class F>
+__device__ __forceinline__ void scan_row(const Row& row, int q0, int q1, int lane, F&& fn, int step = 1) {
+  for (int q = q0 + lane * step; q < q1; q += 32 * step * kLoadsAhead) {
+    float4 v[kLoadsAhead];
+#pragma unroll
+    for (int k = 0; k < kLoadsAhead; ++k)
+      if (q + 32 * step * k < q1) v[k] = __ldg(row.v4 + q + 32 * step * k);
+#pragma unroll
+    for (int k = 0; k < kLoadsAhead; ++k)
+      if (q + 32 * step * k < q1) fn(v[k], q + 32 * step * k);
+  }
+}
+
+// Totals over the warp of NF per-lane sums (value s - c) as pairs
+// hi + lo, identical on every lane: plain FP32 in PLAIN, doubles in
+// FP64MERGE, error-free FP32 pairs otherwise.
+template <int NF, int PREC>
+__device__ __forceinline__ void warp_sum(const float (&s)[NF], const float (&c)[NF], float (&hi)[NF],
+                                         float (&lo)[NF]) {
+#pragma unroll
+  for (int v = 0; v < NF; ++v) {
+    if (PREC == SEP_PREC_PLAIN) {
+      float x = s[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
+      hi[v] = x;
+      lo[v] = 0.0f;
+    } else if (PREC == SEP_PREC_FP64MERGE) {
+      double t = (double)s[v] - (double)c[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      hi[v] = (float)t;
+      lo[v] = (float)(t - (double)hi[v]);
+    } else {
+      float hs = s[v], hc = c[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, hs, o);
+        const float co = __shfl_xor_sync(0xffffffffu, hc, o);
+        pair_add(hs, hc, so, co);
+      }
+      two_sum(hs, -hc, hi[v], lo[v]);
+    }
+  }
+}
+
+// Totals of a pass in the layout unpack_totals reads: NF float pairs, then
+// the NI integer totals as raw bits.
+template <int MODE, int PREC>
+__device__ __forceinline__ void warp_totals(const float (&ss)[Sums<MODE>::NF], const float (&cc)[Sums<MODE>::NF],
+                                            const uint32_t (&ci)[Sums<MODE>::NI], float& n_set, float (&h)[6],
+                                            float (&l)[6]) {
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+  float hi[NF], lo[NF];
+  warp_sum<NF, PREC>(ss, cc, hi, lo);
+  float th[NF + NI], tl[NF + NI];
+#pragma unroll
+  for (int v = 0; v < NF; ++v) {
+    th[v] = hi[v];
+    tl[v] = lo[v];
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    th[NF + i] = __uint_as_float(__reduce_add_sync(0xffffffffu, ci[i]));
+    tl[NF + i] = 0.0f;
+  }
+  unpack_totals<MODE>(th, tl, n_set, h, l);
+}
+
+// Pass A (one lane's share): plain FP32 sums about 0 of the finite entries
+// of every `step`-th group of 4 (a sample of a long row: they only place
+// the core), in the layout of pass_sums.
+template <int MODE>
+__device__ __forceinline__ void lane_full_sums(const Row& row, const float* wts, const int (&ge)[4],
+                                               int lane, int step, float (&ss)[Sums<MODE>::NF],
+                                               uint32_t (&ci)[Sums<MODE>::NI]) {
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) ss[v] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) ci[i] = 0u;
+  if (MODE == MODE_CLASS || MODE == MODE_UNIT) {
+    constexpr int NCLS = MODE == MODE_CLASS ? 4 : 1;
+    int lo = 0;
+#pragma unroll 1
+    for (int cls = 0; cls < NCLS; ++cls) {
+      const int hi = ge[cls];
+      uint32_t cnt = 0;
+      float s1 = 0.0f, s2 = 0.0f;
+      scan_row(row, lo >> 2, hi >> 2, lane, [&](const float4& v4, int) {
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (fabsf(xs[j]) <= FLT_MAX) {   // finite (padding slots hold NaN)
+            ++cnt;
+            s1 = __fadd_rn(s1, xs[j]);
+            s2 = __fmaf_rn(xs[j], xs[j], s2);
+          }
+        }
+      }, step);
+      if (MODE == MODE_CLASS) {
+        const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
+        const uint32_t pk = cnt << (16 * (cls & 1));
+        if (cls < 2) ci[0] += pk;
+        else ci[NI - 1] += pk;
+        ss[0] = fmaf(w, s1, ss[0]);
+        ss[1] = fmaf(w2, s1, ss[1]);
+        ss[2] = fmaf(w2, s2, ss[2]);
+      } else {
+        ci[0] = cnt;
+        ss[0] = s1;
+        ss[1] = s2;
+      }
+      lo = hi;
+    }
+  } else {
+    uint32_t cnt = 0;
+    float om = 0.0f, a1 = 0.0f, oo = 0.0f, b1 = 0.0f, b2 = 0.0f;
+    scan_row(row, 0, ge[3] >> 2, lane, [&](const float4& v4, int q) {
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = wts[4 * q + j];
+        if (w != 0.0f && fabsf(xs[j]) <= FLT_MAX) {
+          const float w2 = __fmul_rn(w, w), w2d = __fmul_rn(w2, xs[j]);
+          ++cnt;
+          om = __fadd_rn(om, w);
+          a1 = __fmaf_rn(w, xs[j], a1);
+          oo = __fadd_rn(oo, w2);
+          b1 = __fadd_rn(b1, w2d);
+          b2 = __fmaf_rn(w2d, xs[j], b2);
+        }
+      }
+    }, step);
+    ci[0] = cnt;
+    ss[0] = om; ss[1] = a1; ss[2] = oo; ss[3] = b1; ss[4] = b2;
+  }
+}
+
+// Pass B (one lane's share): sums about Kf of the entries inside
+// [cLo, cHi] (layout of pass_sums); every other valid entry goes to the
+// lane's tail: slot k at tl[32 k] = (value bits, entry index | class <<
+// 16), written for every entry and kept only for the tail (m counts the
+// slots kept, so the branch-free store of a core entry is overwritten).
+// Returns false when a group of 4 entries found fewer than 4 of the tcap
+// slots left (the sums are then incomplete).
+template <int MODE, bool KAHAN>
+__device__ __forceinline__ bool lane_core_sums(const Row& row, const float* wts, const int (&ge)[4], int lane,
+                                               float cLo, float cHi, float Kf, uint2* tl, int tcap, int& m,
+                                               float (&ss)[Sums<MODE>::NF], float (&cc)[Sums<MODE>::NF],
+                                               uint32_t (&ci)[Sums<MODE>::NI]) {
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) ci[i] = 0u;
+  m = 0;
+  bool fit = true;
+  if (MODE == MODE_CLASS || MODE == MODE_UNIT) {
+    constexpr int NCLS = MODE == MODE_CLASS ? 4 : 1;
+    int lo = 0;
+#pragma unroll 1
+    for (int cls = 0; cls < NCLS; ++cls) {
+      const int hi = ge[cls];
+      uint32_t cnt = 0;
+      Acc<KAHAN> a1, a2;
+      scan_row(row, lo >> 2, hi >> 2, lane, [&](const float4& v4, int q) {
+        if (m + 4 > tcap) fit = false;
+        if (!fit) return;
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool core = xs[j] >= cLo && xs[j] <= cHi;
+          if (core) {
+            const float d = __fsub_rn(xs[j], Kf);
+            ++cnt;
+            a1.add(d);
+            a2.add_prod(d, d);
+          }
+          tl[32 * m] = make_uint2(__float_as_uint(xs[j]), (uint32_t)(4 * q + j) | ((uint32_t)cls << 16));
+          m += (!core && xs[j] == xs[j]) ? 1 : 0;
+        }
+      });
+      if (!fit) return false;
+      const float s1 = a1.val(), s2 = a2.val();
+      if (MODE == MODE_CLASS) {
+        const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
+        const uint32_t pk = cnt << (16 * (cls & 1));
+        if (cls < 2) ci[0] += pk;
+        else ci[NI - 1] += pk;
+        if (KAHAN) {
+          Acc<true> t0, t1, t2;
+          t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
+          t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
+          t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
+        } else {
+          ss[0] = fmaf(w, s1, ss[0]);
+          ss[1] = fmaf(w2, s1, ss[1]);
+          ss[2] = fmaf(w2, s2, ss[2]);
+        }
+      } else {
+        ci[0] = cnt;
+        ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
+      }
+      lo = hi;
+    }
+  } else {
+    uint32_t cnt = 0;
+    Acc<KAHAN> om, a1, oo, b1, b2;
+    scan_row(row, 0, ge[3] >> 2, lane, [&](const float4& v4, int q) {
+      if (m + 4 > tcap) fit = false;
+      if (!fit) return;
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = wts[4 * q + j];
+        if (w == 0.0f) continue;
+        if (xs[j] >= cLo && xs[j] <= cHi) {
+          const float d = __fsub_rn(xs[j], Kf);
+          const float w2 = __fmul_rn(w, w);
+          const float w2d = __fmul_rn(w2, d);
+          ++cnt;
+          om.add(w);
+          a1.add(__fmul_rn(w, d));
+          oo.add(w2);
+          b1.add(w2d);
+          b2.add_prod(w2d, d);
+        } else if (xs[j] == xs[j]) {
+          tl[32 * m] = make_uint2(__float_as_uint(xs[j]), (uint32_t)(4 * q + j));
+          ++m;
+        }
+      }
+    });
+    if (!fit) return false;
+    ci[0] = cnt;
+    ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
+    ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
+  }
+  return true;
+}
+
+// One lane's share of a full pass over [Ln, Hn] about Kf (the layout of
+// pass_sums), read from the staged row.
+template <int MODE, bool KAHAN>
+__device__ __noinline__ void lane_range_sums(const Row& row, const float* wts, const int (&ge)[4],
+                                                int lane, float Ln, float Hn, float Kf,
+                                                float (&ss)[Sums<MODE>::NF], float (&cc)[Sums<MODE>::NF],
+                                                uint32_t (&ci)[Sums<MODE>::NI]) {
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) ci[i] = 0u;
+  if (MODE == MODE_CLASS || MODE == MODE_UNIT) {
+    constexpr int NCLS = MODE == MODE_CLASS ? 4 : 1;
+    int lo = 0;
+#pragma unroll 1
+    for (int cls = 0; cls < NCLS; ++cls) {
+      const int hi = ge[cls];
+      uint32_t cnt = 0;
+      Acc<KAHAN> a1, a2;
+      scan_row(row, lo >> 2, hi >> 2, lane, [&](const float4& v4, int) {
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (xs[j] >= Ln && xs[j] <= Hn) {
+            const float d = __fsub_rn(xs[j], Kf);
+            ++cnt;
+            a1.add(d);
+            a2.add_prod(d, d);
+          }
+        }
+      });
+      const float s1 = a1.val(), s2 = a2.val();
+      if (MODE == MODE_CLASS) {
+        const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
+        const uint32_t pk = cnt << (16 * (cls & 1));
+        if (cls < 2) ci[0] += pk;
+        else ci[NI - 1] += pk;
+        if (KAHAN) {
+          Acc<true> t0, t1, t2;
+          t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
+          t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
+          t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
+        } else {
+          ss[0] = fmaf(w, s1, ss[0]);
+          ss[1] = fmaf(w2, s1, ss[1]);
+          ss[2] = fmaf(w2, s2, ss[2]);
+        }
+      } else {
+        ci[0] = cnt;
+        ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
+      }
+      lo = hi;
+    }
+  } else {
+    uint32_t cnt = 0;
+    Acc<KAHAN> om, a1, oo, b1, b2;
+    scan_row(row, 0, ge[3] >> 2, lane, [&](const float4& v4, int q) {
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = wts[4 * q + j];
+        if (w != 0.0f && xs[j] >= Ln && xs[j] <= Hn) {
+          const float d = __fsub_rn(xs[j], Kf);
+          const float w2 = __fmul_rn(w, w);
+          const float w2d = __fmul_rn(w2, d);
+          ++cnt;
+          om.add(w);
+          a1.add(__fmul_rn(w, d));
+          oo.add(w2);
+          b1.add(w2d);
+          b2.add_prod(w2d, d);
+        }
+      }
+    });
+    ci[0] = cnt;
+    ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
+    ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
+  }
+}
+
+// One lane's tail entries inside [Ln, Hn]: (Omega, A1, OO, B1, B2) about Kf
+// and their count (m: the lane's slots).
+template <int MODE, bool KAHAN>
+__device__ __forceinline__ void lane_tail_sums(const uint2* tl, const float* wts, int m, float Ln, float Hn,
+                                               float Kf, float (&ss)[5], float (&cc)[5], uint32_t& cnt) {
+  Acc<KAHAN> acc[5];
+  cnt = 0;
+  for (int k = 0; k < m; ++k) {
+    const uint2 t = tl[32 * k];
+    const float v = __uint_as_float(t.x);
+    if (v >= Ln && v <= Hn) {
+      float w;
+      if (MODE == MODE_CLASS) w = 1.0f - 0.25f * (float)(t.y >> 16);
+      else if (MODE == MODE_UNIT) w = 1.0f;
+      else w = wts[t.y & 0xffffu];
+      const float d = __fsub_rn(v, Kf);
+      const float w2 = __fmul_rn(w, w);
+      const float w2d = __fmul_rn(w2, d);
+      ++cnt;
+      acc[0].add(w);
+      acc[1].add(__fmul_rn(w, d));
+      acc[2].add(w2);
+      acc[3].add(w2d);
+      acc[4].add_prod(w2d, d);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    ss[v] = acc[v].s;
+    cc[v] = acc[v].c;
+  }
+}
+
+// (h, l) += (a, b) for pairs, in the arithmetic of the precision mode.
+template <int PREC>
+__device__ __forceinline__ void add_pair(float& h, float& l, float a, float b) {
+  if (PREC == SEP_PREC_PLAIN) {
+    h = __fadd_rn(h, a);
+  } else if (PREC == SEP_PREC_FP64MERGE) {
+    const double t = ((double)h + (double)l) + ((double)a + (double)b);
+    h = (float)t;
+    l = (float)(t - (double)h);
+  } else {
+    float s, e;
+    two_sum(h, a, s, e);
+    e = __fadd_rn(e, __fadd_rn(l, b));
+    two_sum(s, e, h, l);
+  }
+}
+
+__device__ __forceinline__ void mark_pixel(uint32_t* bm, const int32_t* cpix, int64_t e) {
+  const int32_t i = __ldg(cpix + e);
+  if (i >= 0) atomicOr(bm + (i >> 5), 1u << (i & 31));
+}
+
+// The first clip interval [lo, hi] from plain FP32 totals of the full set
+// about 0 (h: Omega, A1, OO, B1, B2; the formulas of finalise, poisson_sd
+// and clip_step in single rounding); only the core is placed with it.
+__device__ __forceinline__ void approx_interval(float n_set, const float (&h)[6], float k, int cutoff, int model,
+                                                float dark, float& lo, float& hi, float& mu, float& sd) {
+  lo = -FLT_MAX;
+  hi = FLT_MAX;
+  mu = sd = 0.0f;
+  if (h[0] == 0.0f || h[2] == 0.0f) return;
+  mu = __fdiv_rn(h[1], h[0]);
+  const float vv = __fadd_rn(__fsub_rn(h[4], __fmul_rn(2.0f * mu, h[3])), __fmul_rn(__fmul_rn(mu, mu), h[2]));
+  sd = vv > 0.0f ? __fsqrt_rn(__fdiv_rn(vv, h[2])) : 0.0f;
+  if (model == SEP_ERROR_POISSON) {
+    const float var = __fadd_rn(__fdiv_rn(h[3], h[2]), dark);
+    sd = var > 0.0f ? __fsqrt_rn(var) : 0.0f;
+  }
+  if (cutoff == SEP_CUTOFF_CHAUVENET) {
+    if (n_set <= 2.0f) return;
+    k = chauvenet_k(n_set);
+  }
+  lo = __fsub_rn(mu, __fmul_rn(k, sd));
+  hi = __fadd_rn(mu, __fmul_rn(k, sd));
+}
+
+template <int MODE, int PREC, int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs a) {
+  constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
+  // the tail's share of a step is merged over the lanes in FP32 except
+  // where the per-lane sums are compensated (KAHAN) or merged in FP64
+  constexpr int TPREC = PREC == SEP_PREC_DWORD ? SEP_PREC_PLAIN : PREC;
+  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // [weights (MODE_ENTRY), shared by the warps] then per warp its tail
+  // (8-byte slots, slot k of lane l at 32 k + l)
+  const int capr = MODE == MODE_ENTRY ? (a.cap + 3) & ~3 : 0;
+  float* wts = reinterpret_cast<float*>(smem_raw);
+  uint2* tail = reinterpret_cast<uint2*>(wts + capr) + (size_t)warp * (32 * a.tcap) + lane;
+
+  const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
+  const int f0 = blockIdx.y * a.frames_per_cta;
+  const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
+  const int r0 = __ldg(a.rowptr + b);
+  const int n = __ldg(a.rowptr + b + 1) - r0;      // multiple of 4
+  const int nq = n >> 2;
+  int ge[4];   // end of coefficient class 0..3 in the row; weight-0 carriers follow
+#pragma unroll
+  for (int c = 0; c < 4; ++c) ge[c] = __ldg(a.grp + 4 * b + c);
+
+  if (MODE == MODE_ENTRY) {
+    for (int e = threadIdx.x; e < n; e += 32 * kWarps) {
+      const uint32_t u = __ldg(a.ent + r0 + e);
+      wts[e] = (u & (kZero | kPad)) ? 0.0f : __ldg(a.w + r0 + e);
+    }
+    __syncthreads();
+  }
+  // optional counters: items, pass B scans, overflows, replay steps, tail
+  // entries listed, items marked from the tail, full passes
+  unsigned long long cs[7] = {0, 0, 0, 0, 0, 0, 0};
+
+  for (int f = f0 + warp; f < f1; f += kWarps) {
+    // this item's values: entry e of the row at slot r0 + e of the staged frame
+    const Row row{reinterpret_cast<const float4*>(a.stage + (int64_t)f * a.npos + r0)};
+    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
+    cs[0] += 1;
+    // ------------- pass A: where to place the core -------------
+    float cLo, cHi, K;
+    {
+      float ss[NF], cz[NF];
+      uint32_t ci[NI];
+      // (rows of 2048 entries and more: every 4th group of 4, 512 and more:
+      // every 2nd)
+      const int step = nq >= 512 ? 4 : (nq >= 128 ? 2 : 1);
+      lane_full_sums<MODE>(row, wts, ge, lane, step, ss, ci);
+#pragma unroll
+      for (int v = 0; v < NF; ++v) cz[v] = 0.0f;
+      float n_set, h[6], l[6], lo, hi, mu, sd;
+      warp_totals<MODE, SEP_PREC_PLAIN>(ss, cz, ci, n_set, h, l);
+      approx_interval(n_set * (float)step, h, a.k_clip, a.cutoff, a.error_model, a.dark_var, lo, hi, mu, sd);
+      const float mg = __fmul_rn(kCoreMargin, sd);
+      cLo = __fadd_rn(lo, mg);
+      cHi = __fsub_rn(hi, mg);
+      K = choose_shift(mu, sd);
+    }
+    // ------------- the loop of Eq. 19: replay on core + tail, or full passes -------------
+    Bcast st;
+    st.Ln = -FLT_MAX;
+    st.Hn = FLT_MAX;
+    st.L = -FLT_MAX;
+    st.H = FLT_MAX;
+    st.n_cur = -1.0f;
+    st.steps = -1;
+    st.done = 0;
+    st.Kf = K;
+    bool ovf = false, scan = true;
+    int m = 0;
+    float cn = 0.0f, ch[6], cl[6];
+    for (;;) {
+      const float Ln = st.Ln, Hn = st.Hn;
+      if (scan) {
+        // pass B: the core's sums and the tail, for the core placed last
+        float ss[NF], cc[NF];
+        uint32_t ci[NI];
+        const bool fit =
+            lane_core_sums<MODE, KAHAN>(row, wts, ge, lane, cLo, cHi, K, tail, a.tcap, m, ss, cc, ci);
+        ovf = __any_sync(0xffffffffu, !fit);
+        if (a.clip_stats) {
+          cs[1] += 1;
+          cs[2] += ovf ? 1 : 0;
+          cs[4] += (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)m);
+        }
+        if (!ovf) warp_totals<MODE, PREC>(ss, cc, ci, cn, ch, cl);
+        scan = false;
+      }
+      float n_set, h[6], l[6], Kf;
+      if (!ovf) {
+        // a step of the replay: the core sums plus the tail inside [Ln, Hn]
+        float ts[5], tc[5], th[5], tl[5];
+        uint32_t tn;
+        lane_tail_sums<MODE, KAHAN>(tail, wts, m, Ln, Hn, K, ts, tc, tn);
+        warp_sum<5, TPREC>(ts, tc, th, tl);
+        tn = __reduce_add_sync(0xffffffffu, tn);
+        cs[3] += 1;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          h[v] = ch[v];
+          l[v] = cl[v];
+          add_pair<PREC>(h[v], l[v], th[v], tl[v]);
+        }
+        h[5] = l[5] = 0.0f;
+        n_set = cn + (float)tn;
+        Kf = K;
+      } else {
+        // a tail overflowed: a full pass over [Ln, Hn]
+        float ss[NF], cc[NF];
+        uint32_t ci[NI];
+        Kf = st.Kf;
+        lane_range_sums<MODE, KAHAN>(row, wts, ge, lane, Ln, Hn, Kf, ss, cc, ci);
+        cs[6] += 1;
+        warp_totals<MODE, PREC>(ss, cc, ci, n_set, h, l);
+      }
+      clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model, a.dark_var);
+      if (st.done) break;
+      if (!ovf && (cLo < st.Ln || cHi > st.Hn)) {
+        // the next interval cuts into the core: place it inside and scan again
+        const float mg = __fmul_rn(kCoreMargin, st.sd);
+        cLo = __fadd_rn(st.Ln, mg);
+        cHi = __fsub_rn(st.Hn, mg);
+        K = st.Kf;
+        scan = true;
+      }
+    }
+    if (lane == 0) {
+      a.mean[o] = st.mu_hi;
+      a.sigma[o] = st.sd;
+      a.count[o] = (int32_t)st.n_cur;
+      if (a.bounds) {
+        a.bounds[2 * o] = st.L;
+        a.bounds[2 * o + 1] = st.H;
+      }
+      if (a.iters) a.iters[o] = st.steps;
+    }
+    // threshold of sparsification (Section 3) from the final state
+    const float thr = pick_threshold<PREC>(st, a.k_pick);
+    if (a.thr_out && lane == 0) a.thr_out[o] = thr;
+    if (a.bitmap) {
+      // kept pixels of this bin: its centre entries whose value exceeds the
+      // threshold (only kept pixels touch the pixel table and the bitmap)
+      uint32_t* bm = a.bitmap + (int64_t)f * a.words;
+      const int32_t* cp = a.cpix + r0;
+      // without an overflow and with thr at or above the core, no core entry
+      // exceeds thr: the lane's tail, then the weight-0 carriers of the row;
+      // else every entry (padding slots hold NaN, never above a threshold)
+      const bool from_tail = MODE != MODE_ENTRY && !ovf && thr >= cHi;
+      if (from_tail) {
+        cs[5] += 1;
+        for (int k = 0; k < m; ++k)
+          if (__uint_as_float(tail[32 * k].x) > thr) mark_pixel(bm, cp, (int64_t)(tail[32 * k].y & 0xffffu));
+      }
+      scan_row(row, from_tail ? ge[3] >> 2 : 0, nq, lane, [&](const float4& v4, int q) {
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (xs[j] > thr) mark_pixel(bm, cp, 4 * q + j);
+      });
+    }
+    __syncwarp();   // the tail is rewritten by the warp's next frame
+  }
+  if (a.clip_stats && lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+      if (cs[i]) atomicAdd(a.clip_stats + i, cs[i]);
+  }
+}
+
 // mode 0: set the shared-memory attribute and launch; 1: attribute only
 // (done eagerly before a stream capture); 2: launch only.
 template <int MODE, int PREC, int TPB, int SURR>
@@ -923,16 +1526,71 @@ cudaError_t launch_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStrea
   }
 }
 
+// Opt-in shared memory per block of the current device (cached).
+int smem_optin() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+      v = 48 * 1024;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+template <int MODE, int PREC, int kWarps>
+cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
+  // shared memory: the weights of a row (per-entry weights only), then
+  // each warp's tail (8 bytes a slot, 32 lanes)
+  const long capr = ((long)a.cap + 3) & ~3L;
+  const long wbytes = MODE == MODE_ENTRY ? 4 * capr : 0;
+  const long budget = (long)smem_optin() - kClipStaticSmem - wbytes;
+  long tcap = clip_tail_slots(a.cap, 32 * kWarps);
+  if (kWarps * 256 * tcap > budget) tcap = std::max(0L, budget / (256L * kWarps));
+  if (tcap < 5) tcap = 0;   // no room for a tail: every step runs as a full pass
+  a.tcap = (int32_t)tcap;
+  const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap);
+  auto k = k_clip_warp<MODE, PREC, kWarps>;
+  if (mode != 2) {
+    // the attribute only grows: size classes sharing this instance may set
+    // it in any order before a capture
+    static int attr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if ((int)smem > attr[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr[dev] = (int)smem;
+    }
+    if (mode == 1) return cudaSuccess;
+  }
+  dim3 grid(n_ctas, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
+  k<<<grid, 32 * kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int PREC>
+cudaError_t launch_tail_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
+  switch (tpb) {
+    case 32: return launch_warp_t<MODE, PREC, 1>(a, n_ctas, mode, s);
+    case 64: return launch_warp_t<MODE, PREC, 2>(a, n_ctas, mode, s);
+    case 128: return launch_warp_t<MODE, PREC, 4>(a, n_ctas, mode, s);
+    default: return launch_warp_t<MODE, PREC, 8>(a, n_ctas, mode, s);
+  }
+}
+
 template <int MODE>
 cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
   // the surrogate modes exist for the default precision only
   if (a.rec_feat) return launch_b<MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
   if (a.mlp_w) return launch_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
   switch (prec) {
-    case SEP_PREC_PLAIN: return launch_b<MODE, SEP_PREC_PLAIN, 0>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_KAHAN: return launch_b<MODE, SEP_PREC_KAHAN, 0>(a, n_ctas, tpb, mode, s);
-    case SEP_PREC_FP64MERGE: return launch_b<MODE, SEP_PREC_FP64MERGE, 0>(a, n_ctas, tpb, mode, s);
-    default: return launch_b<MODE, SEP_PREC_DWORD, 0>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_PLAIN: return launch_tail_b<MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_KAHAN: return launch_tail_b<MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);
+    case SEP_PREC_FP64MERGE: return launch_tail_b<MODE, SEP_PREC_FP64MERGE>(a, n_ctas, tpb, mode, s);
+    default: return launch_tail_b<MODE, SEP_PREC_DWORD>(a, n_ctas, tpb, mode, s);
   }
 }
 
@@ -941,6 +1599,14 @@ cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int m
 size_t clip_smem_bytes(int32_t cap, bool weighted) {
   size_t smem = (size_t)cap * (weighted ? 8 : 4);
   return (smem + 15) & ~(size_t)15;
+}
+
+int32_t clip_tail_slots(int32_t cap, int32_t tpb) {
+  // per lane of a warp: 1/8 of the row over 32 lanes, plus the 4 slots a
+  // pass B keeps free and some room for uneven lanes (tpb: the block size,
+  // one warp per item whatever it is)
+  (void)tpb;
+  return (int32_t)((cap + 255) / 256) + 8;
 }
 
 cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, bool split, bool has_norm,

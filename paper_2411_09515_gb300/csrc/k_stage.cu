@@ -1,14 +1,17 @@
-// Staging of a batch: every pixel that the integration matrix uses is
-// corrected once (Section 1.2, divided by its norm, Eq. 1) and written to
-// its staging position, where the clip kernel reads it.
+// Staging of a batch: every pixel of the image is corrected once per frame
+// (Section 1.2, divided by its norm, Eq. 1) and its value is written to the
+// slots of its matrix entries in the frame's staged row (slot e holds entry
+// e's value, padding slots NaN), so the clip kernel reads each bin's values
+// as one contiguous run.
 //
-// One CTA per staging tile (kTileH x kTileW pixels of the image) and group
-// of frames. Threads read tile rows: each thread four consecutive pixels
-// (one vector load where the row is aligned), two frames per step (four in
-// the ring kernel); the tile's values are placed in shared memory at their
-// rank inside the tile,
-// then written out as one contiguous run. Each value is the same IEEE sequence as pixel_value():
-// RN32(RN32(adc - pedestal) / gain), then RN32(. / norm).
+// One CTA per image tile (kTileH x kTileW pixels) and group of frames.
+// Threads read tile rows: each thread four consecutive pixels (one vector
+// load where the row is aligned), two frames per step (four in the ring
+// kernel); the corrected tile sits in shared memory by pixel, then the
+// tile's list of (slot, pixel) pairs, ascending by slot, writes it out (the
+// entries of one bin inside a tile occupy consecutive slots). Each value is
+// the same IEEE sequence as pixel_value(): RN32(RN32(adc - pedestal) /
+// gain), then RN32(. / norm).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,6 +22,7 @@ namespace sep {
 namespace {
 
 constexpr int kTilePix = kTileH * kTileW;
+constexpr int kTileSlots = kTilePix + 4;   // the tile's values, then a NaN (padding slots read it)
 constexpr int kStageThreads = kTilePix / 4;   // 4 consecutive pixels of one row a thread
 constexpr int kRowThreads = kTileW / 4;       // threads covering one tile row
 static_assert(kTileW % 4 == 0 && kStageThreads % 32 == 0 && kStageThreads <= 1024, "tile shape");
@@ -47,34 +51,79 @@ __device__ __forceinline__ void load4(const void* frame, int64_t p, bool (&in)[4
   }
 }
 
+// The tile's (slot, shared-memory index) pairs a thread writes: pairs tid +
+// kStageThreads k for k < kScReg stay in registers for every frame, longer
+// lists read the rest at each scatter. Padding pairs point at the NaN.
+constexpr int kScReg = 8;
+
+struct TileScatter {
+  int slot[kScReg], loc[kScReg];
+  int n;   // pairs held
+  __device__ __forceinline__ void load(const StageArgs& a, int eb, int ne) {
+    n = 0;
+#pragma unroll
+    for (int k = 0; k < kScReg; ++k) {
+      const int j = threadIdx.x + kStageThreads * k;
+      int2 sc = make_int2(0, kTilePix);
+      if (j < ne) {
+        sc = __ldg(a.tile_sc + eb + j);
+        n = k + 1;
+      }
+      slot[k] = sc.x;
+      loc[k] = sc.y >= 0 ? sc.y : kTilePix;
+    }
+  }
+};
+
+// Scatter of NF corrected tiles (tv[h]) of frames f .. f + NF - 1 (the
+// first nf of them) to their entries' slots.
+template <int NF>
+__device__ __forceinline__ void scatter_tile(const StageArgs& a, const TileScatter& ts, const float (*tv)[kTileSlots],
+                                             int eb, int ne, int64_t f, int nf) {
+  float* out[NF];
+#pragma unroll
+  for (int h = 0; h < NF; ++h) out[h] = a.stage + (f + min(h, nf - 1)) * a.npos;
+#pragma unroll
+  for (int k = 0; k < kScReg; ++k) {
+    if (k >= ts.n) break;
+#pragma unroll
+    for (int h = 0; h < NF; ++h)
+      if (h < nf) out[h][ts.slot[k]] = tv[h][ts.loc[k]];
+  }
+  for (int j = threadIdx.x + kStageThreads * kScReg; j < ne; j += kStageThreads) {
+    const int2 sc = __ldg(a.tile_sc + eb + j);
+    const int l = sc.y >= 0 ? sc.y : kTilePix;
+#pragma unroll
+    for (int h = 0; h < NF; ++h)
+      if (h < nf) out[h][sc.x] = tv[h][l];
+  }
+}
+
 template <int DT, bool NORM, bool VEC>
 __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
-  __shared__ float tv[2][kTilePix];
+  __shared__ float tv[2][kTileSlots];
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
-  const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
-  if (t == 0 && tid == 0) {   // the NaN slot of padding entries, once per frame
-    const int f1n = min((int)(blockIdx.y + 1) * a.frames_per_cta, a.n_frames);
-    for (int f = blockIdx.y * a.frames_per_cta; f < f1n; ++f)
-      a.stage[(int64_t)f * a.npos + a.nan_pos] = __int_as_float(0x7fc00000);
-  }
-  if (cnt == 0) return;
+  const int eb = __ldg(a.tile_ebase + t), ne = __ldg(a.tile_ebase + t + 1) - eb;
+  if (ne == 0) return;
+  if (tid < 2) tv[tid][kTilePix] = __int_as_float(0x7fc00000);
+  TileScatter ts;
+  ts.load(a, eb, ne);
+  const int loc0 = (tid / kRowThreads) * kTileW + 4 * (tid % kRowThreads);   // this thread's pixels in the tile
   const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / kRowThreads;
   const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % kRowThreads);
   const int64_t p = r * a.cols + c;    // first of this thread's 4 pixels
   bool in[4];
-  int rank[4];
   float p0[4], g0[4], nm[4];
   bool any = false;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     in[k] = r < a.rows && c + k < a.cols;
-    rank[k] = in[k] ? __ldg(a.tile_rank + p + k) : -1;
-    any = any || rank[k] >= 0;
+    any = any || in[k];
     p0[k] = 0.0f;
     g0[k] = 1.0f;
     nm[k] = 1.0f;
-    if (rank[k] >= 0) {
+    if (in[k]) {
       if (DT == SEP_DTYPE_U16_JF) {
         p0[k] = __ldg(a.ped + p + k);
         g0[k] = __ldg(a.gain + p + k);
@@ -100,7 +149,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
       if (h >= nf) continue;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (rank[k] < 0) continue;
+        if (!in[k]) continue;
         float x;
         if (DT == SEP_DTYPE_U16_JF) {
           const uint32_t u = w[h][k], code = u >> 14;
@@ -115,14 +164,11 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
           x = __uint_as_float(w[h][k]);
         }
         if (NORM) x = __fdiv_rn(x, nm[k]);
-        tv[h][rank[k]] = x;
+        tv[h][loc0 + k] = x;
       }
     }
     __syncthreads();
-    for (int h = 0; h < nf; ++h) {
-      float* out = a.stage + (int64_t)(f + h) * a.npos + base;
-      for (int j = tid; j < cnt; j += kStageThreads) out[j] = tv[h][j];
-    }
+    scatter_tile<2>(a, ts, tv, eb, ne, f, nf);
     __syncthreads();
   }
 }
@@ -137,33 +183,29 @@ template <int DT, bool NORM>
 __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   constexpr int kVec = DT == SEP_DTYPE_U16_JF ? 8 : 16;   // bytes of 4 raw words
   constexpr int kRing = 8;   // frames ahead (a multiple of the 4 frames of a step)
-  __shared__ float tv[4][kTilePix];
+  __shared__ float tv[4][kTileSlots];
   __shared__ __align__(16) unsigned char ring[kRing][kStageThreads * kVec];
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
-  const int base = __ldg(a.tile_base + t), cnt = __ldg(a.tile_base + t + 1) - base;
-  if (t == 0 && tid == 0) {   // the NaN slot of padding entries, once per frame
-    const int f1n = min((int)(blockIdx.y + 1) * a.frames_per_cta, a.n_frames);
-    for (int f = blockIdx.y * a.frames_per_cta; f < f1n; ++f)
-      a.stage[(int64_t)f * a.npos + a.nan_pos] = __int_as_float(0x7fc00000);
-  }
-  if (cnt == 0) return;
+  const int eb = __ldg(a.tile_ebase + t), ne = __ldg(a.tile_ebase + t + 1) - eb;
+  if (ne == 0) return;
+  if (tid < 4) tv[tid][kTilePix] = __int_as_float(0x7fc00000);
+  TileScatter ts;
+  ts.load(a, eb, ne);
+  const int loc0 = (tid / kRowThreads) * kTileW + 4 * (tid % kRowThreads);   // this thread's pixels in the tile
   const int64_t r = (int64_t)(t / a.tiles_x) * kTileH + tid / kRowThreads;
   const int64_t c = (int64_t)(t % a.tiles_x) * kTileW + 4 * (tid % kRowThreads);
   const int64_t p = r * a.cols + c;    // first of this thread's 4 pixels
   // (columns are a multiple of 4: a thread's 4 pixels are all inside or all outside)
   const bool inside = r < a.rows && c < a.cols;
-  int rank[4];
   float p0[4], g0[4], r0[4], nm[4];
-  bool any = false;
+  const bool any = inside;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    rank[k] = inside ? __ldg(a.tile_rank + p + k) : -1;
-    any = any || rank[k] >= 0;
     p0[k] = 0.0f;
     g0[k] = 1.0f;
     nm[k] = 1.0f;
-    if (rank[k] >= 0) {
+    if (inside) {
       if (DT == SEP_DTYPE_U16_JF) {
         p0[k] = __ldg(a.ped + p + k);
         g0[k] = __ldg(a.gain + p + k);
@@ -214,7 +256,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
       if (h >= nf) continue;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (rank[k] < 0) continue;
+        if (!inside) continue;
         float x;
         if (DT == SEP_DTYPE_U16_JF) {
           const uint32_t u = w[h][k], code = u >> 14;
@@ -240,19 +282,16 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
           x = __uint_as_float(w[h][k]);
         }
         if (NORM) x = __fdiv_rn(x, nm[k]);
-        tv[h][rank[k]] = x;
+        tv[h][loc0 + k] = x;
       }
     }
-    // the two slots just read are refilled (this thread's own words, already in registers)
+    // the slots just read are refilled (this thread's own words, already in registers)
     issue(j + kRing);
     issue(j + kRing + 1);
     issue(j + kRing + 2);
     issue(j + kRing + 3);
     __syncthreads();
-    for (int h = 0; h < nf; ++h) {
-      float* out = a.stage + (int64_t)(f0 + j + h) * a.npos + base;
-      for (int q = tid; q < cnt; q += kStageThreads) out[q] = tv[h][q];
-    }
+    scatter_tile<4>(a, ts, tv, eb, ne, (int64_t)(f0 + j), nf);
     __syncthreads();
   }
 }

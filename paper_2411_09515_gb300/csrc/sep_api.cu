@@ -45,10 +45,9 @@ sep_status upload(sep_ctx* ctx, T** dst, const T* src, size_t n) {
   return SEP_OK;
 }
 
-// Row stride of a frame's staged values: the positions plus the NaN slot
-// that padding entries address, rounded up to 32 floats so every frame's row
-// starts 128-byte aligned (vector loads).
-int64_t stage_stride(const sep_csr* csr) { return (csr->h.npos + 1 + 31) & ~(int64_t)31; }
+// Row stride of a frame's staged values: one slot per matrix entry, rounded
+// up to 32 floats so every frame's row starts 128-byte aligned (vector loads).
+int64_t stage_stride(const sep_csr* csr) { return ((int64_t)csr->h.ent.size() + 31) & ~(int64_t)31; }
 
 int64_t bitmap_words(int64_t npix) {
   int64_t w = (npix + 31) / 32;
@@ -171,7 +170,7 @@ void set_interp(sep::PixArgs& p, const sep_csr* csr, const sep_params* params) {
 sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
   int optin = 0;
   SEP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->weighted) + 1024;  // + static shared memory
+  const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->weighted) + sep::kClipStaticSmem;
   if (need > (size_t)optin) {
     char buf[160];
     snprintf(buf, sizeof buf, "largest bin (%d entries) needs %zu bytes of shared memory, device allows %d",
@@ -191,7 +190,8 @@ void free_plan(sep_csr* csr) {
 sep_status make_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds, const int32_t* tpb) {
   if (n_classes < 1 || n_classes > 4) return fail(ctx, SEP_ERR_ARG, "1 to 4 classes");
   for (int i = 0; i < n_classes; ++i) {
-    if (tpb[i] != 64 && tpb[i] != 128 && tpb[i] != 256) return fail(ctx, SEP_ERR_ARG, "threads per block: 64, 128 or 256");
+    if (tpb[i] != 32 && tpb[i] != 64 && tpb[i] != 128 && tpb[i] != 256)
+      return fail(ctx, SEP_ERR_ARG, "threads per block: 32, 64, 128 or 256");
     if (i + 1 < n_classes && (thresholds[i] < 1 || (i > 0 && thresholds[i] <= thresholds[i - 1])))
       return fail(ctx, SEP_ERR_ARG, "thresholds must ascend");
   }
@@ -224,12 +224,18 @@ sep_status make_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_
   return SEP_OK;
 }
 
-int frames_per_cta(const sep_ctx* ctx, int32_t n_frames, int32_t nbins) {
-  // enough CTAs to fill the GPU several times over, at most 4 frames per CTA
-  // (8 and 16 measured slower on 512 Jungfrau-4M frames)
-  int64_t target = (int64_t)ctx->num_sms * 16;
+// block size of the clip kernel without a plan (one warp per item)
+constexpr int32_t kDefaultTpb = 32;
+
+int frames_per_cta(const sep_ctx* ctx, int32_t n_frames, int32_t nbins, int32_t tpb = 32) {
+  // enough CTAs to fill the GPU several times over, at most 4 frames per
+  // warp; the clip kernel gives each warp of a CTA its own frames, so a
+  // CTA takes a multiple of its warps
+  const int64_t target = (int64_t)ctx->num_sms * 16;
   int64_t fpc = ((int64_t)n_frames * nbins) / std::max<int64_t>(target, 1);
-  return (int)std::min<int64_t>(std::max<int64_t>(fpc, 1), 4);
+  fpc = std::min<int64_t>(std::max<int64_t>(fpc, 1), 4);
+  const int64_t w = std::max(tpb / 32, 1);
+  return (int)(((fpc + w - 1) / w) * w);
 }
 
 sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, int32_t n_frames, const sep_params* pr,
@@ -259,6 +265,7 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.bounds = bounds;
   a.iters = iters;
   a.thr_out = thr_out;
+  if (ctx->clip_stats_on) a.clip_stats = ctx->d_clip_stats;
   if (pr->surrogate > 0 && csr->model) {
     a.mlp_w = csr->model->d_wbf;
     a.mlp_norm = csr->model->d_norm;
@@ -277,7 +284,6 @@ cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* cal
   g.fptr = fptr;
   g.npix = csr->npix;
   g.npos = stage_stride(csr);
-  g.nan_pos = csr->h.npos;
   g.rows = csr->h.rows;
   g.cols = csr->h.cols;
   g.tiles_x = csr->h.tiles_x;
@@ -287,8 +293,8 @@ cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* cal
   g.ped = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_ped : nullptr;
   g.gain = calib && dtype == SEP_DTYPE_U16_JF ? calib->d_gain : nullptr;
   g.norm = csr->d_norm;
-  g.tile_rank = csr->d_tile_rank;
-  g.tile_base = csr->d_tile_base;
+  g.tile_ebase = csr->d_tile_ebase;
+  g.tile_sc = csr->d_tile_sc;
   g.stage = stage;
   return sep::launch_stage(g, dtype, csr->has_norm, s);
 }
@@ -302,14 +308,15 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
   if (csr->plan.empty()) {
     a.bin_list = nullptr;
     a.cap = std::max(csr->h.max_row, 4);
-    return sep::launch_integrate_clip(a, csr->h.nbins, 256, split, csr->weighted, precision, mode, s);
+    a.frames_per_cta = frames_per_cta(ctx, a.n_frames, csr->h.nbins, kDefaultTpb);
+    return sep::launch_integrate_clip(a, csr->h.nbins, kDefaultTpb, split, csr->weighted, precision, mode, s);
   }
   const int nc = (int)csr->plan.size();
   if (nc == 1 || mode == 1 || !allow_fork) {
     for (const auto& k : csr->plan) {
       a.bin_list = k.d_bins;
       a.cap = k.cap;
-      a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
+      a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins, k.tpb);
       cudaError_t e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->weighted, precision, mode, s);
       if (e != cudaSuccess) return e;
     }
@@ -322,7 +329,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
     if (i > 0) e = cudaStreamWaitEvent(si, ctx->ev_fork, 0);
     a.bin_list = k.d_bins;
     a.cap = k.cap;
-    a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins);
+    a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins, k.tpb);
     if (e == cudaSuccess)
       e = sep::launch_integrate_clip(a, k.n_bins, k.tpb, split, csr->weighted, precision, mode, si);
     if (e == cudaSuccess && i > 0) e = cudaEventRecord(ctx->ev_join[i], si);
@@ -351,12 +358,15 @@ sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_surr, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_surr, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_clip_stats, SEP_CLIP_STATS * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_clip_stats, 0, SEP_CLIP_STATS * sizeof(unsigned long long));
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_surr) cudaFree(c->d_surr);
+    if (c->d_clip_stats) cudaFree(c->d_clip_stats);
     delete c;
     return SEP_ERR_CUDA;
   }
@@ -373,6 +383,7 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   }
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_surr) cudaFree(ctx->d_surr);
+  if (ctx->d_clip_stats) cudaFree(ctx->d_clip_stats);
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);
@@ -450,9 +461,10 @@ sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* 
       (st = upload(ctx, &c->d_interp_t, c->h.interp_t.data(), c->h.interp_t.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_bop, c->h.bop.data(), c->h.bop.size())) != SEP_OK ||
       (st = upload(ctx, &c->d_grp, c->h.grp.data(), c->h.grp.size())) != SEP_OK ||
-      (st = upload(ctx, &c->d_pos_of, c->h.pos_of.data(), c->h.pos_of.size())) != SEP_OK ||
-      (st = upload(ctx, &c->d_tile_rank, c->h.tile_rank.data(), c->h.tile_rank.size())) != SEP_OK ||
-      (st = upload(ctx, &c->d_tile_base, c->h.tile_base.data(), c->h.tile_base.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_pos_of, c->h.slot_of.data(), c->h.slot_of.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_tile_ebase, c->h.tile_ebase.data(), c->h.tile_ebase.size())) != SEP_OK ||
+      (st = upload(ctx, &c->d_tile_sc, reinterpret_cast<const int2*>(c->h.tile_sc.data()),
+                   c->h.tile_sc.size() / 2)) != SEP_OK ||
       (c->weighted && (st = upload(ctx, &c->d_w, c->h.w.data(), c->h.w.size())) != SEP_OK) ||
       (c->has_norm && (st = upload(ctx, &c->d_norm, norm_host, (size_t)c->npix)) != SEP_OK)) {
     sep_csr_destroy(c);
@@ -480,8 +492,8 @@ void sep_csr_destroy(sep_csr* csr) {
   cudaFree(csr->d_bop);
   cudaFree(csr->d_grp);
   cudaFree(csr->d_pos_of);
-  cudaFree(csr->d_tile_rank);
-  cudaFree(csr->d_tile_base);
+  cudaFree(csr->d_tile_ebase);
+  cudaFree(csr->d_tile_sc);
   delete csr;
 }
 
@@ -522,7 +534,7 @@ sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, flo
   if (rowptr) memcpy(rowptr, h.rowptr.data(), h.rowptr.size() * 4);
   if (col)
     for (size_t e = 0; e < h.ent.size(); ++e)
-      col[e] = (h.ent[e] & sep::kPad) ? -1 : h.perm_inv[h.ent[e] & sep::kColMask];
+      col[e] = (h.ent[e] & sep::kPad) ? -1 : (int32_t)(h.ent[e] & sep::kColMask);
   if (coef) memcpy(coef, h.coef.data(), h.coef.size() * 4);
   if (bin_of_pixel) memcpy(bin_of_pixel, h.bop.data(), h.bop.size() * 4);
   if (bin_centers) memcpy(bin_centers, h.centers.data(), h.centers.size() * 4);
@@ -635,6 +647,23 @@ sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_
   SEP_CUDA(ctx, cudaStreamSynchronize(s));
   if (accepted) *accepted = v[0];
   if (fell_back) *fell_back = v[1];
+  return SEP_OK;
+}
+
+sep_status sep_clip_stats(sep_ctx* ctx, int32_t enable, uint64_t* counts, int32_t reset, sep_stream stream) {
+  if (!ctx) return SEP_ERR_ARG;
+  if (enable < -1 || enable > 1) return fail(ctx, SEP_ERR_ARG, "enable must be -1, 0 or 1");
+  SEP_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (counts || reset) {
+    unsigned long long v[SEP_CLIP_STATS] = {};
+    if (counts) SEP_CUDA(ctx, cudaMemcpyAsync(v, ctx->d_clip_stats, sizeof v, cudaMemcpyDeviceToHost, s));
+    if (reset) SEP_CUDA(ctx, cudaMemsetAsync(ctx->d_clip_stats, 0, sizeof v, s));
+    SEP_CUDA(ctx, cudaStreamSynchronize(s));
+    if (counts)
+      for (int i = 0; i < SEP_CLIP_STATS; ++i) counts[i] = v[i];
+  }
+  if (enable >= 0) ctx->clip_stats_on = enable != 0;
   return SEP_OK;
 }
 
@@ -821,7 +850,8 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                                (uint64_t)peak_capacity, (uint64_t)(uintptr_t)n_peaks_dev,
                                (uint64_t)(uintptr_t)ctx->d_bitmap, (uint64_t)(uintptr_t)ctx->d_aux,
                                (uint64_t)(uintptr_t)s, csr->plan_version, (uint64_t)(uintptr_t)csr->model,
-                               (uint64_t)(uintptr_t)ctx->d_stage, (uint64_t)(uintptr_t)ctx->d_thr};
+                               (uint64_t)(uintptr_t)ctx->d_stage, (uint64_t)(uintptr_t)ctx->d_thr,
+                               (uint64_t)ctx->clip_stats_on};
   {
     uint32_t pw[sizeof(sep_params) / 4];
     memcpy(pw, params, sizeof(sep_params));
@@ -1003,7 +1033,7 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   cudaDeviceProp prop;
   SEP_CUDA(ctx, cudaGetDeviceProperties(&prop, ctx->device));
   char key[512];
-  snprintf(key, sizeof key, "%dx%d|bins=%d|split=%d|nnz=%lld|max=%d|norm=%d|dtype=%d|prec=%d|%s", csr->h.rows,
+  snprintf(key, sizeof key, "warp-tail|%dx%d|bins=%d|split=%d|nnz=%lld|max=%d|norm=%d|dtype=%d|prec=%d|%s", csr->h.rows,
            csr->h.cols, csr->h.nbins, csr->h.split, (long long)csr->nnz, csr->h.max_row, (int)csr->has_norm, dtype,
            params->precision, prop.name);
   // a plan already tuned for this detector and device
@@ -1030,15 +1060,17 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
     }
   }
   // timed search over size-class splits and block sizes
+  // (the clip kernel gives each warp its own frames: the block size sets how
+  // many frames of one bin a CTA holds at once; size classes let short rows
+  // take little shared memory, so more of them fit an SM)
   struct Cand { int nc; int t[3]; int b[4]; };
   std::vector<Cand> cands;
-  for (int b0 : {64, 128, 256}) cands.push_back({1, {0, 0, 0}, {b0, 0, 0, 0}});
-  for (int thr : {1024, 2048, 4096, 8192})
-    for (int b0 : {64, 128, 256})
-      for (int b1 : {128, 256}) cands.push_back({2, {thr, 0, 0}, {b0, b1, 0, 0}});
-  // three classes: small rows need little shared memory and fit more CTAs per SM
-  const int t3[3][2] = {{4096, 8192}, {6144, 10240}, {4096, 10240}};
-  const int b3[4][3] = {{128, 128, 256}, {128, 256, 256}, {64, 128, 256}, {128, 128, 128}};
+  for (int b0 : {32, 64, 128}) cands.push_back({1, {0, 0, 0}, {b0, 0, 0, 0}});
+  for (int thr : {2048, 4096, 6144, 8192})
+    for (const auto& bb : {std::pair<int, int>{32, 32}, {64, 32}, {128, 32}, {64, 64}})
+      cands.push_back({2, {thr, 0, 0}, {bb.first, bb.second, 0, 0}});
+  const int t3[3][2] = {{4096, 8192}, {6144, 10240}, {2048, 6144}};
+  const int b3[3][3] = {{32, 32, 32}, {64, 32, 32}, {128, 64, 32}};
   for (const auto& tt : t3)
     for (const auto& bb : b3) cands.push_back({3, {tt[0], tt[1], 0}, {bb[0], bb[1], bb[2], 0}});
   float* d_out = nullptr;
@@ -1263,7 +1295,7 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
                                (uint64_t)(uintptr_t)n_peaks_dev, (uint64_t)(uintptr_t)ctx->d_bitmap,
                                (uint64_t)(uintptr_t)ctx->d_aux, (uint64_t)(uintptr_t)ctx->d_desc,
                                (uint64_t)(uintptr_t)s, (uint64_t)(uintptr_t)ctx->d_stage,
-                               (uint64_t)(uintptr_t)ctx->d_thr};
+                               (uint64_t)(uintptr_t)ctx->d_thr, (uint64_t)ctx->clip_stats_on};
   for (int d = 0; d < n_det; ++d) {
     key.push_back((uint64_t)(uintptr_t)csrs[d]);
     key.push_back(csrs[d]->plan_version);

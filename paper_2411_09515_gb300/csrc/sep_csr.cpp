@@ -376,11 +376,8 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     out->tile_base[tx * ty] = (int32_t)out->perm_inv.size();
     out->pos_of = pos_of;
     out->npos = (int64_t)out->perm_inv.size();
-    // padding entries address position npos, which the staging kernel
-    // fills with NaN (outside every interval): the gather needs no branch
-    for (auto& u : out->ent)
-      if (u & kPad) u = kPad | (uint32_t)out->npos;
-    // remap and re-sort every group (bin, class) by staging position
+    // re-sort every group (bin, class) by staging position: the entries of
+    // one bin inside one tile then take consecutive slots of the staged row
     std::vector<std::pair<uint32_t, int64_t>> grp_e;
     std::vector<uint32_t> ent2;
     std::vector<float> coef2, w2;
@@ -399,7 +396,7 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
         w2.resize(grp_e.size());
         for (size_t k = 0; k < grp_e.size(); ++k) {
           const int64_t e = grp_e[k].second;
-          ent2[k] = (out->ent[e] & ~kColMask) | grp_e[k].first;
+          ent2[k] = out->ent[e];
           coef2[k] = out->coef[e];
           if (!out->w.empty()) w2[k] = out->w[e];
         }
@@ -412,12 +409,47 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     }
   }
   // per entry: its pixel if the entry carries the pixel's centre bin (one
-  // such entry per staged pixel), else -1; the clip kernel marks kept
-  // pixels through these
+  // such entry per pixel with entries), else -1; the clip kernel marks kept
+  // pixels through these, and the consumers read a pixel's staged value at
+  // its centre entry's slot
   out->cpix.assign((size_t)nnz, -1);
+  out->slot_of.assign((size_t)npix, -1);
   for (int64_t e = 0; e < nnz; ++e) {
     const uint32_t u = out->ent[e];
-    if ((u & kCentre) && !(u & kPad)) out->cpix[(size_t)e] = out->perm_inv[u & kColMask];
+    if ((u & kCentre) && !(u & kPad)) {
+      out->cpix[(size_t)e] = (int32_t)(u & kColMask);
+      out->slot_of[u & kColMask] = (int32_t)e;
+    }
+  }
+  // Staged copy of a frame: one value per entry, in row order (slot e holds
+  // entry e's pixel value; padding slots hold NaN). The staging kernel works
+  // by image tiles: each tile lists the slots of its pixels' entries in
+  // ascending order with the pixel's index inside the tile (row * kTileW +
+  // column), -1 for the padding slots it fills (spread over the tiles).
+  {
+    const int64_t tx = out->tiles_x, nt = (int64_t)out->tiles_x * out->tiles_y;
+    auto tile_of = [&](int64_t e) -> int64_t {
+      const uint32_t u = out->ent[(size_t)e];
+      if (u & kPad) return (e >> 2) % nt;
+      const int64_t i = u & kColMask, r = i / cols, c = i % cols;
+      return (r / kTileH) * tx + c / kTileW;
+    };
+    out->tile_ebase.assign((size_t)nt + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) out->tile_ebase[(size_t)tile_of(e) + 1] += 1;
+    for (int64_t t = 0; t < nt; ++t) out->tile_ebase[(size_t)t + 1] += out->tile_ebase[(size_t)t];
+    std::vector<int64_t> fill_t(out->tile_ebase.begin(), out->tile_ebase.end() - 1);
+    out->tile_sc.assign((size_t)nnz * 2, -1);
+    for (int64_t e = 0; e < nnz; ++e) {
+      const int64_t t = tile_of(e), k = fill_t[(size_t)t]++;
+      const uint32_t u = out->ent[(size_t)e];
+      int32_t loc = -1;
+      if (!(u & kPad)) {
+        const int64_t i = u & kColMask;
+        loc = (int32_t)((i / cols) % kTileH * kTileW + (i % cols) % kTileW);
+      }
+      out->tile_sc[(size_t)k * 2] = (int32_t)e;
+      out->tile_sc[(size_t)k * 2 + 1] = loc;
+    }
   }
   out->rows = gm.rows;
   out->cols = gm.cols;

@@ -14,7 +14,7 @@
 
 // ---- packed CSR entry ---------------------------------------------------
 // One 32-bit word per nonzero of the integration matrix:
-//   bits  0..24  pixel index (column of the matrix), < 2^25
+//   bits  0..24  pixel index (column of the matrix), < 2^25 (0 for padding)
 //   bits 25..26  k - 1 where k / split^2 is the coefficient c_{i,r} (k = 1..4)
 //   bit  27      the entry's bin is the pixel's centre bin (threshold bin)
 //   bit  28      zero coefficient: the entry exists only to carry bit 27
@@ -42,13 +42,18 @@ struct HostCsr {
   std::vector<int32_t> bop;      // [npix] centre bin, -1 masked
   std::vector<float> centers;    // [nbins]
   int32_t max_row = 0;
-  // staging order (entries address pixels by staging position)
-  int64_t npos = 0;                 // staged pixels (those with an entry)
+  // staging order of the pixels (the order of the entries inside each
+  // coefficient group of a row)
+  int64_t npos = 0;                 // pixels with an entry
   int32_t tiles_x = 0, tiles_y = 0;
   std::vector<int32_t> perm_inv;    // [npos] pixel of each staging position
-  std::vector<int32_t> pos_of;      // [npix] staging position of each pixel, -1 if not staged
-  std::vector<int16_t> tile_rank;   // [npix] position inside its tile, -1 not staged
+  std::vector<int32_t> pos_of;      // [npix] staging position of each pixel, -1 if none
+  std::vector<int16_t> tile_rank;   // [npix] position inside its tile, -1 if none
   std::vector<int32_t> tile_base;   // [tiles + 1] first position of each tile
+  // staged copy of a frame (one value per entry, slot = entry index)
+  std::vector<int32_t> slot_of;     // [npix] slot of the pixel's centre entry, -1 if none
+  std::vector<int32_t> tile_ebase;  // [tiles + 1] first scatter pair of each tile
+  std::vector<int32_t> tile_sc;     // [nnz][2] (slot, pixel index in the tile or -1: padding), by tile
 };
 
 constexpr int kTileH = 32, kTileW = 32;   // staging tiles (rows x columns)
@@ -94,21 +99,22 @@ struct ClipArgs {
   const float* mlp_norm = nullptr;
   unsigned long long* surr_stats = nullptr;   // [2]: bins settled by the surrogate, bins that fell back
   int32_t surr_passes = 1;             // verification passes before the plain fallback
+  int32_t tcap = 0;                    // tail slots per thread of the tail-replay kernel (set at launch)
+  unsigned long long* clip_stats = nullptr;   // [SEP_CLIP_STATS] counters of the tail replay, or null
 };
 
 struct StageArgs {         // correction + staging of a batch (k_stage)
   const void* frames;      // contiguous [n_frames][npix], or
   const uint64_t* fptr;    // per frame address (mixed batches), may be null
-  int64_t npix, npos;
+  int64_t npix, npos;      // npos: the staged row stride (slots, >= nnz)
   int32_t rows, cols, tiles_x, tiles_y;
   int32_t n_frames, frames_per_cta;
   const float* ped;        // [3][npix] (raw input)
   const float* gain;       // [3][npix]
   const float* norm;       // [npix] or null
-  const int16_t* tile_rank;
-  const int32_t* tile_base;
-  float* stage;            // [n_frames][npos] (npos: the row stride)
-  int64_t nan_pos;         // the position padding entries address (set to NaN)
+  const int32_t* tile_ebase;   // [tiles + 1]
+  const int2* tile_sc;         // [nnz] (slot, pixel index in the tile or -1 for padding)
+  float* stage;            // [n_frames][npos]: value of entry e at slot e
 };
 
 struct PixArgs {           // what the consumers need to recompute a pixel value
@@ -141,6 +147,10 @@ cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, bool s
                                   int32_t precision, int mode, cudaStream_t s);
 cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaStream_t s);
 size_t clip_smem_bytes(int32_t cap, bool weighted);
+// Tail slots per thread the tail-replay clip kernel asks for (rows of `cap`
+// entries, `tpb` threads); fewer are used where shared memory runs out.
+int32_t clip_tail_slots(int32_t cap, int32_t tpb);
+constexpr int kClipStaticSmem = 2048;   // static shared memory of the clip kernels (upper bound)
 cudaError_t launch_thresholds(const float* mean, const float* sigma, float k_pick, int64_t n, float* thr,
                               cudaStream_t s);
 // Kept-pixel bitmap with each pixel's threshold taken from the profile
@@ -209,6 +219,8 @@ struct sep_ctx {
   int64_t* h_desc = nullptr;   // its pinned staging copy
   size_t desc_len = 0;
   unsigned long long* d_surr = nullptr;   // surrogate counters: settled, fell back
+  unsigned long long* d_clip_stats = nullptr;   // [SEP_CLIP_STATS] tail-replay counters
+  bool clip_stats_on = false;                   // clip launches count into d_clip_stats
   float* d_stage = nullptr;    // staged pixel values of the batch in flight
   size_t stage_len = 0;
   // host pipeline (sep_process_host): chunk slots of frames + outputs
@@ -250,9 +262,9 @@ struct sep_csr {
   float* d_norm = nullptr;
   int32_t* d_bop = nullptr;
   int32_t* d_grp = nullptr;
-  int32_t* d_pos_of = nullptr;
-  int16_t* d_tile_rank = nullptr;
-  int32_t* d_tile_base = nullptr;
+  int32_t* d_pos_of = nullptr;        // slot of each pixel's centre entry in a staged row, -1 if none
+  int32_t* d_tile_ebase = nullptr;
+  int2* d_tile_sc = nullptr;
   const sep_model* model = nullptr;   // surrogate attached by sep_csr_attach_model
 };
 
