@@ -474,27 +474,36 @@ def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / steps
 
+    def scans_per_item():
+        # core scans (passes over the whole row) per bin and frame, one step
+        sep.clip_stats(enable=1, read=False, reset=True, stream=stream)
+        sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)
+        st = sep.clip_stats(enable=0, read=True, reset=True, stream=stream)
+        return round((st["core_scans"] + st["full_passes"]) / max(st["items"], 1), 4)
+
     sep.attach_surrogate(None)
     timed(2)
     plain_ms = timed(args.steps)
-    plain = {k: out[k].clone() for k in ("idx", "n_kept", "count")}
+    plain = {k: out[k].clone() for k in ("idx", "n_kept", "count", "mean", "sigma")}
     res = {"train_frames": args.surrogate_train_frames, "train_rows": rows, "train_loss": round(loss, 5),
-           "train_s": round(t_train, 1), "plain_fps": round(F / (plain_ms * 1e-3), 2)}
-    for passes in (1, 2):
-        sep.attach_surrogate(model, passes=passes)
-        timed(2)
-        sep.surrogate_stats(reset=True, stream=stream)
-        ms = timed(args.steps)
-        acc, fb = sep.surrogate_stats(reset=True, stream=stream)
-        same = 0
-        for f in range(F):
-            n = int(plain["n_kept"][f])
-            if int(out["n_kept"][f]) == n and torch.equal(out["idx"][f, :n], plain["idx"][f, :n]):
-                same += 1
-        res[f"passes{passes}"] = {
-            "fps": round(F / (ms * 1e-3), 2), "settled_frac": round(acc / max(acc + fb, 1), 4),
-            "bins_same_count_frac": round(float((out["count"] == plain["count"]).float().mean().item()), 4),
-            "frames_identical_kept": round(same / F, 4)}
+           "train_s": round(t_train, 1), "plain_fps": round(F / (plain_ms * 1e-3), 2),
+           "plain_row_scans_per_bin": scans_per_item()}
+    sep.attach_surrogate(model)
+    timed(2)
+    sep.surrogate_stats(reset=True, stream=stream)
+    ms = timed(args.steps)
+    acc, fb = sep.surrogate_stats(reset=True, stream=stream)
+    same = 0
+    for f in range(F):
+        n = int(plain["n_kept"][f])
+        if int(out["n_kept"][f]) == n and torch.equal(out["idx"][f, :n], plain["idx"][f, :n]):
+            same += 1
+    res["surrogate"] = {
+        "fps": round(F / (ms * 1e-3), 2), "speedup_vs_plain": round(plain_ms / ms, 4),
+        "predicted_core_held_frac": round(acc / max(acc + fb, 1), 4),
+        "row_scans_per_bin": scans_per_item(),
+        "bins_same_count_frac": round(float((out["count"] == plain["count"]).float().mean().item()), 4),
+        "frames_identical_kept": round(same / F, 4)}
     sep.attach_surrogate(None)
     model.close()
     return res

@@ -117,10 +117,12 @@ typedef struct {
   int32_t patch;             /* peak patch side, odd, 1 .. 15 (Section 4) */
   int32_t min_count;         /* minimum kept pixels in the patch, >= 1 */
   int32_t precision;         /* SEP_PREC_* */
-  int32_t surrogate;         /* 0: plain clip loop. n in 1 .. 8: start from the
-                                prediction of the model attached to the CSR
-                                (sep_csr_attach_model) and verify it in at most n
-                                passes, else run the plain loop for that bin;
+  int32_t surrogate;         /* 0: the first core of the clip kernel's replay is
+                                placed from the first pass's moments; 1 .. 8:
+                                from the prediction of the model attached to
+                                the CSR (sep_csr_attach_model). The results are
+                                those of the plain loop either way (the model
+                                only changes how much of the row is replayed);
                                 needs precision SEP_PREC_DWORD */
   int32_t cutoff;            /* SEP_CUTOFF_FIXED: every step clips at k_clip;
                                 SEP_CUTOFF_CHAUVENET: the cut-off of each step is
@@ -207,12 +209,14 @@ void sep_csr_destroy(sep_csr* csr);
 /* Sizes: pixels, bins, nonzeros, largest row; range[2] as used. Any out pointer may be NULL. */
 sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64_t* nnz,
                         int32_t* max_row, double* range);
-/* Staging order: every pixel with at least one matrix entry has a staging
- * position (its corrected value is written there once per frame and the
- * integration reads it from there). Pixels are grouped by tiles of 32 rows x
- * 32 columns (tiles in row-major order); inside a tile, by centre bin, then
- * radius of the pixel centre, then pixel index. perm_inv [npos] receives the
- * pixel of each position (may be NULL); *npos the number of positions. */
+/* Staging order: the order of the pixels with at least one matrix entry that
+ * sorts the entries inside each coefficient group of a row (so one staging
+ * tile writes consecutive slots of a bin's row). Pixels are grouped by tiles
+ * of 32 rows x 32 columns (tiles in row-major order); inside a tile, by
+ * centre bin, then radius of the pixel centre, then pixel index. perm_inv
+ * [npos] receives the pixel of each position (may be NULL); *npos the number
+ * of positions. (A frame's staged copy holds one value per matrix entry, in
+ * row order: entry e's corrected pixel value at slot e.) */
 sep_status sep_csr_staging(const sep_csr* csr, int32_t* perm_inv, int64_t* npos);
 /* Interpolation table of the smooth background (Section 3; densification
  * and the consumers with interpolate): per pixel, the lower bin a [npix]
@@ -415,9 +419,15 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
 /* ---- learned surrogate of the clip iteration ------------------------------ */
 /*
  * A small network (no counterpart in the paper) predicts a bin's clipped mean
- * and deviation from its first-pass statistics, so the clip loop can start
- * from the prediction and stop once verified; the plain loop remains the
- * fallback. Network: SEP_MLP_IN features -> 64 -> GELU -> 64 -> GELU -> 2,
+ * and deviation, i.e. its final clip interval, from statistics of a sample of
+ * its entries. The clip kernel replays the loop of Eq. 19 exactly on the sums
+ * of a core interval that lies inside every interval the loop visits, plus
+ * the entries outside it; the prediction places that core (half a predicted
+ * deviation inside the predicted final interval), so a good prediction spares
+ * the re-placements and rescans of the row that the plain placement (inside
+ * the first interval) needs, and a poor one costs a rescan. The loop itself,
+ * and so every result, is the plain method's: the plain loop judges every
+ * step. Network: SEP_MLP_IN features -> 64 -> GELU -> 64 -> GELU -> 2,
  * GELU exact (x Phi(x)), weights stored BF16 for every forward / backward,
  * FP32 master copy and FP32 accumulation. Parameter layout (floats):
  * W1 [64][20], b1 [64], W2 [64][64], b2 [64], W3 [2][64], b3 [2].
@@ -458,16 +468,13 @@ sep_status sep_surrogate_train(sep_model* model, const float* x_dev, const float
                                const sep_train_cfg* cfg, float* final_loss, sep_stream stream);
 /* Attach a model to a CSR (NULL detaches). The CSR keeps the pointer, not a
  * copy: the model must outlive its use, and later training of the model is
- * seen by later launches. Calls with params->surrogate > 0 then start each
- * bin from the model's prediction: with the first-pass mean m1 and deviation
- * s1 of the bin, mu^ = m1 + s1 y0, sd^ = s1 exp(y1) (y de-normalised by the
- * target block), candidate set I = {|v - mu^| <= k sd^}; one pass measures I
- * and accepts it iff I is a fixed point of the clip map of Eq. 19, i.e.
- * {|v - mu_I| <= k sd_I} == I; otherwise the next candidate is that set, up
- * to params->surrogate passes, then the plain loop (bit-identical to a call
- * without the surrogate). A bin settled by the surrogate reports -1
- * iterations (iters_dev); bins that the first pass settles alone skip the
- * surrogate. */
+ * seen by later launches. Calls with params->surrogate > 0 then place each
+ * bin's first core from the model's prediction: with the sample mean m1 and
+ * deviation s1 of the bin (the features below), mu^ = m1 + s1 y0 and sd^ =
+ * s1 exp(y1) (y de-normalised by the target block); the core is
+ * [mu^ - k sd^ + sd^ / 2, mu^ + k sd^ - sd^ / 2]. Every result (mean, sigma,
+ * count, bounds, iterations, kept pixels) is the plain loop's, whatever the
+ * prediction; the sums may be taken in another order. */
 sep_status sep_csr_attach_model(sep_csr* csr, const sep_model* model);
 
 /* The whole path from host memory to host memory, pipelined: the batch is
@@ -503,11 +510,15 @@ sep_status sep_correct(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
  * bin, the surrogate's input features feat_dev [n_frames][nbins][SEP_MLP_IN]
  * and its training targets target_dev [n_frames][nbins][2] =
  * ((mu - m1) / s1, log(sd / s1)) of the clipped result (NaN where the bin has
- * fewer than 2 entries in the final set or a zero deviation); m1 and s1 are
- * the mean and deviation (Eqs. 12-13) of the full set. Features:
- * 0 log(n) / 8 (n entries of weight != 0), 1 Omega / n, 2 clamp(m1 / s1, -20,
- * 20) / 4, 3 fraction with z = (v - m1) / s1 > 4, 4 .. 19 the quantiles
- * (j + 1/2) / 16 of z from a 64-bin histogram over [-4, 12). */
+ * fewer than 2 entries in the final set, a zero deviation, or s1 = 0).
+ * The features are taken on a sample of the bin's row: every step-th group
+ * of 4 consecutive entries of each coefficient class (step 4 for rows of
+ * 2048 entries or more, 2 from 512, else 1); m1 and s1 are the sample's mean
+ * and deviation (Eqs. 12-13, FP32). Features: 0 log(step n) / 8 (n: the
+ * sample's finite entries of weight != 0), 1 Omega / n over the sample,
+ * 2 clamp(m1 / s1, -20, 20) / 4, 3 the sample's fraction with
+ * z = (v - m1) / s1 >= 4, 4 .. 19 the quantiles (j + 1/2) / 16 of the
+ * sample's z, read linearly inside a 64-bin histogram over [-4, 12). */
 sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                                 int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                                 float* sigma_dev, int32_t* count_dev, float* feat_dev, float* target_dev,
@@ -522,9 +533,10 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
 sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const float* target_dev, int64_t n,
                                  float* x_dev, float* t_dev, float* norm_host, int64_t* n_valid, sep_stream stream);
 
-/* Of the bins the surrogate ran on: how many it settled and how many fell
- * back to the plain loop, summed over every call since the last reset.
- * Synchronises. */
+/* Of the bins the surrogate placed: how many kept the predicted core to the
+ * end of their loop (accepted) and how many had to re-place it inside a later
+ * interval and rescan the row (fell_back), summed over every call since the
+ * last reset. Synchronises. */
 sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
                                sep_stream stream);
 

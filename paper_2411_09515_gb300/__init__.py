@@ -119,12 +119,13 @@ class Separator:
             setattr(self.params, k, v)
 
     # ---- learned surrogate of the clip loop ----
-    def attach_surrogate(self, model: "Surrogate | None", passes: int = 1):
-        """Start every bin's clip from the model's prediction, verified in at
-        most ``passes`` passes (plain loop where that fails); None detaches."""
+    def attach_surrogate(self, model: "Surrogate | None"):
+        """Place every bin's first replay core from the model's prediction of
+        its final clip interval (the results stay the plain loop's); None
+        detaches."""
         B.sep_csr_attach_model(self.ctx, self.csr, model.model if model is not None else None)
         self.surrogate = model
-        self.params.surrogate = passes if model is not None else 0
+        self.params.surrogate = 1 if model is not None else 0
 
     def record(self, frames, stream=None):
         """Plain clip that also returns the surrogate's features [F][B][20]

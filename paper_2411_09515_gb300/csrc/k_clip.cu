@@ -1,39 +1,35 @@
 // Integration + sigma-clipping over staged pixel values.
 //
-// One CTA (64, 128 or 256 threads: a tuning choice per size class of bins)
-// owns one radial bin (a row of the integration matrix) and walks a group of
-// frames. Per frame it gathers the bin's values from the frame's staged copy
-// (k_stage.cu: corrected pixels, Section 1.2, in an order where each bin
-// reads short contiguous runs) and keeps them in shared memory; every
-// clipping pass (Eq. 19, Section 2.4) then runs on chip.
+// One warp owns one radial bin (a row of the integration matrix) of one
+// frame: it reads the bin's values from the frame's staged copy (k_stage.cu:
+// corrected pixels, Section 1.2, one slot per matrix entry, so a bin's
+// values are one contiguous run), accumulates the weighted moments
+// (Eqs. 8-13) and runs the clip loop of Eq. 19 (Section 2.4) by tail replay
+// (described with the kernel below). The warps of a CTA take other frames
+// of the same bin and never synchronise.
 //
-// Moments (Eqs. 8-13) are accumulated about a shift K: with d = v - K, per
-// set S
+// Moments are accumulated about a shift K: with d = v - K, per set S
 //   Omega = sum w, A1 = sum w d, OO = sum w^2, B1 = sum w^2 d, B2 = sum w^2 d^2,
 //   mu = K + A1 / Omega,  VV = B2 - 2 (mu - K) B1 + (mu - K)^2 OO  (Eq. 11),
 //   sigma = sqrt(VV / OO)  (Eq. 13),
-// which is exact algebra; with K close to mu the correction terms are small,
-// so one pass per moment evaluation suffices. The first pass takes the full
-// set about 0 and is kept whenever that shift is adequate (|mu| <= 2 sigma).
+// which is exact algebra; with K close to mu (or 0 where |mu| <= 2 sigma)
+// the correction terms are small.
 //
 // Rejection is cumulative and symmetric about the current mean, so the set
 // after t steps is every entry whose value lies in an interval [L_t, H_t]:
-// no per-entry flag is kept. Row entries
-// are grouped by coefficient class (a group shares one weight), so per-entry
-// work is unweighted and the class weight is applied once per thread per
-// pass.
+// no per-entry flag is kept. Row entries are grouped by coefficient class (a
+// group shares one weight), so per-entry work is unweighted and the class
+// weight is applied once per lane and class.
 //
 // After the last evaluation the kernel writes mu + k_pick sigma, the bin's
 // sparsification threshold (Section 3); with a bitmap it also marks the
 // bin's kept pixels (its centre entries above the threshold).
 //
-// Precision (SEP_PREC_*): per-thread FP32 sums (Kahan-compensated in KAHAN)
-// and FP32 warp shuffles (error-free pairs in KAHAN). The cross-warp merge,
-// the variance finalisation and the clip bounds run on one warp only: FP64
-// in FP64MERGE, error-free FP32 pairs ("double-word") in DWORD and KAHAN,
-// plain FP32 in PLAIN. FP64 runs at a small fraction of the FP32 rate on this
-// GPU and sits on the serial path of every pass, so DWORD, which issues no
-// FP64 instruction, is the default.
+// Precision (SEP_PREC_*): per-lane FP32 sums (Kahan-compensated in KAHAN);
+// the merge over the lanes and the finalisation in plain FP32 (PLAIN),
+// error-free FP32 pairs ("double-word": KAHAN and DWORD, the default) or
+// FP64 (FP64MERGE). FP64 runs at a small fraction of the FP32 rate on this
+// GPU, so DWORD issues no FP64 instruction.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -195,227 +191,19 @@ __device__ __forceinline__ float pick_threshold(const Bcast& st, float k) {
   return round_dn_pair(th, tl);
 }
 
-// Sum NF float and NI integer per-thread values over the CTA. On return,
-// lane v of warp 0 holds float total v (v < NF) and lane NF + i integer
-// total i, as doubles. Integers go through one redux per warp. Ends without
-// a barrier: the caller's warp 0 works on the totals and then synchronises.
-template <int NF, int NI, int PREC, int kWarps>
-__device__ __forceinline__ void block_sum(float (&s)[NF], float (&c)[NF], uint32_t (&iv)[NI], float (*red_s)[kWarps],
-                                          float (*red_c)[kWarps], uint32_t (*red_i)[kWarps], float& thi,
-                                          float& tlo) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < NF; ++v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (PREC == SEP_PREC_KAHAN) {
-        const float so = __shfl_xor_sync(0xffffffffu, s[v], o);
-        const float co = __shfl_xor_sync(0xffffffffu, c[v], o);
-        pair_add(s[v], c[v], so, co);
-      } else {
-        s[v] = __fadd_rn(s[v], __shfl_xor_sync(0xffffffffu, s[v], o));
-      }
-    }
-  }
-  uint32_t wi[NI];
-#pragma unroll
-  for (int i = 0; i < NI; ++i) wi[i] = __reduce_add_sync(0xffffffffu, iv[i]);
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < NF; ++v) {
-      red_s[v][warp] = s[v];
-      if (PREC == SEP_PREC_KAHAN) red_c[v][warp] = c[v];
-    }
-#pragma unroll
-    for (int i = 0; i < NI; ++i) red_i[i][warp] = wi[i];
-  }
-  __syncthreads();
-  thi = 0.0f;
-  tlo = 0.0f;
-  if (warp == 0 && lane < NF) {
-    if (PREC == SEP_PREC_FP64MERGE) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) t += (double)red_s[lane][w];
-      thi = (float)t;
-      tlo = (float)(t - (double)thi);
-    } else if (PREC == SEP_PREC_PLAIN) {
-      float x = red_s[lane][0];
-#pragma unroll
-      for (int w = 1; w < kWarps; ++w) x = __fadd_rn(x, red_s[lane][w]);
-      thi = x;
-    } else {   // error-free pairs (value = hs - hc)
-      float hs = red_s[lane][0], hc = PREC == SEP_PREC_KAHAN ? red_c[lane][0] : 0.0f;
-#pragma unroll
-      for (int w = 1; w < kWarps; ++w)
-        pair_add(hs, hc, red_s[lane][w], PREC == SEP_PREC_KAHAN ? red_c[lane][w] : 0.0f);
-      two_sum(hs, -hc, thi, tlo);
-    }
-  } else if (warp == 0 && lane < NF + NI) {
-    uint32_t x = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) x += red_i[lane - NF][w];
-    thi = __uint_as_float(x);   // integer totals travel as raw bits (packed counts exceed 2^24)
-  }
-}
-
 template <int MODE>
 struct Sums {
   // per pass, float sums and integer counts:
   //   MODE_UNIT:  (S1, S2) + count
   //   MODE_CLASS: (A1, B1, B2) + class counts packed 16 + 16 bits in two words
   //   MODE_ENTRY: (Omega, A1, OO, B1, B2) + count
-  // (a row holds fewer than 2^16 entries: its values must fit shared memory)
+  // (a row holds fewer than 2^16 entries: the host refuses longer rows; tail
+  // slots keep an entry's index in 16 bits)
   static constexpr int NF = MODE == MODE_UNIT ? 2 : (MODE == MODE_CLASS ? 3 : 5);
   static constexpr int NI = MODE == MODE_CLASS ? 2 : 1;
 };
 
-// Extremes around an interval [Ln, Hn] over the entries of weight != 0:
-// x[0] = max below Ln, x[1] = min inside, x[2] = max inside, x[3] = min above Hn.
-// EXT 1 tracks the two inside the interval only, EXT 2 all four.
-template <int EXT>
-struct Ext {
-  float x[4] = {-INFINITY, INFINITY, -INFINITY, INFINITY};
-  __device__ __forceinline__ void add(float v, float Ln, float Hn) {
-    if (EXT == 1) {
-      if (v >= Ln && v <= Hn) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
-    } else if (EXT == 2) {
-      if (v < Ln) x[0] = fmaxf(x[0], v);
-      else if (v > Hn) x[3] = fminf(x[3], v);
-      else if (v == v) { x[1] = fminf(x[1], v); x[2] = fmaxf(x[2], v); }
-    }
-  }
-};
-
-// One pass: shifted sums about Kf over the entries of weight != 0 whose value
-// lies in [Ln, Hn], and the extremes around the interval (Ext).
-// (tid: the thread's index among the kThreads that share the row)
-template <int MODE, bool KAHAN, int EXT, int kThreads>
-__device__ __forceinline__ void pass_sums(const float4* vals4, const float* wts, const int (&ge)[4], float Ln,
-                                          float Hn, float Kf, Ext<EXT>& ex, float (&ss)[Sums<MODE>::NF],
-                                          float (&cc)[Sums<MODE>::NF], uint32_t (&ci)[Sums<MODE>::NI],
-                                          int tid = threadIdx.x) {
-  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
-#pragma unroll
-  for (int v = 0; v < NF; ++v) ss[v] = cc[v] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < NI; ++i) ci[i] = 0u;
-  if (MODE == MODE_CLASS) {
-    int lo = 0;
-#pragma unroll
-    for (int cls = 0; cls < 4; ++cls) {
-      const int hi = ge[cls];
-      const float w = 1.0f - 0.25f * (float)cls, w2 = w * w;
-      uint32_t cnt = 0;
-      Acc<KAHAN> a1, a2;
-      for (int q = (lo >> 2) + tid; q < (hi >> 2); q += kThreads) {
-        const float4 v4 = vals4[q];
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (EXT) ex.add(xs[j], Ln, Hn);
-          if (xs[j] >= Ln && xs[j] <= Hn) {
-            const float d = __fsub_rn(xs[j], Kf);
-            ++cnt;
-            a1.add(d);
-            a2.add_prod(d, d);
-          }
-        }
-      }
-      const float s1 = a1.val(), s2 = a2.val();
-      ci[cls >> 1] += cnt << (16 * (cls & 1));
-      if (KAHAN) {
-        Acc<true> t0, t1, t2;
-        t0.s = ss[0]; t0.c = cc[0]; t0.add(__fmul_rn(w, s1)); ss[0] = t0.s; cc[0] = t0.c;
-        t1.s = ss[1]; t1.c = cc[1]; t1.add(__fmul_rn(w2, s1)); ss[1] = t1.s; cc[1] = t1.c;
-        t2.s = ss[2]; t2.c = cc[2]; t2.add(__fmul_rn(w2, s2)); ss[2] = t2.s; cc[2] = t2.c;
-      } else {
-        ss[0] = fmaf(w, s1, ss[0]);
-        ss[1] = fmaf(w2, s1, ss[1]);
-        ss[2] = fmaf(w2, s2, ss[2]);
-      }
-      lo = hi;
-    }
-  } else if (MODE == MODE_UNIT) {
-    uint32_t cnt = 0;
-    Acc<KAHAN> a1, a2;
-    for (int q = tid; q < (ge[0] >> 2); q += kThreads) {
-      const float4 v4 = vals4[q];
-      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (EXT) ex.add(xs[j], Ln, Hn);
-        if (xs[j] >= Ln && xs[j] <= Hn) {
-          const float d = __fsub_rn(xs[j], Kf);
-          ++cnt;
-          a1.add(d);
-          a2.add_prod(d, d);
-        }
-      }
-    }
-    ci[0] = cnt;
-    ss[0] = a1.s; cc[0] = a1.c; ss[1] = a2.s; cc[1] = a2.c;
-  } else {
-    uint32_t cnt = 0;
-    Acc<KAHAN> om, a1, oo, b1, b2;
-    for (int q = tid; q < (ge[3] >> 2); q += kThreads) {
-      const float4 v4 = vals4[q];
-      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float w = wts[4 * q + j];
-        if (EXT && w != 0.0f) ex.add(xs[j], Ln, Hn);
-        if (w != 0.0f && xs[j] >= Ln && xs[j] <= Hn) {
-          const float d = __fsub_rn(xs[j], Kf);
-          const float w2 = __fmul_rn(w, w);
-          const float w2d = __fmul_rn(w2, d);
-          ++cnt;
-          om.add(w);
-          a1.add(__fmul_rn(w, d));
-          oo.add(w2);
-          b1.add(w2d);
-          b2.add_prod(w2d, d);
-        }
-      }
-    }
-    ci[0] = cnt;
-    ss[0] = om.s; cc[0] = om.c; ss[1] = a1.s; cc[1] = a1.c; ss[2] = oo.s; cc[2] = oo.c;
-    ss[3] = b1.s; cc[3] = b1.c; ss[4] = b2.s; cc[4] = b2.c;
-  }
-}
-
-// Warp reduction of the extremes, one row per warp in red_x (read after the
-// barrier inside the following block_sum).
-template <int EXT, int kWarps>
-__device__ __forceinline__ void warp_ext(Ext<EXT>& ex, float (*red_x)[kWarps]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    if (EXT == 2) ex.x[0] = fmaxf(ex.x[0], __shfl_xor_sync(0xffffffffu, ex.x[0], o));
-    ex.x[1] = fminf(ex.x[1], __shfl_xor_sync(0xffffffffu, ex.x[1], o));
-    ex.x[2] = fmaxf(ex.x[2], __shfl_xor_sync(0xffffffffu, ex.x[2], o));
-    if (EXT == 2) ex.x[3] = fminf(ex.x[3], __shfl_xor_sync(0xffffffffu, ex.x[3], o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if (EXT == 2 || v == 1 || v == 2) red_x[v][threadIdx.x >> 5] = ex.x[v];
-  }
-}
-
-// Lane 0 of warp 0: the extremes over the CTA (EXT 1: the two inside only).
-template <int EXT, int kWarps>
-__device__ __forceinline__ void cta_ext(const float (*red_x)[kWarps], float (&e)[4]) {
-  e[0] = -INFINITY; e[1] = INFINITY; e[2] = -INFINITY; e[3] = INFINITY;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    if (EXT == 2) e[0] = fmaxf(e[0], red_x[0][w]);
-    e[1] = fminf(e[1], red_x[1][w]);
-    e[2] = fmaxf(e[2], red_x[2][w]);
-    if (EXT == 2) e[3] = fminf(e[3], red_x[3][w]);
-  }
-}
-
-// One step of the clip loop (lane 0 of warp 0) after a pass measured the set
+// One step of the clip loop (every lane of the warp, on identical totals) after a pass measured the set
 // S' = S ∩ [Ln, Hn] (count n_set, sums h/l about Kf). S' == S means nothing
 // was discarded: the loop ends with the moments of S. Otherwise S' becomes
 // the set, its moments are evaluated and the next interval is the
@@ -522,368 +310,6 @@ __device__ __forceinline__ void unpack_totals(const float* th, const float* tl, 
 #pragma unroll
     for (int v = 0; v < 5; ++v) { h[v] = th[v]; l[v] = tl[v]; }
   }
-}
-
-// Surrogate scratch in shared memory (per CTA).
-struct SurrShared {
-  uint32_t hist[64];     // z-histogram of the first-pass set, bins of 0.25 over [-4, 12)
-  float feat[kIn];       // the 20 features
-  float xn[kIn];         // normalised features
-  float h1[kH], h2[kH];  // hidden activations
-  float m1, s1, om, n;   // first-pass weighted mean, deviation, weight and count
-  int accepted;
-};
-
-// Kept-pixel marks issued ahead by the clip kernel (see its frame loop).
-constexpr int kMarkAhead = 4;
-__device__ __forceinline__ void mark_flush(uint32_t* bm, const int32_t (&px)[kMarkAhead]) {
-#pragma unroll
-  for (int k = 0; k < kMarkAhead; ++k)
-    if (px[k] >= 0) atomicOr(bm + (px[k] >> 5), 1u << (px[k] & 31));
-}
-
-// Registers are capped so that 1024 threads stay resident per SM (the
-// serial step of one CTA overlaps the passes of the others).
-template <int MODE, int PREC, int kThreads, int SURR>
-__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_integrate_clip(ClipArgs a) {
-  constexpr int kWarps = kThreads / 32;
-  constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
-  constexpr int NF = Sums<MODE>::NF, NI = Sums<MODE>::NI;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* vals = reinterpret_cast<float*>(smem_raw);
-  float* wts = vals + a.cap;   // MODE_ENTRY only: per-entry weight
-  __shared__ float red_s[NF][kWarps], red_c[NF][kWarps];
-  __shared__ uint32_t red_i[NI][kWarps];
-  __shared__ float red_x[4][kWarps];
-  __shared__ Bcast st, st0;   // st0: the state after the first pass (surrogate fallback)
-  __shared__ SurrShared sv;
-  (void)sv;
-  (void)st0;
-
-  const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
-  const int f0 = blockIdx.y * a.frames_per_cta;
-  const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
-  const int r0 = __ldg(a.rowptr + b);
-  const int n = __ldg(a.rowptr + b + 1) - r0;      // multiple of 4
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int ge[4];   // end of coefficient class 0..3 in the row; weight-0 carriers follow
-#pragma unroll
-  for (int c = 0; c < 4; ++c) ge[c] = __ldg(a.grp + 4 * b + c);
-  float4* vals4 = reinterpret_cast<float4*>(vals);
-  const int nq = n >> 2;
-
-  if (MODE == MODE_ENTRY) {
-    for (int e = tid; e < n; e += kThreads) {
-      const uint32_t u = __ldg(a.ent + r0 + e);
-      wts[e] = (u & (kZero | kPad)) ? 0.0f : __ldg(a.w + r0 + e);
-    }
-  }
-
-  // Kept-pixel marks of the previous frame still to be written: the pixel
-  // loads of its first kMarkAhead kept centre entries are issued at the end
-  // of that frame and consumed after the next frame's entry copy, so their
-  // latency hides behind it (a pixel of -1: nothing to mark).
-  uint32_t* mk_bm = nullptr;
-  int32_t mk_px[kMarkAhead];
-#pragma unroll
-  for (int k = 0; k < kMarkAhead; ++k) mk_px[k] = -1;
-  for (int f = f0; f < f1; ++f) {
-    const float* vf = a.stage + (int64_t)f * a.npos;   // this frame's staged values
-    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
-    if (SURR != 0 && tid < 64) sv.hist[tid] = 0u;
-    // ------------- gather, then the first pass (full set, shift 0) -------------
-    float ss0[NF], cc0[NF];
-    uint32_t ci0[NI];
-    Ext<0> ex0;
-    {
-      // the row's values are contiguous in the staged frame (slot = entry):
-      // 16-byte copies into shared memory (padding slots hold NaN)
-      const unsigned sb = (unsigned)__cvta_generic_to_shared(vals);
-      const float4* src4 = reinterpret_cast<const float4*>(vf + r0);
-      for (int q = tid; q < nq; q += kThreads)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + 16u * (unsigned)q), "l"(src4 + q)
-                     : "memory");
-      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-      if (mk_bm) mark_flush(mk_bm, mk_px);   // the previous frame's marks
-      mk_bm = nullptr;
-      __syncthreads();
-      pass_sums<MODE, KAHAN, 0, kThreads>(vals4, wts, ge, -FLT_MAX, FLT_MAX, 0.0f, ex0, ss0, cc0, ci0);
-    }
-    {
-      float thi, tlo;
-      block_sum<NF, NI, PREC, kWarps>(ss0, cc0, ci0, red_s, red_c, red_i, thi, tlo);
-      if (warp == 0) {
-        float th[NF + NI], tl[NF + NI];
-#pragma unroll
-        for (int v = 0; v < NF + NI; ++v) {
-          th[v] = __shfl_sync(0xffffffffu, thi, v);
-          tl[v] = __shfl_sync(0xffffffffu, tlo, v);
-        }
-        if (lane == 0) {
-          float n_set, h[6], l[6];
-          unpack_totals<MODE>(th, tl, n_set, h, l);
-          st.Ln = -FLT_MAX;
-          st.Hn = FLT_MAX;
-          st.L = -FLT_MAX;
-          st.H = FLT_MAX;
-          st.n_cur = -1.0f;
-          st.steps = -1;
-          st.done = 0;
-          // moments of the full set about 0
-          finalise<PREC>(0.0f, h, l, st);
-          if (SURR != 0) {
-            sv.m1 = st.mu_hi;
-            sv.s1 = st.sd;
-            sv.om = __fadd_rn(h[0], l[0]);
-            sv.n = n_set;
-            sv.accepted = 0;
-          }
-          if (choose_shift(st.mu_hi, st.sd) == 0.0f) {
-            // the shift 0 suits this set: this was the first pass
-            clip_step<PREC>(st, n_set, h, l, 0.0f, -FLT_MAX, FLT_MAX, a.n_iter, a.k_clip, true, a.cutoff,
-                            a.error_model, a.dark_var);
-          } else {
-            // cancellation about 0 is too large: the first pass runs again about the mean
-            st.Kf = st.mu_hi;
-          }
-          if (SURR == 2) st0 = st;
-        }
-      }
-      __syncthreads();   // values and state visible to all
-    }
-
-    if (SURR == 1 || (SURR == 2 && !st.done)) {
-      // ------------- surrogate features: first-pass statistics + z quantiles -------------
-      const float m1 = sv.m1, inv = sv.s1 > 0.0f ? 1.0f / sv.s1 : 0.0f;
-      const int zend = MODE == MODE_UNIT ? ge[0] : ge[3];
-      for (int q = tid; q < (zend >> 2); q += kThreads) {
-        const float4 v4 = vals4[q];
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (!(xs[j] >= -FLT_MAX && xs[j] <= FLT_MAX)) continue;
-          if (MODE == MODE_ENTRY && wts[4 * q + j] == 0.0f) continue;
-          const float zb = fminf(fmaxf(__fmul_rn(__fsub_rn(xs[j], m1), inv) * 4.0f + 16.0f, 0.0f), 63.0f);
-          atomicAdd(&sv.hist[(int)zb], 1u);
-        }
-      }
-      __syncthreads();
-      if (warp == 0) {
-        float tot = 0.0f;
-#pragma unroll 4
-        for (int hb = 0; hb < 64; ++hb) tot += (float)sv.hist[hb];
-        if (lane < 16) {
-          // quantile (lane + 1/2) / 16 of z, linear inside its histogram bin
-          const float target = ((float)lane + 0.5f) * (1.0f / 16.0f) * tot;
-          float cum = 0.0f, zq = 12.0f;
-#pragma unroll 1
-          for (int hb = 0; hb < 64; ++hb) {
-            const float c = (float)sv.hist[hb];
-            if (c > 0.0f && cum + c >= target) {
-              zq = -4.0f + 0.25f * ((float)hb + (target - cum) / c);
-              break;
-            }
-            cum += c;
-          }
-          sv.feat[4 + lane] = tot > 0.0f ? zq : 0.0f;
-        } else if (lane == 16) {
-          float hi_tail = 0.0f;
-#pragma unroll 4
-          for (int hb = 32; hb < 64; ++hb) hi_tail += (float)sv.hist[hb];
-          const float nn = sv.n > 0.0f ? sv.n : 1.0f;
-          sv.feat[0] = logf(nn) * 0.125f;
-          sv.feat[1] = sv.om / nn;
-          sv.feat[2] = sv.s1 > 0.0f ? fminf(fmaxf(sv.m1 / sv.s1, -20.0f), 20.0f) * 0.25f : 0.0f;
-          sv.feat[3] = tot > 0.0f ? hi_tail / tot : 0.0f;
-        }
-        if (SURR == 2) {
-          __syncwarp();
-          if (lane < kIn) sv.xn[lane] = (sv.feat[lane] - a.mlp_norm[lane]) / a.mlp_norm[kIn + lane];
-        }
-      }
-      __syncthreads();
-    }
-
-    if (SURR == 2 && !st.done) {
-      // ------------- predict (fused inference) -------------
-      const __nv_bfloat16* W = a.mlp_w;
-      for (int j = tid; j < kH; j += kThreads) {
-        float acc = __bfloat162float(W[kB1 + j]);
-#pragma unroll
-        for (int k = 0; k < kIn; ++k) acc = fmaf(__bfloat162float(W[kW1 + j * kIn + k]), sv.xn[k], acc);
-        sv.h1[j] = gelu_f(acc);
-      }
-      __syncthreads();
-      for (int idx = tid; idx < 4 * kH; idx += kThreads) {
-        const int j = idx >> 2, part = idx & 3;
-        float acc = 0.0f;
-#pragma unroll
-        for (int k = 16 * part; k < 16 * part + 16; ++k) acc = fmaf(__bfloat162float(W[kW2 + j * kH + k]), sv.h1[k], acc);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (part == 0) sv.h2[j] = gelu_f(acc + __bfloat162float(W[kB2 + j]));
-      }
-      __syncthreads();
-      if (warp == 0) {
-        float y0 = __bfloat162float(W[kW3 + lane]) * sv.h2[lane] + __bfloat162float(W[kW3 + lane + 32]) * sv.h2[lane + 32];
-        float y1 = __bfloat162float(W[kW3 + kH + lane]) * sv.h2[lane] +
-                   __bfloat162float(W[kW3 + kH + lane + 32]) * sv.h2[lane + 32];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          y0 += __shfl_xor_sync(0xffffffffu, y0, off);
-          y1 += __shfl_xor_sync(0xffffffffu, y1, off);
-        }
-        if (lane == 0) {
-          const float* nm = a.mlp_norm;
-          const float u0 = (y0 + __bfloat162float(W[kB3])) * nm[2 * kIn + 2] + nm[2 * kIn];
-          const float u1 = (y1 + __bfloat162float(W[kB3 + 1])) * nm[2 * kIn + 3] + nm[2 * kIn + 1];
-          const float mh = sv.m1 + sv.s1 * u0, sh = sv.s1 * expf(fminf(u1, 20.0f));
-          // candidate set I0 = {|v - mh| <= k sh}
-          st.Ln = mh - a.k_clip * sh;
-          st.Hn = mh + a.k_clip * sh;
-          st.Kf = choose_shift(mh, sh);
-        }
-      }
-      __syncthreads();
-      // ------------- verify: one pass per candidate -------------
-      // Measure I = {v in [Ln, Hn]}: its moments give the next interval
-      // [L', H'] = mu_I -+ k sd_I (Eq. 19), and the extremes around [Ln, Hn]
-      // decide whether {v in [L', H']} == I without another pass: I is a fixed
-      // point of the clip map iff no entry lies between the two intervals.
-      for (int r = 0; r < a.surr_passes; ++r) {
-        const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
-        float ss[NF], cc[NF];
-        uint32_t ci[NI];
-        Ext<2> ex;
-        pass_sums<MODE, KAHAN, 2, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
-        warp_ext<2, kWarps>(ex, red_x);
-        float thi, tlo;
-        block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
-        if (warp == 0) {
-          float th[NF + NI], tl[NF + NI];
-#pragma unroll
-          for (int v = 0; v < NF + NI; ++v) {
-            th[v] = __shfl_sync(0xffffffffu, thi, v);
-            tl[v] = __shfl_sync(0xffffffffu, tlo, v);
-          }
-          if (lane == 0) {
-            float n_set, h[6], l[6], e[4];
-            unpack_totals<MODE>(th, tl, n_set, h, l);
-            cta_ext<2, kWarps>(red_x, e);
-            st.n_cur = n_set;
-            st.L = Ln;
-            st.H = Hn;
-            finalise<PREC>(Kf, h, l, st);
-            float L2 = -FLT_MAX, H2 = FLT_MAX;
-            clip_bounds<PREC>(st, a.k_clip, L2, H2);
-            if (n_set >= 2.0f && e[0] < L2 && L2 <= e[1] && e[2] <= H2 && H2 < e[3]) {
-              sv.accepted = 1;
-            } else {
-              st.Ln = L2;
-              st.Hn = H2;
-              st.Kf = choose_shift(st.mu_hi, st.sd);
-            }
-          }
-        }
-        __syncthreads();
-        if (sv.accepted) break;
-      }
-      if (tid == 0) {
-        if (sv.accepted) {
-          st.steps = -1;   // marks a bin settled by the surrogate
-          st.done = 1;
-        } else {
-          st = st0;        // the plain loop from its state after the first pass
-        }
-        if (a.surr_stats) atomicAdd(a.surr_stats + (sv.accepted ? 0 : 1), 1ull);
-      }
-      __syncthreads();
-    }
-
-    // ------------- the plain clip loop (Eq. 19, cumulative) -------------
-    while (!st.done) {
-      const float Ln = st.Ln, Hn = st.Hn, Kf = st.Kf;
-      float ss[NF], cc[NF];
-      uint32_t ci[NI];
-      Ext<0> ex;
-      pass_sums<MODE, KAHAN, 0, kThreads>(vals4, wts, ge, Ln, Hn, Kf, ex, ss, cc, ci);
-      float thi, tlo;
-      block_sum<NF, NI, PREC, kWarps>(ss, cc, ci, red_s, red_c, red_i, thi, tlo);
-      if (warp == 0) {
-        float th[NF + NI], tl[NF + NI];
-#pragma unroll
-        for (int v = 0; v < NF + NI; ++v) {
-          th[v] = __shfl_sync(0xffffffffu, thi, v);
-          tl[v] = __shfl_sync(0xffffffffu, tlo, v);
-        }
-        if (lane == 0) {
-          float n_set, h[6], l[6];
-          unpack_totals<MODE>(th, tl, n_set, h, l);
-          clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model,
-                          a.dark_var);
-        }
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      a.mean[o] = st.mu_hi;
-      a.sigma[o] = st.sd;
-      a.count[o] = (int32_t)st.n_cur;
-      if (a.bounds) {
-        a.bounds[2 * o] = st.L;
-        a.bounds[2 * o + 1] = st.H;
-      }
-      if (a.iters) a.iters[o] = st.steps;
-      if (SURR == 1) {
-        // training record: features and the plain result as normalised targets
-        for (int k = 0; k < kIn; ++k) a.rec_feat[o * kIn + k] = sv.feat[k];
-        const bool ok = sv.s1 > 0.0f && st.sd > 0.0f && st.n_cur >= 2.0f;
-        a.rec_target[o * 2] = ok ? (st.mu_hi - sv.m1) / sv.s1 : __int_as_float(0x7fc00000);
-        a.rec_target[o * 2 + 1] = ok ? logf(st.sd / sv.s1) : __int_as_float(0x7fc00000);
-      }
-    }
-    // threshold of sparsification (Section 3), evaluated by every thread
-    // from the final state
-    const float thr = pick_threshold<PREC>(st, a.k_pick);
-    if (a.thr_out && tid == 0) a.thr_out[o] = thr;
-    if (a.bitmap) {
-      // kept pixels of this bin: its centre entries (one per pixel whose
-      // centre bin this is) whose value exceeds the threshold; the values
-      // are still in shared memory, only kept pixels touch global memory
-      // (consecutive threads read consecutive groups: no bank conflicts;
-      // the entry's pixel is looked up only for values above the threshold)
-      uint32_t* bm = a.bitmap + (int64_t)f * a.words;
-      int np = 0;
-      int32_t g[kMarkAhead];
-#pragma unroll
-      for (int k = 0; k < kMarkAhead; ++k) g[k] = -1;
-      // (four values per load: rows are padded to multiples of 4 with NaN,
-      // never above a threshold)
-      for (int q = tid; q < nq; q += kThreads) {
-        const float4 v4 = vals4[q];
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (!(xs[j] > thr)) continue;
-          const int e = 4 * q + j;
-          if (np < kMarkAhead) {   // kept for later (a shift register: static indexing)
-#pragma unroll
-            for (int k = kMarkAhead - 1; k > 0; --k) g[k] = g[k - 1];
-            g[0] = r0 + e;
-            ++np;
-          } else {                 // beyond the look-ahead: marked now
-            const int32_t i = __ldg(a.cpix + r0 + e);
-            if (i >= 0) atomicOr(bm + (i >> 5), 1u << (i & 31));
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kMarkAhead; ++k) mk_px[k] = g[k] >= 0 ? __ldg(a.cpix + g[k]) : -1;
-      mk_bm = bm;
-    }
-    __syncthreads();   // vals and state are rewritten by the next frame
-  }
-  if (mk_bm) mark_flush(mk_bm, mk_px);
 }
 
 // ---------------------------------------------------------------------------
@@ -1001,7 +427,7 @@ __device__ __forceinline__ void warp_totals(const float (&ss)[Sums<MODE>::NF], c
 
 // Pass A (one lane's share): plain FP32 sums about 0 of the finite entries
 // of every `step`-th group of 4 (a sample of a long row: they only place
-// the core), in the layout of pass_sums.
+// the core), in the layout unpack_totals reads (per-lane values).
 template <int MODE>
 __device__ __forceinline__ void lane_full_sums(const Row& row, const float* wts, const int (&ge)[4],
                                                int lane, int step, float (&ss)[Sums<MODE>::NF],
@@ -1070,7 +496,7 @@ __device__ __forceinline__ void lane_full_sums(const Row& row, const float* wts,
 }
 
 // Pass B (one lane's share): sums about Kf of the entries inside
-// [cLo, cHi] (layout of pass_sums); every other valid entry goes to the
+// [cLo, cHi] (the layout unpack_totals reads); every other valid entry goes to the
 // lane's tail: slot k at tl[32 k] = (value bits, entry index | class <<
 // 16), written for every entry and kept only for the tail (m counts the
 // slots kept, so the branch-free store of a core entry is overwritten).
@@ -1171,8 +597,8 @@ __device__ __forceinline__ bool lane_core_sums(const Row& row, const float* wts,
   return true;
 }
 
-// One lane's share of a full pass over [Ln, Hn] about Kf (the layout of
-// pass_sums), read from the staged row.
+// One lane's share of a full pass over [Ln, Hn] about Kf (the layout
+// unpack_totals reads), read from the staged row.
 template <int MODE, bool KAHAN>
 __device__ __noinline__ void lane_range_sums(const Row& row, const float* wts, const int (&ge)[4],
                                                 int lane, float Ln, float Hn, float Kf,
@@ -1302,6 +728,125 @@ __device__ __forceinline__ void add_pair(float& h, float& l, float a, float b) {
   }
 }
 
+// ---- surrogate (no counterpart in the paper): features and inference ----
+//
+// Features of an item come from pass A's sample (every step-th group of 4
+// entries): 0 log(n) / 8 with n the sample's valid entries times step,
+// 1 Omega / n over the sample, 2 clamp(m1 / s1, -20, 20) / 4 with m1, s1 the
+// sample's mean and Eq. 13 deviation, 3 the sample's share of z = (v - m1) /
+// s1 above 4, 4 .. 19 the quantiles (j + 1/2) / 16 of z read linearly inside
+// a 64-bin histogram over [-4, 12).
+constexpr float kSurrMargin = 0.5f;   // core margin inside the predicted final interval, in deviations
+
+template <int MODE>
+__device__ __forceinline__ void sample_features(const Row& row, const float* wts, const int (&ge)[4], int lane,
+                                                int step, float n_s, float om_s, float m1, float s1,
+                                                uint32_t* hist, float (&feat)[kIn]) {
+  const float inv = s1 > 0.0f ? 1.0f / s1 : 0.0f;
+  hist[lane] = 0u;
+  hist[lane + 32] = 0u;
+  __syncwarp();
+  auto add = [&](float v) {
+    const float zb = fminf(fmaxf(__fmul_rn(__fsub_rn(v, m1), inv) * 4.0f + 16.0f, 0.0f), 63.0f);
+    atomicAdd(hist + (int)zb, 1u);
+  };
+  if (MODE == MODE_CLASS || MODE == MODE_UNIT) {
+    // the classes hold contiguous ranges: one scan of [0, ge[3]) with the
+    // same group sampling per class as pass A
+    constexpr int NCLS = MODE == MODE_CLASS ? 4 : 1;
+    int lo = 0;
+#pragma unroll 1
+    for (int cls = 0; cls < NCLS; ++cls) {
+      const int hi = ge[cls];
+      scan_row(row, lo >> 2, hi >> 2, lane, [&](const float4& v4, int) {
+        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (fabsf(xs[j]) <= FLT_MAX) add(xs[j]);
+      }, step);
+      lo = hi;
+    }
+  } else {
+    scan_row(row, 0, ge[3] >> 2, lane, [&](const float4& v4, int q) {
+      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (wts[4 * q + j] != 0.0f && fabsf(xs[j]) <= FLT_MAX) add(xs[j]);
+    }, step);
+  }
+  __syncwarp();
+  // cumulative counts: lane l holds bins 2l and 2l + 1
+  const uint32_t c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
+  uint32_t incl = c0 + c1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t upper = tot - __shfl_sync(0xffffffffu, incl, 15);   // bins 32 .. 63: z >= 4
+  __syncwarp();
+  hist[2 * lane] = incl - c1;   // cumulative through bin 2l
+  hist[2 * lane + 1] = incl;
+  __syncwarp();
+  float zq = 0.0f;
+  if (lane < 16 && tot > 0u) {
+    // quantile (lane + 1/2) / 16: the first bin whose cumulative count reaches it
+    const float target = ((float)lane + 0.5f) * (1.0f / 16.0f) * (float)tot;
+    int lo = 0, hi = 63;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((float)hist[mid] >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    const float before = lo > 0 ? (float)hist[lo - 1] : 0.0f;
+    const float c = (float)hist[lo] - before;
+    zq = -4.0f + 0.25f * ((float)lo + (c > 0.0f ? (target - before) / c : 0.0f));
+  }
+  const float n_est = n_s * (float)step;
+  feat[0] = n_est > 0.0f ? logf(n_est) * 0.125f : 0.0f;
+  feat[1] = n_s > 0.0f ? om_s / n_s : 0.0f;
+  feat[2] = s1 > 0.0f ? fminf(fmaxf(m1 / s1, -20.0f), 20.0f) * 0.25f : 0.0f;
+  feat[3] = tot > 0u ? (float)upper / (float)tot : 0.0f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) feat[4 + j] = __shfl_sync(0xffffffffu, zq, j);
+}
+
+// The network on one warp (weights BF16 with W1 and W2 input-major, FP32
+// arithmetic): lane l computes hidden units l and l + 32 of each layer, so
+// the warp reads consecutive weights; every lane returns the de-normalised
+// outputs (mean offset, log-deviation ratio).
+__device__ __forceinline__ void warp_mlp(const __nv_bfloat16* W, const float* nm, const float (&feat)[kIn], int lane,
+                                         float& u0, float& u1) {
+  float a1[2] = {__bfloat162float(W[kB1 + lane]), __bfloat162float(W[kB1 + lane + 32])};
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) {
+    const float xk = (feat[k] - __ldg(nm + k)) / __ldg(nm + kIn + k);
+    a1[0] = fmaf(__bfloat162float(W[kW1 + k * kH + lane]), xk, a1[0]);
+    a1[1] = fmaf(__bfloat162float(W[kW1 + k * kH + lane + 32]), xk, a1[1]);
+  }
+  const float h1[2] = {gelu_f(a1[0]), gelu_f(a1[1])};
+  // layer 2: every input unit comes from the lane that holds it
+  float a2[2] = {__bfloat162float(W[kB2 + lane]), __bfloat162float(W[kB2 + lane + 32])};
+#pragma unroll 4
+  for (int k = 0; k < kH; ++k) {
+    const float hk = __shfl_sync(0xffffffffu, h1[k >> 5], k & 31);
+    a2[0] = fmaf(__bfloat162float(W[kW2 + k * kH + lane]), hk, a2[0]);
+    a2[1] = fmaf(__bfloat162float(W[kW2 + k * kH + lane + 32]), hk, a2[1]);
+  }
+  const float h2a = gelu_f(a2[0]), h2b = gelu_f(a2[1]);
+  // layer 3: two sums over the warp
+  float y0 = __bfloat162float(W[kW3 + lane]) * h2a + __bfloat162float(W[kW3 + lane + 32]) * h2b;
+  float y1 = __bfloat162float(W[kW3 + kH + lane]) * h2a + __bfloat162float(W[kW3 + kH + lane + 32]) * h2b;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+  }
+  u0 = (y0 + __bfloat162float(W[kB3])) * __ldg(nm + 2 * kIn + 2) + __ldg(nm + 2 * kIn);
+  u1 = (y1 + __bfloat162float(W[kB3 + 1])) * __ldg(nm + 2 * kIn + 3) + __ldg(nm + 2 * kIn + 1);
+}
+
 __device__ __forceinline__ void mark_pixel(uint32_t* bm, const int32_t* cpix, int64_t e) {
   const int32_t i = __ldg(cpix + e);
   if (i >= 0) atomicOr(bm + (i >> 5), 1u << (i & 31));
@@ -1331,7 +876,10 @@ __device__ __forceinline__ void approx_interval(float n_set, const float (&h)[6]
   hi = __fadd_rn(mu, __fmul_rn(k, sd));
 }
 
-template <int MODE, int PREC, int kWarps>
+// SURR 0: the plain method; 1: also record the surrogate's features and
+// training targets; 2: place the first core from the surrogate's prediction
+// of the final interval (the replay is the same exact loop).
+template <int MODE, int PREC, int kWarps, int SURR>
 __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs a) {
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
   // the tail's share of a step is merged over the lanes in FP32 except
@@ -1345,6 +893,10 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
   const int capr = MODE == MODE_ENTRY ? (a.cap + 3) & ~3 : 0;
   float* wts = reinterpret_cast<float*>(smem_raw);
   uint2* tail = reinterpret_cast<uint2*>(wts + capr) + (size_t)warp * (32 * a.tcap) + lane;
+  // surrogate modes: a 64-bin histogram per warp after the tails
+  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint2*>(wts + capr) + (size_t)kWarps * 32 * a.tcap) +
+                   64 * warp;
+  (void)hist;
 
   const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
   const int f0 = blockIdx.y * a.frames_per_cta;
@@ -1366,6 +918,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
   // optional counters: items, pass B scans, overflows, replay steps, tail
   // entries listed, items marked from the tail, full passes
   unsigned long long cs[7] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long su[2] = {0, 0};   // surrogate: items whose predicted core held / that re-placed it
 
   for (int f = f0 + warp; f < f1; f += kWarps) {
     // this item's values: entry e of the row at slot r0 + e of the staged frame
@@ -1374,6 +927,8 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
     cs[0] += 1;
     // ------------- pass A: where to place the core -------------
     float cLo, cHi, K;
+    float feat[kIn], m1 = 0.0f, s1 = 0.0f;
+    (void)feat;
     {
       float ss[NF], cz[NF];
       uint32_t ci[NI];
@@ -1390,6 +945,22 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
       cLo = __fadd_rn(lo, mg);
       cHi = __fsub_rn(hi, mg);
       K = choose_shift(mu, sd);
+      if (SURR != 0) {
+        m1 = mu;
+        s1 = sd;
+        sample_features<MODE>(row, wts, ge, lane, step, n_set, h[0], m1, s1, hist, feat);
+      }
+      if (SURR == 2) {
+        // the predicted final interval, and the core half a deviation inside it
+        float u0, u1;
+        warp_mlp(a.mlp_w, a.mlp_norm, feat, lane, u0, u1);
+        const float mh = fmaf(s1, u0, m1), sh = s1 * expf(fminf(u1, 20.0f));
+        if (s1 > 0.0f && sh > 0.0f && fabsf(mh) <= FLT_MAX && sh <= FLT_MAX) {
+          const float half = __fmul_rn(a.k_clip, sh), mgs = __fmul_rn(kSurrMargin, sh);
+          cLo = __fadd_rn(__fsub_rn(mh, half), mgs);
+          cHi = __fsub_rn(__fadd_rn(mh, half), mgs);
+        }
+      }
     }
     // ------------- the loop of Eq. 19: replay on core + tail, or full passes -------------
     Bcast st;
@@ -1402,7 +973,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
     st.done = 0;
     st.Kf = K;
     bool ovf = false, scan = true;
-    int m = 0;
+    int m = 0, scans = 0;
     float cn = 0.0f, ch[6], cl[6];
     for (;;) {
       const float Ln = st.Ln, Hn = st.Hn;
@@ -1413,6 +984,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
         const bool fit =
             lane_core_sums<MODE, KAHAN>(row, wts, ge, lane, cLo, cHi, K, tail, a.tcap, m, ss, cc, ci);
         ovf = __any_sync(0xffffffffu, !fit);
+        ++scans;
         if (a.clip_stats) {
           cs[1] += 1;
           cs[2] += ovf ? 1 : 0;
@@ -1468,7 +1040,15 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
         a.bounds[2 * o + 1] = st.H;
       }
       if (a.iters) a.iters[o] = st.steps;
+      if (SURR == 1) {
+        // training record: the features and the result as normalised targets
+        for (int k = 0; k < kIn; ++k) a.rec_feat[o * kIn + k] = feat[k];
+        const bool ok = s1 > 0.0f && st.sd > 0.0f && st.n_cur >= 2.0f;
+        a.rec_target[o * 2] = ok ? (st.mu_hi - m1) / s1 : __int_as_float(0x7fc00000);
+        a.rec_target[o * 2 + 1] = ok ? logf(st.sd / s1) : __int_as_float(0x7fc00000);
+      }
     }
+    if (SURR == 2) su[(scans == 1 && !ovf) ? 0 : 1] += 1;
     // threshold of sparsification (Section 3) from the final state
     const float thr = pick_threshold<PREC>(st, a.k_pick);
     if (a.thr_out && lane == 0) a.thr_out[o] = thr;
@@ -1500,29 +1080,9 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
     for (int i = 0; i < 7; ++i)
       if (cs[i]) atomicAdd(a.clip_stats + i, cs[i]);
   }
-}
-
-// mode 0: set the shared-memory attribute and launch; 1: attribute only
-// (done eagerly before a stream capture); 2: launch only.
-template <int MODE, int PREC, int TPB, int SURR>
-cudaError_t launch_t(const ClipArgs& a, int n_ctas, int mode, cudaStream_t s) {
-  const size_t smem = clip_smem_bytes(a.cap, MODE == MODE_ENTRY);
-  auto k = k_integrate_clip<MODE, PREC, TPB, SURR>;
-  if (mode != 2) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess || mode == 1) return e;
-  }
-  dim3 grid(n_ctas, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
-  k<<<grid, TPB, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int MODE, int PREC, int SURR>
-cudaError_t launch_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
-  switch (tpb) {
-    case 64: return launch_t<MODE, PREC, 64, SURR>(a, n_ctas, mode, s);
-    case 128: return launch_t<MODE, PREC, 128, SURR>(a, n_ctas, mode, s);
-    default: return launch_t<MODE, PREC, 256, SURR>(a, n_ctas, mode, s);
+  if (SURR == 2 && a.surr_stats && lane == 0) {
+    if (su[0]) atomicAdd(a.surr_stats, su[0]);
+    if (su[1]) atomicAdd(a.surr_stats + 1, su[1]);
   }
 }
 
@@ -1540,7 +1100,7 @@ int smem_optin() {
   return cached[dev];
 }
 
-template <int MODE, int PREC, int kWarps>
+template <int MODE, int PREC, int kWarps, int SURR>
 cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   // shared memory: the weights of a row (per-entry weights only), then
   // each warp's tail (8 bytes a slot, 32 lanes)
@@ -1551,8 +1111,8 @@ cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   if (kWarps * 256 * tcap > budget) tcap = std::max(0L, budget / (256L * kWarps));
   if (tcap < 5) tcap = 0;   // no room for a tail: every step runs as a full pass
   a.tcap = (int32_t)tcap;
-  const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap);
-  auto k = k_clip_warp<MODE, PREC, kWarps>;
+  const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap + (SURR != 0 ? kWarps * 256 : 0));
+  auto k = k_clip_warp<MODE, PREC, kWarps, SURR>;
   if (mode != 2) {
     // the attribute only grows: size classes sharing this instance may set
     // it in any order before a capture
@@ -1571,21 +1131,21 @@ cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MODE, int PREC>
+template <int MODE, int PREC, int SURR = 0>
 cudaError_t launch_tail_b(const ClipArgs& a, int n_ctas, int tpb, int mode, cudaStream_t s) {
   switch (tpb) {
-    case 32: return launch_warp_t<MODE, PREC, 1>(a, n_ctas, mode, s);
-    case 64: return launch_warp_t<MODE, PREC, 2>(a, n_ctas, mode, s);
-    case 128: return launch_warp_t<MODE, PREC, 4>(a, n_ctas, mode, s);
-    default: return launch_warp_t<MODE, PREC, 8>(a, n_ctas, mode, s);
+    case 32: return launch_warp_t<MODE, PREC, 1, SURR>(a, n_ctas, mode, s);
+    case 64: return launch_warp_t<MODE, PREC, 2, SURR>(a, n_ctas, mode, s);
+    case 128: return launch_warp_t<MODE, PREC, 4, SURR>(a, n_ctas, mode, s);
+    default: return launch_warp_t<MODE, PREC, 8, SURR>(a, n_ctas, mode, s);
   }
 }
 
 template <int MODE>
 cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
   // the surrogate modes exist for the default precision only
-  if (a.rec_feat) return launch_b<MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
-  if (a.mlp_w) return launch_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
+  if (a.rec_feat) return launch_tail_b<MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
+  if (a.mlp_w) return launch_tail_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
   switch (prec) {
     case SEP_PREC_PLAIN: return launch_tail_b<MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
     case SEP_PREC_KAHAN: return launch_tail_b<MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);
@@ -1597,7 +1157,9 @@ cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int m
 }  // namespace
 
 size_t clip_smem_bytes(int32_t cap, bool weighted) {
-  size_t smem = (size_t)cap * (weighted ? 8 : 4);
+  // the shared memory a clip launch cannot do without: the per-entry weights
+  // of the longest row (a tail can shrink to nothing)
+  size_t smem = weighted ? (size_t)cap * 4 : 0;
   return (smem + 15) & ~(size_t)15;
 }
 

@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(kGradThreads) k_mlp_grad(const __nv_bfloat16* 
   if (tid == 0) atomicAdd(loss, lsum / (float)n_used);
 }
 
-// Adam step on the FP32 master parameters; refreshes the BF16 copy and
-// clears the gradient for the next batch.
-__global__ void k_adam(float* theta, __nv_bfloat16* wbf, float* m, float* v, float* grad, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+// Adam step on the FP32 master parameters; refreshes the BF16 copies (the
+// training layout and the clip kernel's input-major one) and clears the
+// gradient for the next batch.
+__global__ void k_adam(float* theta, __nv_bfloat16* wbf, __nv_bfloat16* wbt, float* m, float* v, float* grad, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
   const float g = grad[i];
@@ -162,6 +163,7 @@ __global__ void k_adam(float* theta, __nv_bfloat16* wbf, float* m, float* v, flo
   const float th = theta[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   theta[i] = th;
   wbf[i] = __float2bfloat16_rn(th);
+  wbt[mlp_transposed_index(i)] = __float2bfloat16_rn(th);
   grad[i] = 0.0f;
 }
 
@@ -313,11 +315,11 @@ cudaError_t launch_mlp_grad(const __nv_bfloat16* wbf, const float* x, const floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* theta, __nv_bfloat16* wbf, float* m, float* v, float* grad, float lr, int64_t step,
-                        cudaStream_t s) {
+cudaError_t launch_adam(float* theta, __nv_bfloat16* wbf, __nv_bfloat16* wbt, float* m, float* v, float* grad, float lr,
+                        int64_t step, cudaStream_t s) {
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-  k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(theta, wbf, m, v, grad, lr, b1, b2, 1e-8f, c1, c2);
+  k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(theta, wbf, wbt, m, v, grad, lr, b1, b2, 1e-8f, c1, c2);
   return cudaGetLastError();
 }
 

@@ -168,6 +168,13 @@ void set_interp(sep::PixArgs& p, const sep_csr* csr, const sep_params* params) {
 }
 
 sep_status check_bin_fits(sep_ctx* ctx, const sep_csr* csr) {
+  // the clip kernel keeps an entry's index inside its row in 16 bits and, with
+  // per-entry weights, the longest row's weights in shared memory
+  if (csr->h.max_row >= 65536) {
+    char buf[120];
+    snprintf(buf, sizeof buf, "largest bin has %d entries; at most 65535 are supported", csr->h.max_row);
+    return fail(ctx, SEP_ERR_CSR, buf);
+  }
   int optin = 0;
   SEP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
   const size_t need = sep::clip_smem_bytes(csr->h.max_row, csr->weighted) + sep::kClipStaticSmem;
@@ -267,10 +274,9 @@ sep::ClipArgs clip_args(sep_ctx* ctx, const sep_csr* csr, const float* stage, in
   a.thr_out = thr_out;
   if (ctx->clip_stats_on) a.clip_stats = ctx->d_clip_stats;
   if (pr->surrogate > 0 && csr->model) {
-    a.mlp_w = csr->model->d_wbf;
+    a.mlp_w = csr->model->d_wbt;
     a.mlp_norm = csr->model->d_norm;
     a.surr_stats = ctx->d_surr;
-    a.surr_passes = pr->surrogate;
   }
   return a;
 }

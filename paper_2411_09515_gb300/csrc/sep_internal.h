@@ -92,13 +92,13 @@ struct ClipArgs {
   // mixed batches: per launch frame, the first output row (in bins) of its
   // profile; null = rows f * nbins
   const int64_t* orow = nullptr;
-  // surrogate: record features + targets (training data), or predict + verify
+  // surrogate: record features + targets (training data), or place the
+  // first core from the prediction
   float* rec_feat = nullptr;           // [rows][20]
   float* rec_target = nullptr;         // [rows][2]
   const __nv_bfloat16* mlp_w = nullptr;
   const float* mlp_norm = nullptr;
-  unsigned long long* surr_stats = nullptr;   // [2]: bins settled by the surrogate, bins that fell back
-  int32_t surr_passes = 1;             // verification passes before the plain fallback
+  unsigned long long* surr_stats = nullptr;   // [2]: bins whose predicted core held, bins that re-placed it
   int32_t tcap = 0;                    // tail slots per thread of the tail-replay kernel (set at launch)
   unsigned long long* clip_stats = nullptr;   // [SEP_CLIP_STATS] counters of the tail replay, or null
 };
@@ -272,6 +272,7 @@ struct sep_model {
   sep_ctx* ctx = nullptr;
   float* d_params = nullptr;      // FP32 master parameters
   __nv_bfloat16* d_wbf = nullptr; // BF16 copy read by every forward / backward
+  __nv_bfloat16* d_wbt = nullptr; // the same, W1 and W2 input-major (the clip kernel's inference)
   float* d_m = nullptr;           // Adam moments
   float* d_v = nullptr;
   float* d_grad = nullptr;

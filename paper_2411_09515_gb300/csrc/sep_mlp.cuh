@@ -18,6 +18,21 @@ constexpr int kB2 = kW2 + kH * kH;
 constexpr int kW3 = kB2 + kH;
 constexpr int kB3 = kW3 + kOut * kH;
 constexpr int kNParams = kB3 + kOut;   // 5634
+// The clip kernel's copy of the weights keeps W1 and W2 input-major (at
+// kW1 + k kH + j and kW2 + k kH + j for unit j and input k), so that the
+// lanes of a warp, one hidden unit each, read consecutive weights.
+__host__ __device__ __forceinline__ int mlp_transposed_index(int i) {
+  if (i >= kW1 && i < kB1) {
+    const int j = (i - kW1) / kIn, k = (i - kW1) % kIn;
+    return kW1 + k * kH + j;
+  }
+  if (i >= kW2 && i < kB2) {
+    const int j = (i - kW2) / kH, k = (i - kW2) % kH;
+    return kW2 + k * kH + j;
+  }
+  return i;
+}
+
 // normalisation block stored with a model: feature mean[20], feature std[20],
 // target mean[2], target std[2]
 constexpr int kNNorm = 2 * kIn + 2 * kOut;
@@ -54,8 +69,8 @@ __device__ __forceinline__ void mlp_eval(const float* W, const float (&x)[kIn], 
 size_t mlp_grad_smem();
 cudaError_t launch_mlp_grad(const __nv_bfloat16* wbf, const float* x, const float* t, int64_t n, int64_t n_used,
                             int64_t start, int64_t stride, float* grad, float* loss, cudaStream_t s);
-cudaError_t launch_adam(float* theta, __nv_bfloat16* wbf, float* m, float* v, float* grad, float lr, int64_t step,
-                        cudaStream_t s);
+cudaError_t launch_adam(float* theta, __nv_bfloat16* wbf, __nv_bfloat16* wbt, float* m, float* v, float* grad, float lr,
+                        int64_t step, cudaStream_t s);
 cudaError_t launch_mlp_forward(const __nv_bfloat16* wbf, const float* x, int64_t n, float* y, cudaStream_t s);
 cudaError_t launch_zero(float* p, int64_t n, cudaStream_t s);
 int64_t prep_blocks(int64_t n);

@@ -40,6 +40,7 @@ uint64_t splitmix(uint64_t& s) {
 sep_status model_alloc(sep_ctx* ctx, sep_model* m) {
   const size_t P = sep::kNParams;
   if (cudaMalloc((void**)&m->d_params, P * 4) != cudaSuccess || cudaMalloc((void**)&m->d_wbf, P * 2) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_wbt, P * 2) != cudaSuccess ||
       cudaMalloc((void**)&m->d_m, P * 4) != cudaSuccess || cudaMalloc((void**)&m->d_v, P * 4) != cudaSuccess ||
       cudaMalloc((void**)&m->d_grad, P * 4) != cudaSuccess || cudaMalloc((void**)&m->d_loss, 8) != cudaSuccess ||
       cudaMalloc((void**)&m->d_norm, sep::kNNorm * 4) != cudaSuccess)
@@ -52,10 +53,14 @@ sep_status model_alloc(sep_ctx* ctx, sep_model* m) {
 }
 
 sep_status upload_params(sep_model* m, const float* host) {
-  std::vector<__nv_bfloat16> bf(sep::kNParams);
-  for (int i = 0; i < sep::kNParams; ++i) bf[i] = __float2bfloat16_rn(host[i]);
+  std::vector<__nv_bfloat16> bf(sep::kNParams), bt(sep::kNParams);
+  for (int i = 0; i < sep::kNParams; ++i) {
+    bf[i] = __float2bfloat16_rn(host[i]);
+    bt[sep::mlp_transposed_index(i)] = bf[i];
+  }
   MCUDA(m->ctx, cudaMemcpy(m->d_params, host, sep::kNParams * 4, cudaMemcpyHostToDevice));
   MCUDA(m->ctx, cudaMemcpy(m->d_wbf, bf.data(), sep::kNParams * 2, cudaMemcpyHostToDevice));
+  MCUDA(m->ctx, cudaMemcpy(m->d_wbt, bt.data(), sep::kNParams * 2, cudaMemcpyHostToDevice));
   return SEP_OK;
 }
 
@@ -101,6 +106,7 @@ void sep_model_destroy(sep_model* m) {
   if (m->ctx) cudaSetDevice(m->ctx->device);
   cudaFree(m->d_params);
   cudaFree(m->d_wbf);
+  cudaFree(m->d_wbt);
   cudaFree(m->d_m);
   cudaFree(m->d_v);
   cudaFree(m->d_grad);
@@ -172,7 +178,7 @@ sep_status sep_surrogate_train(sep_model* m, const float* x_dev, const float* t_
       MCUDA(m->ctx, sep::launch_mlp_grad(m->d_wbf, x_dev, t_dev, n, used, start, stride, m->d_grad,
                                          m->d_loss, s));
       m->step += 1;
-      MCUDA(m->ctx, sep::launch_adam(m->d_params, m->d_wbf, m->d_m, m->d_v, m->d_grad, cfg->lr, m->step, s));
+      MCUDA(m->ctx, sep::launch_adam(m->d_params, m->d_wbf, m->d_wbt, m->d_m, m->d_v, m->d_grad, cfg->lr, m->step, s));
     }
     float l = 0;
     MCUDA(m->ctx, cudaMemcpyAsync(&l, m->d_loss, 4, cudaMemcpyDeviceToHost, s));
