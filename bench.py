@@ -172,6 +172,22 @@ def measured_traffic(F):
     return int(rec["bytes_per_frame"] * F)
 
 
+def leg_status(sep, out=None, kcap=None, pcap=None):
+    """The device status word of the leg just run (read and cleared by the
+    library), with its largest kept-pixel and peak counts against the
+    capacities; a leg whose outputs overflowed is marked void."""
+    st = {"device_status": int(sep.device_status())}
+    if out is not None:
+        st["max_kept"] = int(out["n_kept"].max().item())
+        st["max_peaks"] = int(out["n_peaks"].max().item())
+        if kcap is not None:
+            st["kept_capacity"] = kcap
+            st["peak_capacity"] = pcap
+    if st["device_status"] != 0:
+        st["void"] = "capacity overflow: outputs truncated, this leg's number is not a valid measurement"
+    return st
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -212,6 +228,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    sep.device_status()   # clear the status word before the timed region
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -228,7 +245,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), device=f"cuda:{local}")
     per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
-    status = sep.device_status()
+    main_leg = leg_status(sep, out, kcap, pcap)
+    status = main_leg["device_status"]
     n_kept = out["n_kept"].cpu().numpy()
     n_peaks = out["n_peaks"].cpu().numpy()
 
@@ -250,6 +268,7 @@ def run_ours(args):
     k1.record(stream)
     torch.cuda.synchronize()
     k_ms = k0.elapsed_time(k1) / args.steps
+    clip_leg = leg_status(sep)
 
     # end to end through the public API from pinned host memory to pinned
     # host memory (the library pipelines copies and compute by chunks)
@@ -259,6 +278,7 @@ def run_ours(args):
     for _ in range(2):
         sep.process_host(host, host_out, kcap, pcap, chunk_frames=args.chunk_frames, stream=stream)
     torch.cuda.synchronize()
+    sep.device_status()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -267,21 +287,42 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), device=f"cuda:{local}")
+    e2e_leg = leg_status(sep)
+    e2e_leg["max_kept"] = int(host_out["n_kept"].max())
+    e2e_leg["max_peaks"] = int(host_out["n_peaks"].max())
 
     # densification (Section 3) of the batch's sparse output, timed alone
+    sep.device_status()
     dens = densify_eval(sep, out, F, stream, args)
+    dens.update(leg_status(sep))
     # the clip variants of Section 2.4 on the same batch, and the veto
     variants = variants_eval(sep, dev, out, kcap, pcap, stream, args)
 
     # the learned surrogate against the plain loop on the same batch
     sur = None
     if args.surrogate_train_frames > 0:
+        sep.device_status()
         sur = surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args)
+        sur.update(leg_status(sep, out, kcap, pcap))
 
-    # oracle on the host cores, rank 0 at N = 1 only
+    # oracle on the host cores, rank 0 at N = 1 only, with the precision
+    # modes' errors against it on the same frames
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(det, mask, cal, frames_np, args.cpu_frames)
+        nc = max(1, min(args.cpu_frames, F))
+        modes = {}
+        for name, pv in (("plain", B.SEP_PREC_PLAIN), ("kahan", B.SEP_PREC_KAHAN),
+                         ("fp64merge", B.SEP_PREC_FP64MERGE), ("dword", B.SEP_PREC_DWORD)):
+            sep.set_params(precision=pv)
+            r = sep.integrate_clip(dev[:nc])
+            modes[name] = (r["mean"].double().cpu().numpy(), r["sigma"].double().cpu().numpy())
+        sep.set_params(precision=prec)
+        cpu = cpu_baseline(det, mask, cal, frames_np, args.cpu_frames, modes)
+
+    # uneven batching (1M / 4M / 16M frames in one graph)
+    mixed = None
+    if world == 1 and args.mixed_frames > 0:
+        mixed = mixed_eval(args.mixed_frames, 3, 2, args.kept_capacity, args.peak_capacity)
 
     # thresholds from the smooth background, last (it overwrites the outputs)
     interp = interp_eval(sep, dev, out, kcap, pcap, stream)
@@ -309,22 +350,26 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "k_stage + k_integrate_clip", "achieved": round(achieved, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": measured_traffic(F),
-                         "peak_source": src, "kernel_ms": round(k_ms, 4),
+                         "peak_source": src, "kernel_ms": round(k_ms, 4), "kernel_leg": clip_leg,
                          "algorithmic_bytes_per_launch": alg,
                          "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                          "whole_path": {"bytes_per_frame": round(path_bytes, 1),
                                         "frames_s_at_peak": round(path_roof, 1),
                                         "frac": round(value / world / path_roof, 4)}},
             "e2e": {"value": round(whole_job_rate(F, args.steps, world, e2e_ms), 2), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "chunk_frames": args.chunk_frames},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "chunk_frames": args.chunk_frames,
+                    **e2e_leg},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            # each precision mode's error against the FP64 oracle on the same frames
+            "precision": cpu.get("precision") if cpu else None,
             "surrogate": sur,
             "densify": dens,
             "variants": variants,
             "interpolated_thresholds": interp,
-            "device_status": status,
+            "mixed": mixed,
+            "device_status": status, "main_leg": main_leg,
             "mean_kept_per_frame": float(n_kept.mean()), "mean_peaks_per_frame": float(n_peaks.mean()),
             "setup_s": round(t_gen, 1),
         }
@@ -355,12 +400,20 @@ def variants_eval(sep, dev, out, kcap, pcap, stream, args):
 
     res = {}
     base = (sep.params.cutoff, sep.params.error_model)
+    # the Poisson deviation of these low-count frames is below the azimuthal
+    # one: those models keep several times more pixels and peaks, so the
+    # variants write into outputs sized for them
+    vk, vp = max(kcap, 1 << 21), max(pcap, 1 << 18)
+    vout = sep.alloc_outputs(F, vk, vp)
     for name, kw in (("chauvenet", {"cutoff": SEP_CUTOFF_CHAUVENET}), ("poisson", {"error_model": SEP_ERROR_POISSON}),
                      ("hybrid", {"error_model": SEP_ERROR_HYBRID})):
         sep.set_params(**kw)
-        ms = timed(lambda: sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream), 3)
-        res[name] = {"frames_s": round(F / (ms * 1e-3), 1), "ms_per_step": round(ms, 3)}
+        sep.device_status()
+        ms = timed(lambda: sep.process_batch(dev, vk, vp, out=vout, use_graph=True, stream=stream), 3)
+        res[name] = {"frames_s": round(F / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+                     **leg_status(sep, vout, vk, vp)}
         sep.set_params(cutoff=base[0], error_model=base[1])
+    del vout
     sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)   # the plain outputs again
     dst = {k: torch.empty_like(out[k]) for k in ("idx", "val", "peaks", "n_kept", "n_peaks")}
     thr = 20
@@ -371,9 +424,10 @@ def variants_eval(sep, dev, out, kcap, pcap, stream, args):
             sep.compact_frames(lst, n, out[k], out=dst[k], stream=stream)
         return n
 
+    sep.device_status()
     ms = timed(veto_step, 5)
     n = int(veto_step().item())
-    res["veto"] = {"min_peaks": thr, "frames_passed": n, "frames": F, "ms": round(ms, 3)}
+    res["veto"] = {"min_peaks": thr, "frames_passed": n, "frames": F, "ms": round(ms, 3), **leg_status(sep)}
     return res
 
 
@@ -390,6 +444,7 @@ def interp_eval(sep, dev, out, kcap, pcap, stream):
         run = lambda: sep.process_batch(dev, kcap, pcap, out=out, use_graph=True, stream=stream)
         run()
         torch.cuda.synchronize()
+        sep.device_status()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(3):
@@ -400,7 +455,7 @@ def interp_eval(sep, dev, out, kcap, pcap, stream):
         return {"frames_s": round(F / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
                 "mean_kept_per_frame": float(out["n_kept"].float().mean().item()),
                 "mean_peaks_per_frame": float(out["n_peaks"].float().mean().item()),
-                "device_status": sep.device_status()}
+                **leg_status(sep, out, kcap, pcap)}
     except Exception as e:   # reported, not hidden: the line still carries the other measurements
         return {"error": f"{type(e).__name__}: {e}"}
     finally:
@@ -509,31 +564,51 @@ def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
     return res
 
 
-def cpu_baseline(det, mask, cal, frames_np, n):
-    """The oracle as it stands on a bounded sample of the same frames, all host cores."""
+def cpu_baseline(det, mask, cal, frames_np, n, gpu_modes=None):
+    """The oracle as it stands on a bounded sample of the same frames, all
+    host cores; with gpu_modes (name -> (mean, sigma) of the library on those
+    frames in each precision mode) also the modes' errors against the
+    oracle's per-bin results."""
     import oracle
     W = oracle.weights(det, mask)
     threads = oracle.max_threads()
     n = max(1, min(n, frames_np.shape[0]))
     t0 = time.time()
-    oracle.process_frames(det, W, frames_np[:n], calib=cal, threads=threads)
+    mean, sigma, _, _ = oracle.process_frames(det, W, frames_np[:n], calib=cal, threads=threads)
     dt = time.time() - t0
-    return {"value": round(n / dt, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} of the batch's JF4M raw frames through oracle.process_frames (FP64), weights excluded"}
+    res = {"value": round(n / dt, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{n} of the batch's JF4M raw frames through oracle.process_frames (FP64), weights excluded"}
+    if gpu_modes:
+        prec = {"frames": n, "note": "per-bin relative error against the oracle over every bin with a "
+                                     "nonzero deviation (a bin whose clip decision sits in the 1e-5 band "
+                                     "may follow another trajectory; the GPU tests replay those)"}
+        ok = sigma > 0
+        for name, (gm, gs) in gpu_modes.items():
+            em = np.abs(gm[:n] - mean) / np.maximum(np.abs(mean), 1e-2 * sigma)
+            es = np.abs(gs[:n] - sigma) / np.maximum(sigma, 1e-30)
+            em, es = em[ok], es[ok]
+            within = (np.abs(gm[:n] - mean) <= 1e-5 * np.abs(mean) + 1e-7 * sigma) & \
+                     (np.abs(gs[:n] - sigma) <= 1e-5 * sigma)
+            prec[name] = {"mean_rel_err_median": float(np.median(em)), "mean_rel_err_p999": float(np.quantile(em, 0.999)),
+                          "mean_rel_err_max": float(em.max()), "sigma_rel_err_median": float(np.median(es)),
+                          "sigma_rel_err_p999": float(np.quantile(es, 0.999)), "sigma_rel_err_max": float(es.max()),
+                          "bins_within_1e-5": float(within[ok].mean()), "bins": int(ok.sum())}
+        res["precision"] = prec
+    return res
 
 
-def run_mixed(args):
+def mixed_eval(n_frames, steps, warmup, kcap, pcap):
     """Uneven batching: a stream of float32 photon frames from 1M, 4M and 16M
     Jungfrau-shaped detectors (3:2:1, 600 / 1000 / 2000 bins, no splitting)
     in one call and one captured graph, schedules autotuned per detector.
-    Reports aggregate frames/s and GB/s, and frames/s per detector size."""
+    Returns aggregate frames/s and GB/s, and frames/s per detector size."""
     import torch
     import synth
     from paper_2411_09515_gb300 import Context, Separator, process_mixed
     rng = np.random.default_rng(7)
     dets = [synth.det_jf1m(nbins=600), synth.det_jf4m(split=1, nbins=1000), synth.det_jf16m(nbins=2000)]
     masks = [d.mask() for d in dets]
-    groups = max(1, args.frames // 6)
+    groups = max(1, n_frames // 6)
     pattern = []
     for _ in range(groups):
         grp = [0, 1, 0, 2, 1, 0]
@@ -554,17 +629,19 @@ def run_mixed(args):
         sample = torch.stack(per[d][:8])
         tuned[d] = {"ms": seps[d].autotune(sample), **seps[d].get_plan()}
     # 16M frames keep ~0.7 M pixels and carry up to a few thousand peaks
-    kcap, pcap = max(args.kept_capacity, 1 << 20), max(args.peak_capacity, 1 << 15)
-    for _ in range(args.warmup):
+    kcap, pcap = max(kcap, 1 << 20), max(pcap, 1 << 15)
+    for _ in range(warmup):
         out = process_mixed(seps, frames, kcap, pcap)
     torch.cuda.synchronize()
+    seps[0].device_status()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         out = process_mixed(seps, frames, kcap, pcap)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
+    status = leg_status(seps[0], out, kcap, pcap)
     n = len(frames)
     byts = sum(4 * dets[d].npix for d in pattern)
     per_size = {}
@@ -576,17 +653,26 @@ def run_mixed(args):
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             seps[d].process_batch(batch, kcap, pcap, out=o)
         a1.record()
         torch.cuda.synchronize()
-        per_size[name] = round(batch.shape[0] / (a0.elapsed_time(a1) / args.steps) * 1e3, 1)
-    line = {"metric": "mixed 1M/4M/16M frames/s (clip+sparsify+peaks), one graph", "value": round(n / ms * 1e3, 2),
-            "unit": "frames/s", "ms_per_step": round(ms, 3), "steps": args.steps, "warmup": args.warmup,
-            "frames_per_step": n, "gbs_input": round(byts / (ms * 1e-3) / 1e9, 1), "per_size_frames_s": per_size,
-            "plans": tuned, "dtype": "f32", "data": "synthetic", "device_status": seps[0].device_status(),
-            "max_kept_per_frame": int(out["n_kept"].max().item()), "max_peaks_per_frame": int(out["n_peaks"].max().item()),
-            "capacities": [kcap, pcap],
+        per_size[name] = round(batch.shape[0] / (a0.elapsed_time(a1) / steps) * 1e3, 1)
+    res = {"frames_s": round(n / ms * 1e3, 2), "ms_per_step": round(ms, 3), "frames_per_step": n,
+           "sizes": {"1M": len(per[0]), "4M": len(per[1]), "16M": len(per[2])},
+           "gbs_input": round(byts / (ms * 1e-3) / 1e9, 1), "per_size_frames_s": per_size, "plans": tuned,
+           **status}
+    for sp in seps:
+        sp.close()
+    ctx.close()
+    return res
+
+
+def run_mixed(args):
+    r = mixed_eval(args.frames, args.steps, args.warmup, args.kept_capacity, args.peak_capacity)
+    line = {"metric": "mixed 1M/4M/16M frames/s (clip+sparsify+peaks), one graph", "value": r["frames_s"],
+            "unit": "frames/s", "ms_per_step": r["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32", "data": "synthetic", **r,
             "config": {"workload": "mixed f32 1M:4M:16M = 3:2:1, 600/1000/2000 bins, no split"}}
     print(json.dumps(line), flush=True)
 
@@ -632,6 +718,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--chunk-frames", type=int, default=64)
     ap.add_argument("--surrogate-train-frames", type=int, default=256)
+    ap.add_argument("--mixed-frames", type=int, default=24)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge", "dword"], default="dword")
     ap.add_argument("--workload", choices=["jf4m", "mixed"], default="jf4m")

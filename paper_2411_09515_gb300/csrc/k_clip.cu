@@ -346,6 +346,7 @@ __device__ __forceinline__ void unpack_totals(const float* th, const float* tl, 
 // synchronises (its warps take other frames of the same bin).
 constexpr float kCoreMargin = 1.0f;   // core margin inside the clip interval, in deviations
 constexpr int kLoadsAhead = 4;        // 16-byte loads in flight per lane in a scan of the row
+constexpr int kWarpsPerSM = 16;       // resident warps per SM the register budget is sized for
 
 // One item's row: entry e's staged value at v4[e / 4] (padding slots NaN).
 struct Row {
@@ -880,7 +881,7 @@ __device__ __forceinline__ void approx_interval(float n_set, const float (&h)[6]
 // training targets; 2: place the first core from the surrogate's prediction
 // of the final interval (the replay is the same exact loop).
 template <int MODE, int PREC, int kWarps, int SURR>
-__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs a) {
+__global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp(ClipArgs a) {
   constexpr bool KAHAN = PREC == SEP_PREC_KAHAN;
   // the tail's share of a step is merged over the lanes in FP32 except
   // where the per-lane sums are compensated (KAHAN) or merged in FP64
@@ -915,16 +916,19 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
     }
     __syncthreads();
   }
-  // optional counters: items, pass B scans, overflows, replay steps, tail
-  // entries listed, items marked from the tail, full passes
-  unsigned long long cs[7] = {0, 0, 0, 0, 0, 0, 0};
+  // optional counters (added by lane 0 as they occur): items, pass B
+  // scans, overflows, replay steps, tail entries listed, items marked from
+  // the tail, full passes
+  auto stat = [&](int i, unsigned v) {
+    if (a.clip_stats && lane == 0 && v) atomicAdd(a.clip_stats + i, (unsigned long long)v);
+  };
   unsigned long long su[2] = {0, 0};   // surrogate: items whose predicted core held / that re-placed it
 
   for (int f = f0 + warp; f < f1; f += kWarps) {
     // this item's values: entry e of the row at slot r0 + e of the staged frame
     const Row row{reinterpret_cast<const float4*>(a.stage + (int64_t)f * a.npos + r0)};
     const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
-    cs[0] += 1;
+    stat(0, 1);
     // ------------- pass A: where to place the core -------------
     float cLo, cHi, K;
     float feat[kIn], m1 = 0.0f, s1 = 0.0f;
@@ -986,9 +990,10 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
         ovf = __any_sync(0xffffffffu, !fit);
         ++scans;
         if (a.clip_stats) {
-          cs[1] += 1;
-          cs[2] += ovf ? 1 : 0;
-          cs[4] += (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)m);
+          const unsigned listed = __reduce_add_sync(0xffffffffu, (unsigned)m);
+          stat(1, 1);
+          stat(2, ovf ? 1 : 0);
+          stat(4, listed);
         }
         if (!ovf) warp_totals<MODE, PREC>(ss, cc, ci, cn, ch, cl);
         scan = false;
@@ -1001,7 +1006,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
         lane_tail_sums<MODE, KAHAN>(tail, wts, m, Ln, Hn, K, ts, tc, tn);
         warp_sum<5, TPREC>(ts, tc, th, tl);
         tn = __reduce_add_sync(0xffffffffu, tn);
-        cs[3] += 1;
+        stat(3, 1);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           h[v] = ch[v];
@@ -1017,7 +1022,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
         uint32_t ci[NI];
         Kf = st.Kf;
         lane_range_sums<MODE, KAHAN>(row, wts, ge, lane, Ln, Hn, Kf, ss, cc, ci);
-        cs[6] += 1;
+        stat(6, 1);
         warp_totals<MODE, PREC>(ss, cc, ci, n_set, h, l);
       }
       clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model, a.dark_var);
@@ -1062,7 +1067,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
       // else every entry (padding slots hold NaN, never above a threshold)
       const bool from_tail = MODE != MODE_ENTRY && !ovf && thr >= cHi;
       if (from_tail) {
-        cs[5] += 1;
+        stat(5, 1);
         for (int k = 0; k < m; ++k)
           if (__uint_as_float(tail[32 * k].x) > thr) mark_pixel(bm, cp, (int64_t)(tail[32 * k].y & 0xffffu));
       }
@@ -1074,11 +1079,6 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_clip_warp(ClipArgs
       });
     }
     __syncwarp();   // the tail is rewritten by the warp's next frame
-  }
-  if (a.clip_stats && lane == 0) {
-#pragma unroll
-    for (int i = 0; i < 7; ++i)
-      if (cs[i]) atomicAdd(a.clip_stats + i, cs[i]);
   }
   if (SURR == 2 && a.surr_stats && lane == 0) {
     if (su[0]) atomicAdd(a.surr_stats, su[0]);
@@ -1164,11 +1164,12 @@ size_t clip_smem_bytes(int32_t cap, bool weighted) {
 }
 
 int32_t clip_tail_slots(int32_t cap, int32_t tpb) {
-  // per lane of a warp: 1/8 of the row over 32 lanes, plus the 4 slots a
-  // pass B keeps free and some room for uneven lanes (tpb: the block size,
-  // one warp per item whatever it is)
+  // per lane of a warp: 1/12 of the row over 32 lanes (a tail holds about
+  // 1/20 of a row's entries), plus the 4 slots a pass B keeps free and some
+  // room for uneven lanes; a lane that runs out switches its item to full
+  // passes (tpb: the block size, one warp per item whatever it is)
   (void)tpb;
-  return (int32_t)((cap + 255) / 256) + 8;
+  return (int32_t)((cap + 383) / 384) + 6;
 }
 
 cudaError_t launch_integrate_clip(const ClipArgs& a, int n_ctas, int tpb, bool split, bool has_norm,

@@ -260,15 +260,17 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
         float x;
         if (DT == SEP_DTYPE_U16_JF) {
           const uint32_t u = w[h][k], code = u >> 14;
-          if (code == 0 && r0[k] != 0.0f) {
+          const float d0 = __fsub_rn((float)(u & 0x3FFFu), p0[k]);
+          const float q0 = __fmul_rn(d0, r0[k]);
+          const float aq = fabsf(q0);
+          if (code == 0 && r0[k] != 0.0f && ((aq >= 0x1p-125f && aq <= 0x1p125f) || d0 == 0.0f)) {
             // RN((adc - ped) / gain) without a division: with r = RN(1/gain)
             // and q = RN(d r), the residual e = d - q gain is exact under a
             // fused multiply-add, and RN(q + e r) is the correctly rounded
-            // quotient (Markstein's correction, IBM J. Res. Dev. 34(1), 1990;
-            // gain and quotient are normal here)
-            const float d = __fsub_rn((float)(u & 0x3FFFu), p0[k]);
-            const float q = __fmul_rn(d, r0[k]);
-            x = __fmaf_rn(__fmaf_rn(-q, g0[k], d), r0[k], q);
+            // quotient (Markstein's correction, IBM J. Res. Dev. 34(1), 1990);
+            // the range tests keep gain, quotient and residual normal,
+            // elsewhere the IEEE division runs
+            x = __fmaf_rn(__fmaf_rn(-q0, g0[k], d0), r0[k], q0);
           } else {
             float ped = p0[k], gain = g0[k];
             if (code != 0) {   // gain levels 1 and 2

@@ -278,66 +278,11 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
 
   if (too_many) return "exact area fractions: a pixel spans more than 15 bins (bins far narrower than pixels)";
 
-  // Row layout (one row per bin): entries grouped by coefficient class,
-  // largest coefficient first (class c holds k = s*s - c sub-pixels, c = 0 ..
-  // s*s - 1), then the weight-0 centre carriers; columns ascend inside a
-  // group; every group is padded with flagged entries to a multiple of 4 so
-  // the kernels move 4 entries per vector access and apply a class's weight
-  // once per group instead of once per entry.
-  const int NC = s * s + 1;                 // coefficient classes + carriers
-  std::vector<int64_t> cc((size_t)B * NC, 0);
-  for (int64_t i = 0; i < npix; ++i)
-    for (int t = 0; t < pn[i]; ++t) {
-      const int k = pk[(size_t)i * maxe + t];
-      const int c = k == 0 ? NC - 1 : s * s - k;
-      cc[(size_t)pb[(size_t)i * maxe + t] * NC + c] += 1;
-    }
-  auto pad4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
-  out->rowptr.assign((size_t)B + 1, 0);
-  out->grp.assign((size_t)B * 4, 0);
-  std::vector<int64_t> fill((size_t)B * NC, 0);
-  int64_t pos = 0;
-  int32_t max_row = 0;
-  for (int32_t b = 0; b < B; ++b) {
-    const int64_t r0 = pos;
-    for (int c = 0; c < NC; ++c) {
-      fill[(size_t)b * NC + c] = pos;
-      pos += pad4(cc[(size_t)b * NC + c]);
-      if (c < 4) out->grp[(size_t)b * 4 + c] = (int32_t)(pos - r0);
-    }
-    for (int c = NC - 1; c < 4; ++c) out->grp[(size_t)b * 4 + c] = out->grp[(size_t)b * 4 + (NC - 2)];
-    if (pos > (int64_t)std::numeric_limits<int32_t>::max()) return "too many nonzeros";
-    out->rowptr[b + 1] = (int32_t)pos;
-    max_row = std::max(max_row, (int32_t)(pos - r0));
-  }
-  const int64_t nnz = pos;
-  out->ent.assign((size_t)nnz, kPad);
-  out->coef.assign((size_t)nnz, 0.0f);
-  if (norm || exact) out->w.assign((size_t)nnz, 0.0f);   // per-entry weights c * norm
-  const double inv = 1.0 / (double)(s * s);
-  for (int64_t i = 0; i < npix; ++i) {
-    for (int t = 0; t < pn[i]; ++t) {
-      const int32_t b = pb[(size_t)i * maxe + t];
-      const int k = pk[(size_t)i * maxe + t];
-      const int c = k == 0 ? NC - 1 : s * s - k;
-      const int64_t e = fill[(size_t)b * NC + c]++;
-      uint32_t u = (uint32_t)i;
-      if (k == 0) u |= kZero;
-      else u |= (uint32_t)(k - 1) << kKShift;
-      if (b == bop[i]) u |= kCentre;
-      out->ent[e] = u;
-      const double cf = exact ? pc[(size_t)i * maxe + t] : (double)k * inv;
-      out->coef[e] = (float)cf;
-      if (norm || exact) out->w[e] = (float)(cf * (norm ? (double)norm[i] : 1.0));
-    }
-  }
-  // Staging order of the pixel values. The clip kernel gathers each bin's
-  // values from a staged copy of the frame in which pixels are grouped by
-  // tiles of kTileH x kTileW and, inside a tile, by centre bin (then radius,
-  // then pixel index): a bin's entries then read short contiguous runs (one
-  // per tile it crosses) instead of single pixels scattered over the image. Only pixels
-  // with at least one entry are staged. Entries address their pixel by its
-  // staging position; each coefficient group is re-sorted by position.
+  // Staging order of the pixels: grouped by tiles of kTileH x kTileW and,
+  // inside a tile, by centre bin (then radius, then pixel index). Only
+  // pixels with at least one entry take part. It orders the entries inside
+  // every coefficient group of a row (below), so the entries of one bin in
+  // one tile are consecutive.
   {
     const int64_t tx = (cols + kTileW - 1) / kTileW, ty = (rows + kTileH - 1) / kTileH;
     out->tiles_x = (int32_t)tx;
@@ -376,37 +321,88 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
     out->tile_base[tx * ty] = (int32_t)out->perm_inv.size();
     out->pos_of = pos_of;
     out->npos = (int64_t)out->perm_inv.size();
-    // re-sort every group (bin, class) by staging position: the entries of
-    // one bin inside one tile then take consecutive slots of the staged row
-    std::vector<std::pair<uint32_t, int64_t>> grp_e;
-    std::vector<uint32_t> ent2;
-    std::vector<float> coef2, w2;
-    for (int32_t b = 0; b < B; ++b) {
-      for (int c = 0; c < NC; ++c) {
-        const int64_t g1 = fill[(size_t)b * NC + c], g0 = g1 - cc[(size_t)b * NC + c];
-        grp_e.clear();
-        for (int64_t e = g0; e < g1; ++e) {
-          const uint32_t u = out->ent[e];
-          const uint32_t p = (uint32_t)pos_of[u & kColMask];
-          grp_e.emplace_back(p, e);
-        }
-        std::sort(grp_e.begin(), grp_e.end());
-        ent2.resize(grp_e.size());
-        coef2.resize(grp_e.size());
-        w2.resize(grp_e.size());
-        for (size_t k = 0; k < grp_e.size(); ++k) {
-          const int64_t e = grp_e[k].second;
-          ent2[k] = out->ent[e];
-          coef2[k] = out->coef[e];
-          if (!out->w.empty()) w2[k] = out->w[e];
-        }
-        for (size_t k = 0; k < grp_e.size(); ++k) {
-          out->ent[g0 + (int64_t)k] = ent2[k];
-          out->coef[g0 + (int64_t)k] = coef2[k];
-          if (!out->w.empty()) out->w[g0 + (int64_t)k] = w2[k];
-        }
-      }
+  }
+
+  // Row layout (one row per bin): entries grouped by coefficient class,
+  // largest coefficient first (class c holds k = s*s - c sub-pixels, c = 0 ..
+  // s*s - 1), then the weight-0 centre carriers; inside a group the entries
+  // follow the staging order, so those of one staging tile form a run. Each
+  // run is padded with flagged entries to a multiple of kRunAlign (8) slots:
+  // the staging kernel, which writes a tile's runs into the frame's staged
+  // row (slot = entry), then writes whole 32-byte sectors. Groups and rows
+  // hold multiples of 8 entries, so the kernels move 4 entries per vector
+  // access and apply a class's weight once per group.
+  constexpr int64_t kRunAlign = 8;
+  const int NC = s * s + 1;                 // coefficient classes + carriers
+  struct Ent {
+    uint64_t key;   // (bin * NC + class) << 32 | staging position
+    int64_t i;      // pixel
+    int t;          // its entry
+  };
+  std::vector<Ent> all;
+  {
+    int64_t n_real = 0;
+    for (int64_t i = 0; i < npix; ++i) n_real += pn[i];
+    all.reserve((size_t)n_real);
+  }
+  for (int64_t i = 0; i < npix; ++i)
+    for (int t = 0; t < pn[i]; ++t) {
+      const int32_t b = pb[(size_t)i * maxe + t];
+      const int k = pk[(size_t)i * maxe + t];
+      const int c = k == 0 ? NC - 1 : s * s - k;
+      all.push_back({((uint64_t)((int64_t)b * NC + c) << 32) | (uint32_t)out->pos_of[i], i, t});
     }
+  std::sort(all.begin(), all.end(), [](const Ent& x, const Ent& y) { return x.key < y.key; });
+  auto tile_of = [&](int64_t i) { return (i / cols) / kTileH * (int64_t)out->tiles_x + (i % cols) / kTileW; };
+  // slots: entries and their runs' padding, row by row
+  out->rowptr.assign((size_t)B + 1, 0);
+  out->grp.assign((size_t)B * 4, 0);
+  std::vector<int64_t> slot_of_ent(all.size());
+  int64_t pos = 0;
+  int32_t max_row = 0;
+  {
+    size_t j = 0;
+    for (int32_t b = 0; b < B; ++b) {
+      const int64_t r0 = pos;
+      for (int c = 0; c < NC; ++c) {
+        const uint64_t g = (uint64_t)((int64_t)b * NC + c);
+        int64_t run_tile = -1;
+        while (j < all.size() && (all[j].key >> 32) == g) {
+          const int64_t tl = tile_of(all[j].i);
+          if (tl != run_tile) {   // a new run starts on a sector boundary
+            pos = (pos + kRunAlign - 1) / kRunAlign * kRunAlign;
+            run_tile = tl;
+          }
+          slot_of_ent[j++] = pos++;
+        }
+        pos = (pos + kRunAlign - 1) / kRunAlign * kRunAlign;
+        if (c < 4) out->grp[(size_t)b * 4 + c] = (int32_t)(pos - r0);
+      }
+      for (int c = NC - 1; c < 4; ++c) out->grp[(size_t)b * 4 + c] = out->grp[(size_t)b * 4 + (NC - 2)];
+      if (pos > (int64_t)std::numeric_limits<int32_t>::max()) return "too many nonzeros";
+      out->rowptr[b + 1] = (int32_t)pos;
+      max_row = std::max(max_row, (int32_t)(pos - r0));
+    }
+  }
+  const int64_t nnz = pos;
+  out->ent.assign((size_t)nnz, kPad);
+  out->coef.assign((size_t)nnz, 0.0f);
+  if (norm || exact) out->w.assign((size_t)nnz, 0.0f);   // per-entry weights c * norm
+  const double inv = 1.0 / (double)(s * s);
+  for (size_t j = 0; j < all.size(); ++j) {
+    const int64_t i = all[j].i;
+    const int t = all[j].t;
+    const int32_t b = pb[(size_t)i * maxe + t];
+    const int k = pk[(size_t)i * maxe + t];
+    const int64_t e = slot_of_ent[j];
+    uint32_t u = (uint32_t)i;
+    if (k == 0) u |= kZero;
+    else u |= (uint32_t)(k - 1) << kKShift;
+    if (b == bop[i]) u |= kCentre;
+    out->ent[e] = u;
+    const double cf = exact ? pc[(size_t)i * maxe + t] : (double)k * inv;
+    out->coef[e] = (float)cf;
+    if (norm || exact) out->w[e] = (float)(cf * (norm ? (double)norm[i] : 1.0));
   }
   // per entry: its pixel if the entry carries the pixel's centre bin (one
   // such entry per pixel with entries), else -1; the clip kernel marks kept
@@ -425,15 +421,21 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   // entry e's pixel value; padding slots hold NaN). The staging kernel works
   // by image tiles: each tile lists the slots of its pixels' entries in
   // ascending order with the pixel's index inside the tile (row * kTileW +
-  // column), -1 for the padding slots it fills (spread over the tiles).
+  // column), -1 for the padding slots of its runs (a run's padding follows
+  // its entries, so the tile writes whole sectors).
   {
     const int64_t tx = out->tiles_x, nt = (int64_t)out->tiles_x * out->tiles_y;
-    auto tile_of = [&](int64_t e) -> int64_t {
+    std::vector<int32_t> slot_tile((size_t)nnz, 0);
+    for (int64_t e = 0, cur = 0; e < nnz; ++e) {
       const uint32_t u = out->ent[(size_t)e];
-      if (u & kPad) return (e >> 2) % nt;
-      const int64_t i = u & kColMask, r = i / cols, c = i % cols;
-      return (r / kTileH) * tx + c / kTileW;
-    };
+      if (!(u & kPad)) {
+        const int64_t i = u & kColMask, r = i / cols, c = i % cols;
+        cur = (r / kTileH) * tx + c / kTileW;
+      }
+      slot_tile[(size_t)e] = (int32_t)cur;
+    }
+    auto tile_of = [&](int64_t e) -> int64_t { return slot_tile[(size_t)e]; };
+    (void)nt;
     out->tile_ebase.assign((size_t)nt + 1, 0);
     for (int64_t e = 0; e < nnz; ++e) out->tile_ebase[(size_t)tile_of(e) + 1] += 1;
     for (int64_t t = 0; t < nt; ++t) out->tile_ebase[(size_t)t + 1] += out->tile_ebase[(size_t)t];

@@ -30,17 +30,21 @@ RTOL = 1e-5
 PEAK_RTOL = 1e-4
 
 
-def close(a, b, rtol=RTOL, sd=None):
+MEAN_FLOOR = 1e-7
+
+
+def close(a, b, rtol=RTOL, sd=None, floor=MEAN_FLOOR):
     """|a - b| <= rtol |b|; where the bin's deviation sd is 0 the bound is
-    1e-6 max(1, |b|); with a deviation, an absolute floor of 1e-7 sd (one
-    FP32 rounding of the bin's spread) covers means that sit near zero
-    relative to their spread, which have no relative precision in FP32."""
+    1e-6 max(1, |b|); with a deviation, an absolute floor of floor * sd (by
+    default 1e-7 sd, one FP32 rounding of the bin's spread) covers means that
+    sit near zero relative to their spread, which have no relative precision
+    in FP32 (the plain mode's sums); floor=0 drops it."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     tol = rtol * np.abs(b)
     if sd is not None:
         sd = np.asarray(sd, np.float64)
-        tol = np.where(sd == 0, 1e-6 * np.maximum(1.0, np.abs(b)), tol + 1e-7 * sd)
+        tol = np.where(sd == 0, 1e-6 * np.maximum(1.0, np.abs(b)), tol + floor * sd)
     return np.abs(a - b) <= tol + 1e-30
 
 
@@ -66,12 +70,14 @@ class Frame:
         return self.W.pix[e], self.W.c[e]
 
 
-def check_clip(fr: Frame, mean, sigma, count, bounds):
+def check_clip(fr: Frame, mean, sigma, count, bounds, floor=MEAN_FLOOR):
     """Returns (number of banded bins, list of bins whose GPU stats come from a
-    different trajectory). Raises AssertionError on a mismatch."""
+    different trajectory). Raises AssertionError on a mismatch. floor: the
+    absolute floor of the mean's tolerance in deviations (see close)."""
     ref = fr.ref
     banded = ref["band"] < BAND
-    ok = close(mean, ref["mean"], sd=ref["sigma"]) & close(sigma, ref["sigma"], sd=ref["sigma"]) & (count == ref["count"])
+    ok = close(mean, ref["mean"], sd=ref["sigma"], floor=floor) & close(sigma, ref["sigma"], sd=ref["sigma"]) & \
+        (count == ref["count"])
     bad = np.flatnonzero(~ok & ~banded)
     assert bad.size == 0, (f"{bad.size} unbanded bins differ, e.g. bin {bad[0]}: gpu "
                            f"({mean[bad[0]]}, {sigma[bad[0]]}, {count[bad[0]]}) oracle "
@@ -84,8 +90,8 @@ def check_clip(fr: Frame, mean, sigma, count, bounds):
         vv = fr.sig[pix]
         sel = (vv >= L) & (vv <= H)
         mu, sd, n = oracle.moments_subset(pix, c, sel.astype(np.uint8), fr.sig, fr.norm, model=fr.model, dark=fr.dark)
-        assert close(mean[b], mu, sd=np.array(sd)) and close(sigma[b], sd, sd=np.array(sd)) and count[b] == n, \
-            (b, mean[b], mu, sigma[b], sd, count[b], n)
+        assert close(mean[b], mu, sd=np.array(sd), floor=floor) and close(sigma[b], sd, sd=np.array(sd)) and \
+            count[b] == n, (b, mean[b], mu, sigma[b], sd, count[b], n)
         moved.append((b, mu, sd))
     return int(banded.sum()), moved
 
@@ -152,9 +158,12 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3, truncated=
         return False
 
     def near_tie(i):
-        # the local maximum between two values equal up to one binary32
-        # rounding of signal / norm (Eq. 1) may go either way: the library
-        # compares the binary32 values, the oracle the FP64 quotients
+        # with a norm, the local maximum between two values equal up to one
+        # binary32 rounding of signal / norm (Eq. 1) may go either way: the
+        # library compares the binary32 values, the oracle the FP64 quotients.
+        # Without a norm both compare the same binary32 values: no excuse.
+        if fr.norm is None:
+            return False
         r0, c0 = divmod(int(i), cols)
         vi = fr.v[i]
         for r in range(r0 - h, r0 + h + 1):
@@ -180,7 +189,7 @@ def check_peaks(det, fr: Frame, peaks, excused, patch=3, min_count=3, truncated=
 
 
 def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, bounds=None, norm=None,
-                chauvenet=False, model=0, dark=0.0, interp=None):
+                chauvenet=False, model=0, dark=0.0, interp=None, floor=MEAN_FLOOR):
     """Frame f of a batch's outputs `o` (numpy arrays as returned by the
     library) against the oracle on the frame's signal. Returns (banded bins,
     bins on another trajectory, excused pixels)."""
@@ -188,7 +197,7 @@ def check_frame(det, W, sig, o, f, n_iter=5, k_clip=3.0, k_pick=3.0, kcap=None, 
                interp=interp)
     if bounds is None:
         bounds = np.tile(np.array([-np.inf, np.inf], np.float32), (W.nbins, 1))
-    nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds)
+    nb, moved = check_clip(fr, o["mean"][f], o["sigma"][f], o["count"][f], bounds, floor=floor)
     excused = check_kept(fr, o["idx"][f], o["val"][f], o["n_kept"][f], moved, capacity=kcap)
     pcap = o["peaks"].shape[1]
     peaks = o["peaks"][f][: int(o["n_peaks"][f])].copy().view(np.dtype([("idx", "<i4"), ("y", "<f4"), ("x", "<f4"),

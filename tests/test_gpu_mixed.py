@@ -49,3 +49,41 @@ def test_mixed_stream_equals_per_detector_batches():
     for s in seps:
         s.close()
     ctx.close()
+
+
+def test_mixed_stream_1m_16m_against_the_oracle():
+    """One 1M and one 16M Jungfrau-shaped float32 frame (600 / 2000 bins, no
+    splitting), with a 4M frame between them, in one mixed call: the 1M and
+    16M frames' profiles, kept pixels and peaks against the FP64 oracle."""
+    import oracle
+    from parity import check_frame
+    ctx = Context(0)
+    dets = [synth.det_jf1m(nbins=600), synth.det_jf4m(split=1, nbins=1000), synth.det_jf16m(nbins=2000)]
+    masks = [d.mask() for d in dets]
+    seps = [Separator.from_detector(d, mask=m, context=ctx) for d, m in zip(dets, masks)]
+    pattern = [0, 1, 2]
+    frames, host = [], []
+    for g, d in enumerate(pattern):
+        fr = synth.frames(dets[d], synth.spec_mixed(seed=70 + g, hit_rate=1.0), g, 1, mask=masks[d])[0]
+        host.append(fr)
+        frames.append((d, torch.from_numpy(fr[0]).cuda()))
+    kcap, pcap = 1 << 20, 1 << 15
+    out = process_mixed(seps, frames, kcap, pcap)
+    torch.cuda.synchronize()
+    assert seps[0].device_status() == 0
+    rows = out["row_off"]
+    for g in (0, 2):
+        d = pattern[g]
+        r0, r1 = rows[g], rows[g + 1]
+        o = {"mean": out["mean"][r0:r1].cpu().numpy()[None], "sigma": out["sigma"][r0:r1].cpu().numpy()[None],
+             "count": out["count"][r0:r1].cpu().numpy()[None],
+             "idx": out["idx"][g:g + 1].cpu().numpy(), "val": out["val"][g:g + 1].cpu().numpy(),
+             "n_kept": out["n_kept"][g:g + 1].cpu().numpy(), "peaks": out["peaks"][g:g + 1].cpu().numpy(),
+             "n_peaks": out["n_peaks"][g:g + 1].cpu().numpy()}
+        # the final sets' bounds, from the same kernel on the frame alone
+        bnd = seps[d].integrate_clip(frames[g][1][None], bounds=True)["bounds"].cpu().numpy()
+        W = oracle.weights(dets[d], masks[d])
+        check_frame(dets[d], W, host[g][0], o, 0, kcap=kcap, bounds=bnd[0])
+    for s in seps:
+        s.close()
+    ctx.close()

@@ -57,10 +57,30 @@ def test_standalone_calls_equal_the_batch():
     assert np.array_equal(ic["mean"].cpu().numpy(), o["mean"])
     assert np.array_equal(ic["sigma"].cpu().numpy(), o["sigma"])
     # the standalone sparsify takes float32 profiles: its thresholds may differ
-    # from the fused ones by a rounding of the mean, hence by band pixels only
-    nk = sp["n_kept"].cpu().numpy()
-    assert np.all(np.abs(nk - o["n_kept"]) <= 2)
-    assert np.all(np.abs(pk["n_peaks"].cpu().numpy() - o["n_peaks"]) <= 1)
+    # from the fused ones (rounded from the extended mean) by a rounding of
+    # the mean, hence only at pixels within the band of their threshold
+    W = oracle.weights(det)
+    bop = W.bin_of_pixel
+    mean, sigma = o["mean"], o["sigma"]
+    sidx, snk = sp["idx"].cpu().numpy(), sp["n_kept"].cpu().numpy()
+    pks = pk["peaks"].cpu().numpy()
+    npk = pk["n_peaks"].cpu().numpy()
+    for f in range(3):
+        a = o["idx"][f][: o["n_kept"][f]]
+        b = sidx[f][: snk[f]]
+        diff = np.setxor1d(a, b)
+        v = fr[f].reshape(-1).astype(np.float64)
+        thr = (mean[f] + 3.0 * sigma[f]).astype(np.float64)[bop[diff]]
+        assert np.all(np.abs(v[diff] - thr) <= 1e-5 * np.abs(thr)), (f, diff)
+        # peaks differ only where a differing kept pixel lies in the patch
+        ga = peaks_to_numpy(torch.from_numpy(o["peaks"][f]), o["n_peaks"][f])["idx"]
+        gb = peaks_to_numpy(torch.from_numpy(pks[f]), npk[f])["idx"]
+        near = set()
+        for i in diff:
+            r0, c0 = divmod(int(i), det.cols)
+            near.update((r0 + dr) * det.cols + c0 + dc for dr in (-1, 0, 1) for dc in (-1, 0, 1))
+        for i in np.setxor1d(ga, gb):
+            assert int(i) in near, (f, i)
 
 
 def test_graph_replay_is_deterministic():
@@ -90,8 +110,11 @@ def jf_small():
     return det, mask, cal, fr, W
 
 
-@pytest.mark.parametrize("precision", [SEP_PREC_DWORD, SEP_PREC_FP64MERGE, SEP_PREC_KAHAN])
-def test_jungfrau_raw_split_parity(jf_small, precision):
+# the compensated and FP64-merged modes meet the relative tolerance without
+# the mean's absolute floor; the plain mode (FP32 sums throughout) keeps it
+@pytest.mark.parametrize("precision,floor", [(SEP_PREC_DWORD, 0.0), (SEP_PREC_FP64MERGE, 0.0), (SEP_PREC_KAHAN, 0.0),
+                                             (SEP_PREC_PLAIN, 1e-7)])
+def test_jungfrau_raw_split_parity(jf_small, precision, floor):
     det, mask, cal, fr, W = jf_small
     sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)
     kcap = det.npix // 4
@@ -100,20 +123,9 @@ def test_jungfrau_raw_split_parity(jf_small, precision):
     tot_band = 0
     for f in range(fr.shape[0]):
         sig = oracle.jf_photons(fr[f], cal[0], cal[1])
-        nb, nm, ne = check_frame(det, W, sig, o, f, kcap=kcap, bounds=bnd[f])
+        nb, nm, ne = check_frame(det, W, sig, o, f, kcap=kcap, bounds=bnd[f], floor=floor)
         tot_band += nb
     assert sep.device_status() == 0
-
-
-def test_plain_precision_error_is_reported_not_hidden(jf_small):
-    det, mask, cal, fr, W = jf_small
-    sep = Separator.from_detector(det, mask=mask, calib=cal, precision=SEP_PREC_PLAIN)
-    o, _ = run_batch(sep, fr[:2], det.npix // 4, 20000)
-    sig = oracle.jf_photons(fr[0], cal[0], cal[1])
-    ref = oracle.integrate_clip(W, sig)
-    ok = ref["count"] > 0
-    rel = np.abs(o["mean"][0][ok] - ref["mean"][ok]) / np.abs(ref["mean"][ok])
-    assert np.median(rel) < 1e-4
 
 
 def test_correction_bit_exact_all_raw_codes():
@@ -137,6 +149,52 @@ def test_correction_bit_exact_all_raw_codes():
     got = sp["val"][0].cpu().numpy()
     want = oracle.jf_photons(raw[0], ped, gain)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def _adversarial_gains():
+    """Level-0 gains where a division by a correctly rounded reciprocal plus
+    one correction step is most exposed: significands of all ones and just
+    above a power of two, exact powers of two, both signs, across exponents
+    up to and beyond the range the shortcut accepts (2^-100 .. 2^100)."""
+    one_less = np.nextafter(np.float32(2), np.float32(0))     # 1.11..1b
+    one_more = np.nextafter(np.float32(1), np.float32(2))     # 1.00..01b
+    g = []
+    for e in (-101, -100, -60, -7, -1, 0, 1, 5, 40, 99, 100):
+        for m in (np.float32(1), one_less, one_more, np.float32(1.5), np.float32(40) / np.float32(32)):
+            v = np.ldexp(m, e).astype(np.float32)
+            g += [v, -v]
+    return np.array(g, np.float32)
+
+
+def test_level0_division_adversarial_gains():
+    """The level-0 quotient RN((adc - ped) / gain) of the staging kernel,
+    bit for bit against the oracle's binary32 definition, on every 14-bit
+    ADC value and adversarial gains and pedestals (integers, fractions close
+    to the ADC values, tiny, zero)."""
+    rows, cols = 128, 128
+    n = rows * cols
+    det = synth.Detector("adv", rows, cols, dist_m=0.1, center_px=(64.3, 60.7), nbins=8, split=2)
+    raw = np.arange(n, dtype=np.uint32).astype(np.uint16)          # code 0: level 0, adc = 0 .. 16383
+    adc = raw.astype(np.float32)
+    rng = np.random.default_rng(5)
+    peds = [np.float32(1500.25) + rng.normal(0, 50, n).astype(np.float32),
+            np.round(rng.uniform(0, 16000, n)).astype(np.float32),
+            adc - np.float32(2.0 ** -10),                          # tiny differences
+            np.full(n, np.float32(1e-30)), np.zeros(n, np.float32)]
+    lv = np.ones(n, np.float32)
+    for gi, g0 in enumerate(_adversarial_gains()):
+        ped0 = peds[gi % len(peds)]
+        ped = np.stack([ped0, lv * 14000, lv * 15000]).astype(np.float32)
+        gain = np.stack([np.full(n, g0, np.float32), lv * -1.5, lv * -0.1]).astype(np.float32)
+        sep = Separator.from_detector(det, calib=(ped, gain))
+        got = sep.correct(torch.from_numpy(raw.astype(np.int16)[None]).cuda()).cpu().numpy()[0]
+        want = oracle.jf_photons(raw, ped, gain)
+        staged = ~np.isnan(got)
+        assert staged.sum() > 0.9 * n
+        a, b = got[staged], want[staged]
+        same = (a.view(np.uint32) == b.view(np.uint32)) | (np.isnan(a) & np.isnan(b))
+        assert same.all(), (g0, np.flatnonzero(~same)[:5], a[~same][:5], b[~same][:5])
+        sep.close()
 
 
 def test_staged_correction_bit_exact_all_raw_codes():

@@ -143,7 +143,12 @@ def _row_sample(ex, b, step_of):
     col, coef = ex["col"][r0:r1], ex["coef"][r0:r1]
     ng = (r1 - r0) // 4
     step = step_of(ng)
-    gcls = coef[0::4]                       # a group's class: its first entry's coefficient
+    # a group's class: the coefficient of its first matrix entry; a group of
+    # padding slots only (col -1) lies inside the class of the run before it
+    gcls = np.zeros(ng, np.float32)
+    for q in range(ng):
+        real = np.flatnonzero(col[4 * q:4 * q + 4] >= 0)
+        gcls[q] = coef[4 * q + real[0]] if real.size else (gcls[q - 1] if q else 0.0)
     keep = np.zeros(r1 - r0, bool)
     g = 0
     while g < ng:
