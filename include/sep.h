@@ -20,6 +20,8 @@
  *    wait that gave up) are OR-ed into the context's device status word,
  *    read and cleared with sep_get_device_status.
  *  - sep_last_error(ctx) describes the last host-side failure on ctx.
+ *  - Calls run on their context's device and leave the calling thread's
+ *    current CUDA device as they found it.
  *  - The library never exits, aborts or traps.
  *  - Not thread-safe per context: calls on one sep_ctx must not overlap in
  *    host threads.
@@ -233,6 +235,30 @@ sep_status sep_csr_interp(const sep_csr* csr, int32_t* lower_bin, float* weight)
  * bin_of_pixel [npix] (-1 = masked), bin_centers [nbins]. */
 sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, float* coef,
                           int32_t* bin_of_pixel, float* bin_centers);
+/* Host-side check of an integration matrix in the layout sep_csr_export
+ * writes (Section 2.2: one CSR row per radial bin), for matrices built or
+ * edited outside the library. No device call; nothing is launched.
+ *  rowptr [nbins+1]: rowptr[0] = 0, non-decreasing, rowptr[nbins] = nnz.
+ *  col [nnz]: pixel index in [0, npix), or -1 for a padding slot.
+ *  coef [nnz]: finite, in [0, 1]; 0 on padding slots; the coefficients of
+ *      one pixel over all bins sum to at most 1 (its area, up to 1e-6).
+ *  bin_of_pixel [npix] (may be NULL): in [-1, nbins).
+ *  calib_npix: the pixel count of the calibration to be used with the
+ *      matrix (must equal npix), or -1 for no calibration.
+ *  msg [msg_len] (may be NULL): receives the first violation, or "".
+ * Returns SEP_OK, or SEP_ERR_ARG at the first violation (non-monotone
+ * row pointer, column, coefficient or bin out of range, calibration of
+ * another size). */
+sep_status sep_csr_validate(const int32_t* rowptr, const int32_t* col, const float* coef,
+                            const int32_t* bin_of_pixel, int32_t nbins, int64_t nnz, int64_t npix,
+                            int64_t calib_npix, char* msg, int32_t msg_len);
+/* The same checks on a built matrix handle (its host copy, plus the tables
+ * the kernels follow: class ends, centre entries, staging scatter lists)
+ * and, when calib is not NULL, that the calibration covers the detector
+ * and belongs to the matrix's context. sep_build_csr runs the matrix checks
+ * itself before any upload. SEP_OK or SEP_ERR_ARG / SEP_ERR_STATE (reason
+ * in sep_last_error of the matrix's context). Host only. */
+sep_status sep_csr_check(const sep_csr* csr, const sep_calib* calib);
 
 /* ---- detector calibration (Section 1.2) ---------------------------------- */
 /*
@@ -565,19 +591,18 @@ sep_status sep_model_load(sep_ctx* ctx, const char* path, sep_model** out);
  * sep_sparsify with no allocation during the call (the paper has no
  * counterpart; this is an interface for callers, not part of the method).
  * sep_sparsify grows context-owned scratch with cudaMalloc when a batch needs
- * more; callers that must not allocate at call time (code being recorded into
- * a CUDA graph, real-time acquisition threads, processes whose device memory
- * is fixed after start-up) use this variant instead. Its scratch is one
- * static 16 MiB device array in the library, which every GPU that loads the
- * library holds until exit. Arguments, outputs and results are those of
- * sep_sparsify.
+ * more; callers that must not allocate at call time (real-time acquisition
+ * threads, processes whose device memory is fixed after start-up) use this
+ * variant instead. Its scratch is one static 16 MiB device array in the
+ * library, which every GPU that loads the library holds until exit.
+ * Arguments, their checks (the same refusals), outputs and results are those
+ * of sep_sparsify.
  *  - Limit: n_frames * (bitmap bytes ceil(npix/32)*4 rounded up to 32, plus
  *    4 * nbins, plus 4 per 8192 bitmap words) must fit 16 MiB (about 28
  *    Jungfrau-4M frames, about 1900 frames of 256 x 256); larger batches
  *    return SEP_ERR_ARG before any launch (split the batch).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, no allocation); make that first call before any
- *    stream capture.
+ *    (cudaGetSymbolAddress, no allocation).
  *  - All calls share the array, which keeps the last call's contents; calls
  *    that overlap on the GPU (other streams or host threads) race on it.
  */

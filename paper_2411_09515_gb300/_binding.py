@@ -36,7 +36,8 @@ EXPORTS = ["sep_version", "sep_ctx_create", "sep_ctx_destroy", "sep_last_error",
            "sep_model_create", "sep_model_destroy", "sep_model_params", "sep_model_norm", "sep_mlp_forward",
            "sep_mlp_loss_grad", "sep_surrogate_train", "sep_model_save", "sep_model_load", "sep_csr_attach_model",
            "sep_surrogate_record", "sep_surrogate_prepare", "sep_surrogate_stats", "sep_csr_staging", "sep_correct",
-           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames", "sep_csr_interp", "sep_clip_stats"]
+           "sep_process_host", "sep_densify", "sep_veto", "sep_compact_frames", "sep_csr_interp", "sep_clip_stats",
+           "sep_csr_validate", "sep_csr_check"]
 
 SEP_MLP_IN, SEP_MLP_HIDDEN, SEP_MLP_OUT, SEP_MLP_PARAMS, SEP_MLP_NORM = 20, 64, 2, 5634, 44
 SEP_CLIP_STATS = 8
@@ -98,6 +99,9 @@ def lib():
     L.sep_csr_info.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     L.sep_csr_export.argtypes = [_vp] * 6
+    L.sep_csr_validate.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_char_p,
+                                   C.c_int32]
+    L.sep_csr_check.argtypes = [_vp, _vp]
     L.sep_calib_create.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(_vp)]
     L.sep_calib_destroy.argtypes = [_vp]
     L.sep_calib_destroy.restype = None
@@ -254,6 +258,25 @@ def sep_csr_export(csr):
     if st != SEP_OK:
         raise SepError(st, "sep_csr_export")
     return {"rowptr": rowptr, "col": col, "coef": coef, "bin_of_pixel": bop, "bin_centers": centers, **info}
+
+
+def sep_csr_validate(rowptr, col, coef, bin_of_pixel, npix, calib_npix=-1):
+    """Host-side check of a matrix in the export layout: (status, reason)."""
+    rp = np.ascontiguousarray(rowptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32)
+    cf = np.ascontiguousarray(coef, np.float32)
+    bp = None if bin_of_pixel is None else np.ascontiguousarray(bin_of_pixel, np.int32)
+    if cl.size != cf.size:
+        raise ValueError("col and coef differ in size")
+    msg = C.create_string_buffer(256)
+    st = lib().sep_csr_validate(_ptr(rp), _ptr(cl), _ptr(cf), _ptr(bp), rp.size - 1, cl.size, int(npix),
+                                int(calib_npix), msg, len(msg))
+    return st, msg.value.decode()
+
+
+def sep_csr_check(csr, calib=None):
+    """The matrix checks on a built handle (and the calibration's size)."""
+    return lib().sep_csr_check(csr, calib)
 
 
 def sep_calib_create(ctx, csr, ped, gain):

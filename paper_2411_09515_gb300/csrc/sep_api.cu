@@ -346,11 +346,20 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
 
 }  // namespace
 
+namespace sep {
+sep_status check_call(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames, int32_t dtype,
+                      int32_t n_frames, const sep_params* params) {
+  return check_common(ctx, csr, calib, frames, dtype, n_frames, params);
+}
+}  // namespace sep
+
 extern "C" {
 
 const char* sep_version(void) { return SEP_VERSION_STRING; }
 
 sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!out) return SEP_ERR_ARG;
   *out = nullptr;
   int n = 0;
@@ -418,6 +427,8 @@ void sep_ctx_destroy(sep_ctx* ctx) {
 const char* sep_last_error(const sep_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* status_out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx || !status_out) return SEP_ERR_ARG;
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
   int32_t v = 0;
@@ -430,6 +441,8 @@ sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* statu
 
 sep_status sep_build_csr(sep_ctx* ctx, const sep_geometry* geom, const uint8_t* mask_host, const float* norm_host,
                          sep_csr** out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!geom || !out) return fail(ctx, SEP_ERR_ARG, "geometry and out must not be NULL");
   *out = nullptr;
   sep_csr* c = new (std::nothrow) sep_csr();
@@ -547,8 +560,42 @@ sep_status sep_csr_export(const sep_csr* csr, int32_t* rowptr, int32_t* col, flo
   return SEP_OK;
 }
 
+sep_status sep_csr_validate(const int32_t* rowptr, const int32_t* col, const float* coef, const int32_t* bin_of_pixel,
+                            int32_t nbins, int64_t nnz, int64_t npix, int64_t calib_npix, char* msg, int32_t msg_len) {
+  std::string why;
+  try {
+    why = sep::validate_matrix(rowptr, col, coef, bin_of_pixel, nbins, nnz, npix);
+  } catch (const std::bad_alloc&) {
+    why = "host allocation failed";
+  }
+  if (why.empty() && calib_npix >= 0 && calib_npix != npix) why = "calibration covers another number of pixels";
+  if (msg && msg_len > 0) {
+    const size_t n = std::min(why.size(), (size_t)msg_len - 1);
+    memcpy(msg, why.data(), n);
+    msg[n] = 0;
+  }
+  return why.empty() ? SEP_OK : SEP_ERR_ARG;
+}
+
+sep_status sep_csr_check(const sep_csr* csr, const sep_calib* calib) {
+  if (!csr) return SEP_ERR_ARG;
+  sep_ctx* ctx = csr->ctx;
+  std::string why;
+  try {
+    why = sep::validate_host_csr(csr->h);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, SEP_ERR_OOM, "host allocation failed");
+  }
+  if (!why.empty()) return fail(ctx, SEP_ERR_ARG, why);
+  if (calib && calib->npix != csr->npix) return fail(ctx, SEP_ERR_ARG, "calibration size differs from the detector");
+  if (calib && ctx && calib->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "calibration belongs to another context");
+  return SEP_OK;
+}
+
 sep_status sep_calib_create(sep_ctx* ctx, const sep_csr* csr, const float* ped_host, const float* gain_host,
                             sep_calib** out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (!csr || !ped_host || !gain_host || !out) return fail(ctx, SEP_ERR_ARG, "NULL argument");
   if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr belongs to another context");
@@ -581,6 +628,8 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
                               int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                               float* sigma_dev, int32_t* count_dev, float* bounds_dev, int32_t* iters_dev,
                               sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (n_frames > 0 && (!mean_dev || !sigma_dev || !count_dev)) return fail(ctx, SEP_ERR_ARG, "NULL output");
@@ -598,6 +647,8 @@ sep_status sep_integrate_clip(sep_ctx* ctx, const sep_csr* csr, const sep_calib*
 
 sep_status sep_correct(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                        int32_t dtype, int32_t n_frames, float* out_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_params p{};
   p.n_iter = 0;
   p.k_clip = 1.0f;
@@ -622,6 +673,8 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
                                 int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                                 float* sigma_dev, int32_t* count_dev, float* feat_dev, float* target_dev,
                                 sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (params->surrogate != 0) return fail(ctx, SEP_ERR_ARG, "recording runs the plain loop: surrogate must be 0");
@@ -644,6 +697,8 @@ sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_cali
 
 sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_back, int32_t reset,
                                sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
   unsigned long long v[2] = {0, 0};
@@ -657,6 +712,8 @@ sep_status sep_surrogate_stats(sep_ctx* ctx, uint64_t* accepted, uint64_t* fell_
 }
 
 sep_status sep_clip_stats(sep_ctx* ctx, int32_t enable, uint64_t* counts, int32_t reset, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (enable < -1 || enable > 1) return fail(ctx, SEP_ERR_ARG, "enable must be -1, 0 or 1");
   SEP_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -684,6 +741,8 @@ sep_status sep_sparsify(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
                         int32_t dtype, int32_t n_frames, const sep_params* params, const float* mean_dev,
                         const float* sigma_dev, int32_t* idx_dev, float* val_dev, int64_t capacity,
                         int32_t* n_kept_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
@@ -717,6 +776,8 @@ sep_status sep_peakfind(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib
                         const float* sigma_dev, const int32_t* idx_dev, const int32_t* n_kept_dev,
                         int64_t kept_capacity, sep_peak* peaks_dev, int64_t capacity, int32_t* n_peaks_dev,
                         sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (capacity < 0 || kept_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
@@ -746,6 +807,8 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
                        const float* sigma_dev, const int32_t* idx_dev, const float* val_dev,
                        int64_t kept_capacity, const int32_t* n_kept_dev, const float* noise_dev, float fill,
                        int32_t interpolate, float* out_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (!csr) return fail(ctx, SEP_ERR_ARG, "NULL matrix");
   if (csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "matrix belongs to another context");
@@ -766,6 +829,8 @@ sep_status sep_densify(sep_ctx* ctx, const sep_csr* csr, int32_t n_frames, const
 
 sep_status sep_veto(sep_ctx* ctx, int32_t n_frames, const int32_t* n_peaks_dev, int32_t min_peaks,
                     int32_t* frame_list_dev, int32_t* n_pass_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (n_frames < 0 || n_frames > (1 << 24) || min_peaks < 0) return fail(ctx, SEP_ERR_ARG, "n_frames or min_peaks");
   if (!n_pass_dev || (n_frames > 0 && (!n_peaks_dev || !frame_list_dev))) return fail(ctx, SEP_ERR_ARG, "NULL argument");
@@ -778,6 +843,8 @@ sep_status sep_veto(sep_ctx* ctx, int32_t n_frames, const int32_t* n_peaks_dev, 
 sep_status sep_compact_frames(sep_ctx* ctx, int32_t n_frames, const int32_t* frame_list_dev,
                               const int32_t* n_pass_dev, int64_t row_bytes, const void* src_dev, void* dst_dev,
                               sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (n_frames < 0 || n_frames > SEP_MAX_FRAMES || row_bytes < 0 || row_bytes % 4)
     return fail(ctx, SEP_ERR_ARG, "n_frames or row_bytes");
@@ -798,6 +865,8 @@ sep_status sep_process_batch(sep_ctx* ctx, const sep_csr* csr, const sep_calib* 
                              float* sigma_dev, int32_t* count_dev, int32_t* idx_dev, float* val_dev,
                              int64_t kept_capacity, int32_t* n_kept_dev, sep_peak* peaks_dev, int64_t peak_capacity,
                              int32_t* n_peaks_dev, int32_t use_graph, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
@@ -906,6 +975,8 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
                             float* sigma_host, int32_t* count_host, int32_t* idx_host, float* val_host,
                             int64_t kept_capacity, int32_t* n_kept_host, sep_peak* peaks_host,
                             int64_t peak_capacity, int32_t* n_peaks_host, int32_t chunk_frames, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_host, dtype, n_frames, params, true);
   if (st != SEP_OK) return st;
   if (kept_capacity < 0 || peak_capacity < 0) return fail(ctx, SEP_ERR_ARG, "capacity < 0");
@@ -1006,6 +1077,8 @@ sep_status sep_process_host(sep_ctx* ctx, const sep_csr* csr, const sep_calib* c
 
 sep_status sep_csr_set_plan(sep_ctx* ctx, sep_csr* csr, int32_t n_classes, const int32_t* thresholds,
                             const int32_t* tpb) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (!csr || csr->ctx != ctx) return fail(ctx, SEP_ERR_STATE, "csr missing or from another context");
   if (!tpb || (n_classes > 1 && !thresholds)) return fail(ctx, SEP_ERR_ARG, "NULL argument");
@@ -1031,6 +1104,8 @@ sep_status sep_csr_get_plan(const sep_csr* csr, int32_t* n_classes, int32_t* thr
 sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, const void* frames_dev, int32_t dtype,
                         int32_t n_frames, const sep_params* params, const char* cache_path, float* best_ms,
                         sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   sep_status st = check_common(ctx, csr, calib, frames_dev, dtype, n_frames, params);
   if (st != SEP_OK) return st;
   if (n_frames < 1) return fail(ctx, SEP_ERR_ARG, "autotuning needs at least one sample frame");
@@ -1150,6 +1225,8 @@ sep_status sep_process_mixed(sep_ctx* ctx, int32_t n_det, sep_csr* const* csrs, 
                              int32_t* idx_dev, float* val_dev, int64_t kept_capacity, int32_t* n_kept_dev,
                              sep_peak* peaks_dev, int64_t peak_capacity, int32_t* n_peaks_dev, int32_t use_graph,
                              sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   if (n_det < 1 || n_det > 4 || !csrs) return fail(ctx, SEP_ERR_ARG, "1 to 4 detectors");
   if (n_frames < 0 || n_frames > SEP_MAX_FRAMES || (n_frames > 0 && !frames))

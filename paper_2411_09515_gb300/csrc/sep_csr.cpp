@@ -463,7 +463,86 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
   out->bop.swap(bop);
   out->centers.resize(B);
   for (int32_t b = 0; b < B; ++b) out->centers[b] = (float)(lo + ((double)b + 0.5) * (hi - lo) / (double)B);
+  // a matrix the kernels cannot follow safely never leaves the host
+  const std::string why = validate_host_csr(*out);
+  return why.empty() ? why : "internal matrix check failed: " + why;
+}
+
+
+// Matrix in the export layout (Section 2.2's CSR: rows are bins; col -1 marks
+// a padding slot). Every index the kernels follow is checked against the
+// array it indexes; the first violation is returned.
+std::string validate_matrix(const int32_t* rowptr, const int32_t* col, const float* coef, const int32_t* bop,
+                            int32_t nbins, int64_t nnz, int64_t npix) {
+  auto at = [](const char* what, int64_t i) { return std::string(what) + " at " + std::to_string(i); };
+  if (nbins <= 0) return "nbins must be > 0";
+  if (nnz < 0 || npix <= 0) return "nnz must be >= 0 and npix > 0";
+  if (!rowptr) return "rowptr is NULL";
+  if (nnz > 0 && (!col || !coef)) return "col / coef is NULL";
+  if (rowptr[0] != 0) return "rowptr[0] != 0";
+  for (int32_t b = 0; b < nbins; ++b)
+    if (rowptr[b + 1] < rowptr[b]) return at("rowptr decreases (non-monotone row pointer) at bin", b);
+  if ((int64_t)rowptr[nbins] != nnz) return "rowptr[nbins] differs from nnz";
+  // coefficients of one pixel over all bins sum to its area share, at most 1
+  std::vector<double> area((size_t)npix, 0.0);
+  for (int64_t e = 0; e < nnz; ++e) {
+    const int32_t c = col[e];
+    const float w = coef[e];
+    if (c < -1 || (int64_t)c >= npix) return at("column out of range [-1, npix) at entry", e);
+    if (!(w >= 0.0f && w <= 1.0f)) return at("coefficient outside [0, 1] at entry", e);
+    if (c == -1) {
+      if (w != 0.0f) return at("padding slot with a nonzero coefficient at entry", e);
+      continue;
+    }
+    area[(size_t)c] += w;
+  }
+  for (int64_t i = 0; i < npix; ++i)
+    if (area[(size_t)i] > 1.0 + 1e-6) return at("coefficients of a pixel sum above 1 at pixel", i);
+  if (bop)
+    for (int64_t i = 0; i < npix; ++i)
+      if (bop[i] < -1 || bop[i] >= nbins) return at("bin_of_pixel out of range [-1, nbins) at pixel", i);
   return std::string();
 }
 
+// The packed layout the kernels read: the matrix checks above on its
+// exported view, then the kernel-side tables (class ends, centre entries,
+// staging tables).
+std::string validate_host_csr(const HostCsr& h) {
+  const int64_t npix = (int64_t)h.rows * h.cols, nnz = (int64_t)h.ent.size();
+  if ((int64_t)h.rowptr.size() != (int64_t)h.nbins + 1) return "rowptr size differs from nbins + 1";
+  if ((int64_t)h.coef.size() != nnz || (int64_t)h.cpix.size() != nnz) return "entry tables differ in size";
+  if ((int64_t)h.bop.size() != npix) return "bin_of_pixel size differs from npix";
+  std::vector<int32_t> col((size_t)nnz);
+  for (int64_t e = 0; e < nnz; ++e) {
+    const uint32_t u = h.ent[(size_t)e];
+    col[(size_t)e] = (u & kPad) ? -1 : (int32_t)(u & kColMask);
+  }
+  std::string why = validate_matrix(h.rowptr.data(), col.data(), h.coef.data(), h.bop.data(), h.nbins, nnz, npix);
+  if (!why.empty()) return why;
+  if ((int64_t)h.grp.size() != 4 * (int64_t)h.nbins) return "class table size differs from 4 nbins";
+  for (int32_t b = 0; b < h.nbins; ++b) {
+    const int32_t n = h.rowptr[b + 1] - h.rowptr[b];
+    if (n % 4) return "row length not a multiple of 4 at bin " + std::to_string(b);
+    int32_t prev = 0;
+    for (int c = 0; c < 4; ++c) {
+      const int32_t g = h.grp[(size_t)b * 4 + c];
+      if (g < prev || g > n || g % 4) return "class ends out of order at bin " + std::to_string(b);
+      prev = g;
+    }
+  }
+  for (int64_t e = 0; e < nnz; ++e)
+    if (h.cpix[(size_t)e] < -1 || h.cpix[(size_t)e] >= npix) return "centre entry pixel out of range at " + std::to_string(e);
+  if ((int64_t)h.slot_of.size() != npix) return "centre slot table size differs from npix";
+  for (int64_t i = 0; i < npix; ++i)
+    if (h.slot_of[(size_t)i] < -1 || h.slot_of[(size_t)i] >= nnz) return "centre slot out of range at pixel " + std::to_string(i);
+  if (h.tile_ebase.empty() || h.tile_ebase.front() != 0 || (int64_t)h.tile_ebase.back() * 2 != (int64_t)h.tile_sc.size())
+    return "staging scatter table bounds";
+  for (size_t t = 0; t + 1 < h.tile_ebase.size(); ++t)
+    if (h.tile_ebase[t + 1] < h.tile_ebase[t]) return "staging scatter table decreases at tile " + std::to_string(t);
+  for (size_t k = 0; k < h.tile_sc.size(); k += 2) {
+    if (h.tile_sc[k] < 0 || h.tile_sc[k] >= nnz) return "staging slot out of range";
+    if (h.tile_sc[k + 1] < -1 || h.tile_sc[k + 1] >= kTileH * kTileW) return "staging tile index out of range";
+  }
+  return std::string();
+}
 }  // namespace sep

@@ -10,6 +10,7 @@
 #include <tuple>
 #include <vector>
 
+#include "nvtx3/nvToolsExt.h"
 #include "sep.h"
 
 // ---- packed CSR entry ---------------------------------------------------
@@ -20,6 +21,32 @@
 //   bit  28      zero coefficient: the entry exists only to carry bit 27
 //   bit  29      padding (no pixel): groups are padded to 4 entries
 namespace sep {
+// Restores the calling thread's current device when a C-ABI entry point
+// returns: entry points select their context's device for their own calls
+// and leave the caller's selection as they found it.
+struct DeviceGuard {
+  int dev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (dev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != dev) cudaSetDevice(dev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// An NVTX range named after the C-ABI entry point for the duration of the
+// call (a profiler shows each library call on the host timeline; without a
+// tool attached a push and a pop cost a few nanoseconds).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 constexpr uint32_t kColBits = 25;
 constexpr uint32_t kColMask = (1u << kColBits) - 1u;
 constexpr uint32_t kKShift = 25;
@@ -60,6 +87,11 @@ constexpr int kTileH = 32, kTileW = 32;   // staging tiles (rows x columns)
 
 // Returns an empty string on success, else the reason.
 std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const float* norm, HostCsr* out);
+// Checks of a matrix in the export layout (sep_csr_validate) and of the
+// packed layout the kernels read; empty on success, else the first violation.
+std::string validate_matrix(const int32_t* rowptr, const int32_t* col, const float* coef, const int32_t* bop,
+                            int32_t nbins, int64_t nnz, int64_t npix);
+std::string validate_host_csr(const HostCsr& h);
 
 // ---- kernel launch parameters -------------------------------------------
 struct ClipArgs {
@@ -190,6 +222,12 @@ cudaError_t launch_peaks(const PixArgs& p, int32_t n_frames, int32_t nbins, cons
                          const int32_t* n_kept, int64_t kcap, int32_t patch, int32_t min_count,
                          sep_peak* peaks, int64_t pcap, int32_t* n_peaks, int32_t* scratch, int32_t* status,
                          cudaStream_t s);
+// The argument and parameter checks every batch entry point runs (context,
+// matrix, calibration, frames, dtype, frame count, sep_params); on success
+// the context's device is current.
+sep_status check_call(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames, int32_t dtype,
+                      int32_t n_frames, const sep_params* params);
+
 }  // namespace sep
 
 // ---- handles --------------------------------------------------------------

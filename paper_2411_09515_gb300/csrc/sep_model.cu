@@ -69,6 +69,8 @@ sep_status upload_params(sep_model* m, const float* host) {
 extern "C" {
 
 sep_status sep_model_create(sep_ctx* ctx, uint64_t seed, sep_model** out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx || !out) return SEP_ERR_ARG;
   *out = nullptr;
   MCUDA(ctx, cudaSetDevice(ctx->device));
@@ -116,6 +118,8 @@ void sep_model_destroy(sep_model* m) {
 }
 
 sep_status sep_model_params(sep_model* m, float* get_host, const float* set_host) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m) return SEP_ERR_ARG;
   MCUDA(m->ctx, cudaSetDevice(m->ctx->device));
   if (get_host) MCUDA(m->ctx, cudaMemcpy(get_host, m->d_params, sep::kNParams * 4, cudaMemcpyDeviceToHost));
@@ -124,6 +128,8 @@ sep_status sep_model_params(sep_model* m, float* get_host, const float* set_host
 }
 
 sep_status sep_model_norm(sep_model* m, float* get_host, const float* set_host) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m) return SEP_ERR_ARG;
   if (get_host) memcpy(get_host, m->norm, sizeof(m->norm));
   if (set_host) {
@@ -137,6 +143,8 @@ sep_status sep_model_norm(sep_model* m, float* get_host, const float* set_host) 
 }
 
 sep_status sep_mlp_forward(sep_model* m, const float* x_dev, int64_t n, float* y_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m || n < 0 || (n > 0 && (!x_dev || !y_dev))) return SEP_ERR_ARG;
   MCUDA(m->ctx, cudaSetDevice(m->ctx->device));
   MCUDA(m->ctx, sep::launch_mlp_forward(m->d_wbf, x_dev, n, y_dev, (cudaStream_t)stream));
@@ -145,6 +153,8 @@ sep_status sep_mlp_forward(sep_model* m, const float* x_dev, int64_t n, float* y
 
 sep_status sep_mlp_loss_grad(sep_model* m, const float* x_dev, const float* t_dev, int64_t n, float* grad_dev,
                              float* loss_dev, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m || n < 1 || !x_dev || !t_dev || !grad_dev || !loss_dev) return SEP_ERR_ARG;
   MCUDA(m->ctx, cudaSetDevice(m->ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -156,6 +166,8 @@ sep_status sep_mlp_loss_grad(sep_model* m, const float* x_dev, const float* t_de
 
 sep_status sep_surrogate_train(sep_model* m, const float* x_dev, const float* t_dev, int64_t n,
                                const sep_train_cfg* cfg, float* final_loss, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m || !cfg || n < 1 || !x_dev || !t_dev) return SEP_ERR_ARG;
   if (cfg->epochs < 1 || cfg->batch < 64 || !(cfg->lr > 0.0f)) return mfail(m->ctx, SEP_ERR_ARG, "bad training config");
   MCUDA(m->ctx, cudaSetDevice(m->ctx->device));
@@ -191,6 +203,8 @@ sep_status sep_surrogate_train(sep_model* m, const float* x_dev, const float* t_
 
 sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const float* target_dev, int64_t n,
                                  float* x_dev, float* t_dev, float* norm_host, int64_t* n_valid, sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx || n < 0 || !norm_host || !n_valid || (n > 0 && (!feat_dev || !target_dev || !x_dev || !t_dev)))
     return mfail(ctx, SEP_ERR_ARG, "bad surrogate_prepare arguments");
   MCUDA(ctx, cudaSetDevice(ctx->device));
@@ -261,6 +275,8 @@ sep_status sep_surrogate_prepare(sep_ctx* ctx, const float* feat_dev, const floa
 }
 
 sep_status sep_model_save(const sep_model* m, const char* path) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!m || !path) return SEP_ERR_ARG;
   const size_t P = sep::kNParams;
   std::vector<float> buf(3 * P);
@@ -282,6 +298,8 @@ sep_status sep_model_save(const sep_model* m, const char* path) {
 }
 
 sep_status sep_model_load(sep_ctx* ctx, const char* path, sep_model** out) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx || !path || !out) return SEP_ERR_ARG;
   *out = nullptr;
   FILE* f = fopen(path, "rb");

@@ -3,11 +3,10 @@
 // sep_sparsify keeps its scratch (a kept-pixel bitmap, per-bin thresholds and
 // per-tile counts) in buffers owned by the context, grown with cudaMalloc on
 // first use or when a larger batch arrives. Some callers must not allocate
-// when they call: code recording a CUDA graph (cudaMalloc is not allowed
-// inside a stream capture), a real-time acquisition thread that must never
-// block on the device allocator, or a process whose device memory is fixed
-// after start-up. This variant runs the same kernels with its scratch in one
-// statically allocated device array instead.
+// when they call: a real-time acquisition thread that must never block on
+// the device allocator, or a process whose device memory is fixed after
+// start-up. This variant runs the same checks and kernels with its scratch
+// in one statically allocated device array instead.
 //
 // The array (kNoallocScratchBytes) lives in every GPU that loads the library
 // until the process exits. All calls share it and it keeps the last call's
@@ -43,26 +42,20 @@ extern "C" sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, con
                                            const sep_params* params, const float* mean_dev, const float* sigma_dev,
                                            int32_t* idx_dev, float* val_dev, int64_t capacity, int32_t* n_kept_dev,
                                            sep_stream stream) {
+  sep::DeviceGuard device_guard;
+  sep::NvtxRange nvtx_range(__func__);
   if (!ctx) return SEP_ERR_ARG;
   auto fail = [&](sep_status st, const std::string& m) {
     ctx->err = m;
     return st;
   };
-  if (!csr || csr->ctx != ctx) return fail(csr ? SEP_ERR_STATE : SEP_ERR_ARG, "csr missing or from another context");
-  if (n_frames < 0 || capacity < 0) return fail(SEP_ERR_ARG, "n_frames and capacity must be >= 0");
-  if (n_frames > SEP_MAX_FRAMES) return fail(SEP_ERR_ARG, "n_frames above SEP_MAX_FRAMES");
-  if (n_frames > 0 && (!frames_dev || !mean_dev || !sigma_dev || !n_kept_dev || (capacity > 0 && (!idx_dev || !val_dev))))
-    return fail(SEP_ERR_ARG, "NULL argument");
-  if (dtype == SEP_DTYPE_U16_JF) {
-    if (!calib || calib->ctx != ctx || calib->npix != csr->npix)
-      return fail(SEP_ERR_ARG, "raw frames need this detector's calibration");
-  } else if (dtype != SEP_DTYPE_F32) {
-    return fail(SEP_ERR_ARG, "unknown dtype");
-  }
-  if (!params || !(params->k_pick >= 0.0f) || !isfinite(params->k_pick) ||
-      (params->interpolate != 0 && params->interpolate != 1))
-    return fail(SEP_ERR_ARG, "bad params");
   if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(SEP_ERR_ARG, "device index too large");
+  // the checks of sep_sparsify, which also make the context's device current
+  const sep_status st = sep::check_call(ctx, csr, calib, frames_dev, dtype, n_frames, params);
+  if (st != SEP_OK) return st;
+  if (capacity < 0) return fail(SEP_ERR_ARG, "capacity < 0");
+  if (n_frames > 0 && (!mean_dev || !sigma_dev || !n_kept_dev || (capacity > 0 && (!idx_dev || !val_dev))))
+    return fail(SEP_ERR_ARG, "NULL argument");
   if (n_frames == 0) return SEP_OK;
 
   // scratch layout: bitmap [F][words] | thresholds [F][nbins] | tile counts
@@ -76,8 +69,7 @@ extern "C" sep_status sep_sparsify_noalloc(sep_ctx* ctx, const sep_csr* csr, con
     return fail(SEP_ERR_ARG, "batch needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
                                  std::to_string(kNoallocScratchBytes) + " (use fewer frames per call)");
 
-  cudaError_t e = cudaSetDevice(ctx->device);
-  if (e != cudaSuccess) return fail(SEP_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  cudaError_t e = cudaSuccess;
   void* base;
   {
     // first call on a device: look up the array's device address (no allocation)
