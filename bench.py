@@ -503,7 +503,7 @@ def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
     the whole path with it against the plain path on the bench batch."""
     import torch
     import synth
-    from paper_2411_09515_gb300 import Surrogate
+    from paper_2411_09515_gb300 import Surrogate, _binding as B
     F = dev.shape[0]
     spec = synth.spec_jf_serial(7777)
     t0 = time.time()
@@ -539,7 +539,7 @@ def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
     sep.attach_surrogate(None)
     timed(2)
     plain_ms = timed(args.steps)
-    plain = {k: out[k].clone() for k in ("idx", "n_kept", "count", "mean", "sigma")}
+    plain = {k: out[k].clone() for k in ("idx", "val", "n_kept", "count", "mean", "sigma")}
     res = {"train_frames": args.surrogate_train_frames, "train_rows": rows, "train_loss": round(loss, 5),
            "train_s": round(t_train, 1), "plain_fps": round(F / (plain_ms * 1e-3), 2),
            "plain_row_scans_per_bin": scans_per_item()}
@@ -548,17 +548,35 @@ def surrogate_eval(sep, det, mask, cal, dev, out, kcap, pcap, stream, args):
     sep.surrogate_stats(reset=True, stream=stream)
     ms = timed(args.steps)
     acc, fb = sep.surrogate_stats(reset=True, stream=stream)
-    same = 0
+    # kept sets against the plain path's: identical, or differing only in
+    # pixels whose value lies within 1e-5 relative of the plain threshold
+    # (the two paths sum the same sets in another order)
+    bop = torch.from_numpy(B.sep_csr_export(sep.csr)["bin_of_pixel"]).to(dev.device).long()
+    k_pick = float(sep.params.k_pick)
+    same = same_band = 0
     for f in range(F):
-        n = int(plain["n_kept"][f])
-        if int(out["n_kept"][f]) == n and torch.equal(out["idx"][f, :n], plain["idx"][f, :n]):
+        n, m = int(plain["n_kept"][f]), int(out["n_kept"][f])
+        a_idx, b_idx = plain["idx"][f, :n].long(), out["idx"][f, :m].long()
+        if n == m and torch.equal(a_idx, b_idx):
             same += 1
+            same_band += 1
+            continue
+        vals = torch.cat([plain["val"][f, :n], out["val"][f, :m]])
+        idx = torch.cat([a_idx, b_idx])
+        u, inv, cnt = torch.unique(idx, return_inverse=True, return_counts=True)
+        diff = cnt[inv] == 1
+        px, v = idx[diff], vals[diff].double()
+        b = bop[px]
+        thr = plain["mean"][f, b].double() + k_pick * plain["sigma"][f, b].double()
+        if bool(torch.all((v - thr).abs() <= 1e-5 * thr.abs())):
+            same_band += 1
     res["surrogate"] = {
         "fps": round(F / (ms * 1e-3), 2), "speedup_vs_plain": round(plain_ms / ms, 4),
         "predicted_core_held_frac": round(acc / max(acc + fb, 1), 4),
         "row_scans_per_bin": scans_per_item(),
         "bins_same_count_frac": round(float((out["count"] == plain["count"]).float().mean().item()), 4),
-        "frames_identical_kept": round(same / F, 4)}
+        "frames_identical_kept": round(same / F, 4),
+        "frames_identical_kept_outside_band": round(same_band / F, 4)}
     sep.attach_surrogate(None)
     model.close()
     return res

@@ -537,14 +537,18 @@ sep_status sep_correct(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib,
  * and its training targets target_dev [n_frames][nbins][2] =
  * ((mu - m1) / s1, log(sd / s1)) of the clipped result (NaN where the bin has
  * fewer than 2 entries in the final set, a zero deviation, or s1 = 0).
- * The features are taken on a sample of the bin's row: every step-th group
- * of 4 consecutive entries of each coefficient class (step 4 for rows of
- * 2048 entries or more, 2 from 512, else 1); m1 and s1 are the sample's mean
- * and deviation (Eqs. 12-13, FP32). Features: 0 log(step n) / 8 (n: the
- * sample's finite entries of weight != 0), 1 Omega / n over the sample,
- * 2 clamp(m1 / s1, -20, 20) / 4, 3 the sample's fraction with
- * z = (v - m1) / s1 >= 4, 4 .. 19 the quantiles (j + 1/2) / 16 of the
- * sample's z, read linearly inside a 64-bin histogram over [-4, 12). */
+ * The first features are taken on a sample of the bin's row: every step-th
+ * group of 4 consecutive entries of each coefficient class (step 4 for rows
+ * of 2048 entries or more, 2 from 512, else 1); m1 and s1 are the sample's
+ * mean and deviation (Eqs. 12-13, FP32). Features: 0 log(step n) / 8 (n:
+ * the sample's finite entries of weight != 0), 1 Omega / n over the sample,
+ * 2 clamp(m1 / s1, -20, 20) / 4. The rest come from a sketch of at most 128
+ * of the row's weighted entries (element s = 0 .. 127 is entry s when the
+ * G groups of 4 before the weight-0 carriers hold at most 128 entries, else
+ * entry 4 floor(s G / 128) + s mod 4; non-finite values left out): 3 the
+ * sketch's fraction with v >= m1 + 4 s1, 4 .. 19 its values at ranks
+ * floor((j + 1/2) n' / 16) of n' in ascending order, as z = (v - m1) / s1
+ * clamped to [-4, 12]. */
 sep_status sep_surrogate_record(sep_ctx* ctx, const sep_csr* csr, const sep_calib* calib, const void* frames_dev,
                                 int32_t dtype, int32_t n_frames, const sep_params* params, float* mean_dev,
                                 float* sigma_dev, int32_t* count_dev, float* feat_dev, float* target_dev,

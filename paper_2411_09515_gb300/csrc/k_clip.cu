@@ -731,90 +731,85 @@ __device__ __forceinline__ void add_pair(float& h, float& l, float a, float b) {
 
 // ---- surrogate (no counterpart in the paper): features and inference ----
 //
-// Features of an item come from pass A's sample (every step-th group of 4
-// entries): 0 log(n) / 8 with n the sample's valid entries times step,
-// 1 Omega / n over the sample, 2 clamp(m1 / s1, -20, 20) / 4 with m1, s1 the
-// sample's mean and Eq. 13 deviation, 3 the sample's share of z = (v - m1) /
-// s1 above 4, 4 .. 19 the quantiles (j + 1/2) / 16 of z read linearly inside
-// a 64-bin histogram over [-4, 12).
+// Features of an item: 0 log(n) / 8 with n the valid entries of pass A's
+// sample (every step-th group of 4 entries) times step, 1 Omega / n over
+// that sample, 2 clamp(m1 / s1, -20, 20) / 4 with m1, s1 the sample's mean
+// and Eq. 13 deviation; then, over a stratified subsample of at most 128 of
+// the row's valid entries (sketch_element), 3 the share with z = (v - m1) /
+// s1 >= 4 and 4 .. 19 the order statistics of z at ranks floor((j + 1/2)
+// n' / 16) (n' the subsample's size; z clamped to [-4, 12]). The subsample
+// is one 16-byte load per lane and four values a lane, sorted across the
+// warp by a bitonic network.
 constexpr float kSurrMargin = 0.5f;   // core margin inside the predicted final interval, in deviations
+
+// Entry of the row behind sketch element s (0 .. 127) of a row whose first
+// G groups of 4 hold its weighted entries: every entry when the row has at
+// most 128 of them, else one entry of group floor(s G / 128) (-1: none).
+__device__ __forceinline__ int sketch_element(int s, int G) {
+  if (4 * G <= 128) return s < 4 * G ? s : -1;
+  return 4 * (int)(((long long)s * G) >> 7) + (s & 3);
+}
 
 template <int MODE>
 __device__ __forceinline__ void sample_features(const Row& row, const float* wts, const int (&ge)[4], int lane,
                                                 int step, float n_s, float om_s, float m1, float s1,
-                                                uint32_t* hist, float (&feat)[kIn]) {
+                                                float (&feat)[kIn]) {
+  const int G = ge[3] >> 2;
+  // element s = 32 r + lane of the sketch in x[r] (+inf where none)
+  float x[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = sketch_element(32 * r + lane, G);
+    float v = INFINITY;
+    if (e >= 0) {
+      const float4 q = __ldg(row.v4 + (e >> 2));
+      const float c = (e & 3) == 0 ? q.x : ((e & 3) == 1 ? q.y : ((e & 3) == 2 ? q.z : q.w));
+      const bool ok = fabsf(c) <= FLT_MAX && (MODE != MODE_ENTRY || wts[e] != 0.0f);
+      v = ok ? c : INFINITY;
+    }
+    x[r] = v;
+  }
+  // ascending bitonic sort of the 128 elements (index 32 r + lane)
+#pragma unroll
+  for (int k = 2; k <= 128; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      float y[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) y[r] = j >= 32 ? x[r ^ (j >> 5)] : __shfl_xor_sync(0xffffffffu, x[r], j);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = 32 * r + lane;
+        const bool up = (e & k) == 0, low = (e & j) == 0;
+        x[r] = (low == up) ? fminf(x[r], y[r]) : fmaxf(x[r], y[r]);
+      }
+    }
+  }
+  int nv = 0, hi4 = 0;
+  const float z4 = fmaf(4.0f, s1, m1);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    nv += __popc(__ballot_sync(0xffffffffu, x[r] <= FLT_MAX));
+    hi4 += __popc(__ballot_sync(0xffffffffu, x[r] <= FLT_MAX && x[r] >= z4));
+  }
   const float inv = s1 > 0.0f ? 1.0f / s1 : 0.0f;
-  hist[lane] = 0u;
-  hist[lane + 32] = 0u;
-  __syncwarp();
-  auto add = [&](float v) {
-    const float zb = fminf(fmaxf(__fmul_rn(__fsub_rn(v, m1), inv) * 4.0f + 16.0f, 0.0f), 63.0f);
-    atomicAdd(hist + (int)zb, 1u);
-  };
-  if (MODE == MODE_CLASS || MODE == MODE_UNIT) {
-    // the classes hold contiguous ranges: one scan of [0, ge[3]) with the
-    // same group sampling per class as pass A
-    constexpr int NCLS = MODE == MODE_CLASS ? 4 : 1;
-    int lo = 0;
-#pragma unroll 1
-    for (int cls = 0; cls < NCLS; ++cls) {
-      const int hi = ge[cls];
-      scan_row(row, lo >> 2, hi >> 2, lane, [&](const float4& v4, int) {
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (fabsf(xs[j]) <= FLT_MAX) add(xs[j]);
-      }, step);
-      lo = hi;
-    }
-  } else {
-    scan_row(row, 0, ge[3] >> 2, lane, [&](const float4& v4, int q) {
-      const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (wts[4 * q + j] != 0.0f && fabsf(xs[j]) <= FLT_MAX) add(xs[j]);
-    }, step);
-  }
-  __syncwarp();
-  // cumulative counts: lane l holds bins 2l and 2l + 1
-  const uint32_t c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
-  uint32_t incl = c0 + c1;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-  const uint32_t upper = tot - __shfl_sync(0xffffffffu, incl, 15);   // bins 32 .. 63: z >= 4
-  __syncwarp();
-  hist[2 * lane] = incl - c1;   // cumulative through bin 2l
-  hist[2 * lane + 1] = incl;
-  __syncwarp();
-  float zq = 0.0f;
-  if (lane < 16 && tot > 0u) {
-    // quantile (lane + 1/2) / 16: the first bin whose cumulative count reaches it
-    const float target = ((float)lane + 0.5f) * (1.0f / 16.0f) * (float)tot;
-    int lo = 0, hi = 63;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((float)hist[mid] >= target) hi = mid;
-      else lo = mid + 1;
-    }
-    const float before = lo > 0 ? (float)hist[lo - 1] : 0.0f;
-    const float c = (float)hist[lo] - before;
-    zq = -4.0f + 0.25f * ((float)lo + (c > 0.0f ? (target - before) / c : 0.0f));
-  }
   const float n_est = n_s * (float)step;
   feat[0] = n_est > 0.0f ? logf(n_est) * 0.125f : 0.0f;
   feat[1] = n_s > 0.0f ? om_s / n_s : 0.0f;
   feat[2] = s1 > 0.0f ? fminf(fmaxf(m1 / s1, -20.0f), 20.0f) * 0.25f : 0.0f;
-  feat[3] = tot > 0u ? (float)upper / (float)tot : 0.0f;
+  feat[3] = nv > 0 ? (float)hi4 / (float)nv : 0.0f;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) feat[4 + j] = __shfl_sync(0xffffffffu, zq, j);
+  for (int j = 0; j < 16; ++j) {
+    const int p = ((2 * j + 1) * nv) >> 5;   // floor((j + 1/2) nv / 16)
+    const int r = p >> 5;
+    const float mine = r == 0 ? x[0] : (r == 1 ? x[1] : (r == 2 ? x[2] : x[3]));
+    const float q = __shfl_sync(0xffffffffu, mine, p & 31);
+    feat[4 + j] = nv > 0 ? fminf(fmaxf(__fmul_rn(__fsub_rn(q, m1), inv), -4.0f), 12.0f) : 0.0f;
+  }
 }
 
 // The network on one warp (weights BF16 with W1 and W2 input-major, FP32
-// arithmetic): lane l computes hidden units l and l + 32 of each layer, so
+// arithmetic; W and nm in shared memory): lane l computes hidden units l and l + 32 of each layer, so
 // the warp reads consecutive weights; every lane returns the de-normalised
 // outputs (mean offset, log-deviation ratio).
 __device__ __forceinline__ void warp_mlp(const __nv_bfloat16* W, const float* nm, const float (&feat)[kIn], int lane,
@@ -822,7 +817,7 @@ __device__ __forceinline__ void warp_mlp(const __nv_bfloat16* W, const float* nm
   float a1[2] = {__bfloat162float(W[kB1 + lane]), __bfloat162float(W[kB1 + lane + 32])};
 #pragma unroll
   for (int k = 0; k < kIn; ++k) {
-    const float xk = (feat[k] - __ldg(nm + k)) / __ldg(nm + kIn + k);
+    const float xk = (feat[k] - nm[k]) / nm[kIn + k];
     a1[0] = fmaf(__bfloat162float(W[kW1 + k * kH + lane]), xk, a1[0]);
     a1[1] = fmaf(__bfloat162float(W[kW1 + k * kH + lane + 32]), xk, a1[1]);
   }
@@ -844,8 +839,8 @@ __device__ __forceinline__ void warp_mlp(const __nv_bfloat16* W, const float* nm
     y0 += __shfl_xor_sync(0xffffffffu, y0, o);
     y1 += __shfl_xor_sync(0xffffffffu, y1, o);
   }
-  u0 = (y0 + __bfloat162float(W[kB3])) * __ldg(nm + 2 * kIn + 2) + __ldg(nm + 2 * kIn);
-  u1 = (y1 + __bfloat162float(W[kB3 + 1])) * __ldg(nm + 2 * kIn + 3) + __ldg(nm + 2 * kIn + 1);
+  u0 = (y0 + __bfloat162float(W[kB3])) * nm[2 * kIn + 2] + nm[2 * kIn];
+  u1 = (y1 + __bfloat162float(W[kB3 + 1])) * nm[2 * kIn + 3] + nm[2 * kIn + 1];
 }
 
 __device__ __forceinline__ void mark_pixel(uint32_t* bm, const int32_t* cpix, int64_t e) {
@@ -894,10 +889,17 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
   const int capr = MODE == MODE_ENTRY ? (a.cap + 3) & ~3 : 0;
   float* wts = reinterpret_cast<float*>(smem_raw);
   uint2* tail = reinterpret_cast<uint2*>(wts + capr) + (size_t)warp * (32 * a.tcap) + lane;
-  // surrogate modes: a 64-bin histogram per warp after the tails
-  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint2*>(wts + capr) + (size_t)kWarps * 32 * a.tcap) +
-                   64 * warp;
-  (void)hist;
+  // with inference (SURR 2) the network's normalisation and BF16 weights
+  // follow the tails, copied once per CTA (read by every item, they would
+  // otherwise compete with the streamed rows for the L1 cache)
+  float* nm_s = reinterpret_cast<float*>(reinterpret_cast<uint2*>(wts + capr) + (size_t)kWarps * 32 * a.tcap);
+  __nv_bfloat16* w_s = reinterpret_cast<__nv_bfloat16*>(nm_s + kNNorm);
+  (void)w_s;
+  if (SURR == 2) {
+    for (int i = threadIdx.x; i < kNParams; i += 32 * kWarps) w_s[i] = a.mlp_w[i];
+    for (int i = threadIdx.x; i < kNNorm; i += 32 * kWarps) nm_s[i] = __ldg(a.mlp_norm + i);
+    __syncthreads();
+  }
 
   const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
   const int f0 = blockIdx.y * a.frames_per_cta;
@@ -931,6 +933,7 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
     stat(0, 1);
     // ------------- pass A: where to place the core -------------
     float cLo, cHi, K;
+    float pLo = 0.0f, pHi = 0.0f, pK = 0.0f;   // SURR 2: the plain placement, for a retry
     float feat[kIn], m1 = 0.0f, s1 = 0.0f;
     (void)feat;
     {
@@ -952,12 +955,15 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
       if (SURR != 0) {
         m1 = mu;
         s1 = sd;
-        sample_features<MODE>(row, wts, ge, lane, step, n_set, h[0], m1, s1, hist, feat);
+        sample_features<MODE>(row, wts, ge, lane, step, n_set, h[0], m1, s1, feat);
       }
       if (SURR == 2) {
         // the predicted final interval, and the core half a deviation inside it
+        pLo = cLo;
+        pHi = cHi;
+        pK = K;
         float u0, u1;
-        warp_mlp(a.mlp_w, a.mlp_norm, feat, lane, u0, u1);
+        warp_mlp(w_s, nm_s, feat, lane, u0, u1);
         const float mh = fmaf(s1, u0, m1), sh = s1 * expf(fminf(u1, 20.0f));
         if (s1 > 0.0f && sh > 0.0f && fabsf(mh) <= FLT_MAX && sh <= FLT_MAX) {
           const float half = __fmul_rn(a.k_clip, sh), mgs = __fmul_rn(kSurrMargin, sh);
@@ -976,7 +982,7 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
     st.steps = -1;
     st.done = 0;
     st.Kf = K;
-    bool ovf = false, scan = true;
+    bool ovf = false, scan = true, retried = SURR != 2;
     int m = 0, scans = 0;
     float cn = 0.0f, ch[6], cl[6];
     for (;;) {
@@ -994,6 +1000,19 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
           stat(1, 1);
           stat(2, ovf ? 1 : 0);
           stat(4, listed);
+        }
+        if (!retried) {
+          // first pass B only (the plain placement is inside the first
+          // interval, not necessarily inside a later one): when the
+          // predicted core left more entries outside it than the tail holds
+          // (a heavy-tailed bin), the plain placement instead
+          retried = true;
+          if (ovf) {
+            cLo = pLo;
+            cHi = pHi;
+            K = pK;
+            continue;
+          }
         }
         if (!ovf) warp_totals<MODE, PREC>(ss, cc, ci, cn, ch, cl);
         scan = false;
@@ -1106,12 +1125,13 @@ cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   // each warp's tail (8 bytes a slot, 32 lanes)
   const long capr = ((long)a.cap + 3) & ~3L;
   const long wbytes = MODE == MODE_ENTRY ? 4 * capr : 0;
-  const long budget = (long)smem_optin() - kClipStaticSmem - wbytes;
+  const long budget = (long)smem_optin() - kClipStaticSmem - wbytes -
+                     (SURR == 2 ? kNNorm * 4 + ((kNParams * 2 + 15) & ~15) : 0);
   long tcap = clip_tail_slots(a.cap, 32 * kWarps);
   if (kWarps * 256 * tcap > budget) tcap = std::max(0L, budget / (256L * kWarps));
   if (tcap < 5) tcap = 0;   // no room for a tail: every step runs as a full pass
   a.tcap = (int32_t)tcap;
-  const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap + (SURR != 0 ? kWarps * 256 : 0));
+  const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap + (SURR == 2 ? kNNorm * 4 + ((kNParams * 2 + 15) & ~15) : 0));
   auto k = k_clip_warp<MODE, PREC, kWarps, SURR>;
   if (mode != 2) {
     // the attribute only grows: size classes sharing this instance may set
@@ -1145,7 +1165,8 @@ template <int MODE>
 cudaError_t launch_p(const ClipArgs& a, int n_ctas, int tpb, int32_t prec, int mode, cudaStream_t s) {
   // the surrogate modes exist for the default precision only
   if (a.rec_feat) return launch_tail_b<MODE, SEP_PREC_DWORD, 1>(a, n_ctas, tpb, mode, s);
-  if (a.mlp_w) return launch_tail_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, tpb, mode, s);
+  // (inference: at least 4 warps a CTA share one copy of the weights)
+  if (a.mlp_w) return launch_tail_b<MODE, SEP_PREC_DWORD, 2>(a, n_ctas, std::max(tpb, 128), mode, s);
   switch (prec) {
     case SEP_PREC_PLAIN: return launch_tail_b<MODE, SEP_PREC_PLAIN>(a, n_ctas, tpb, mode, s);
     case SEP_PREC_KAHAN: return launch_tail_b<MODE, SEP_PREC_KAHAN>(a, n_ctas, tpb, mode, s);

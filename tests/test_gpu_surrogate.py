@@ -164,6 +164,34 @@ def _row_sample(ex, b, step_of):
     return col[sel], coef[sel].astype(np.float64), step
 
 
+def _sketch(ex, b, sig):
+    """The feature sketch's values of row b: element s (0 .. 127) is entry s
+    when the row's weighted groups G hold at most 128 entries, else entry
+    4 floor(s G / 128) + s mod 4; kept where it is a finite value of weight
+    > 0."""
+    r0, r1 = int(ex["rowptr"][b]), int(ex["rowptr"][b + 1])
+    col, coef = ex["col"][r0:r1], ex["coef"][r0:r1]
+    ng = (r1 - r0) // 4
+    G = ng
+    cls = 1.0
+    for q in range(ng):
+        real = np.flatnonzero(col[4 * q:4 * q + 4] >= 0)
+        if real.size:
+            cls = coef[4 * q + real[0]]
+        if cls == 0:                          # the weight-0 carriers close the weighted groups
+            G = q
+            break
+    out = []
+    for s_ in range(128):
+        if 4 * G <= 128:
+            e = s_ if s_ < 4 * G else -1
+        else:
+            e = 4 * ((s_ * G) >> 7) + (s_ & 3)
+        if e >= 0 and col[e] >= 0 and coef[e] > 0 and np.isfinite(sig[col[e]]):
+            out.append(sig[col[e]])
+    return np.asarray(out, np.float64)
+
+
 def test_record_features_and_targets(jf_train):
     det, mask, cal, fr, _ = jf_train
     sep = Separator.from_detector(det, mask=mask, calib=cal)
@@ -197,15 +225,17 @@ def test_record_features_and_targets(jf_train):
         assert feat[b, 0] == pytest.approx(math.log(n * step) / 8, rel=1e-5)
         assert feat[b, 1] == pytest.approx(om / n, rel=1e-5)
         assert feat[b, 2] == pytest.approx(max(min(m1 / s1, 20), -20) / 4, rel=1e-3, abs=1e-4)
-        z = (v - m1) / s1
-        assert feat[b, 3] == pytest.approx((z >= 4).mean(), abs=2.0 / n)
+        # the sketch: at most 128 entries spread over the weighted groups,
+        # sorted; its share above m1 + 4 s1 and 16 order statistics of z
+        sk = np.sort(_sketch(ex, b, sig))
+        nv = sk.size
+        assert nv > 0
+        assert feat[b, 3] == pytest.approx((sk >= m1 + 4 * s1).mean(), abs=1.0 / nv + 1e-6)
         q = feat[b, 4:]
         assert np.all(np.diff(q) >= 0) and q[0] >= -4 and q[-1] <= 12
-        # a quantile read off the 0.25-wide histogram lies within one bin of the exact one
-        for j in (3, 8, 12):
-            exact = np.quantile(z, (j + 0.5) / 16)
-            if -4 < exact < 12:
-                assert abs(q[j] - exact) <= 0.25 + 1e-3, (b, j, q[j], exact)
+        ranks = ((2 * np.arange(16) + 1) * nv) >> 5
+        want = np.clip((sk[ranks] - m1) / s1, -4, 12)
+        assert np.allclose(q, want, rtol=1e-4, atol=2e-3), (b, q, want)
         mu, sd = F.ref["mean"][b], F.ref["sigma"][b]
         if F.ref["count"][b] >= 2 and sd > 0 and F.ref["band"][b] >= BAND:
             assert tgt[b, 0] == pytest.approx((mu - m1) / s1, rel=1e-3, abs=1e-3)
