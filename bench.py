@@ -128,7 +128,7 @@ def setup_workload(F, rank, seed=2024):
 
 def algorithmic_bytes_clip(F, npix, nvalid, nnz, nbins):
     """Minimum DRAM bytes of one staged integrate + clip of F raw frames
-    (k_stage + k_integrate_clip): every raw word once (2 B/pixel/frame), the
+    (k_stage_ring + k_clip_warp): every raw word once (2 B/pixel/frame), the
     calibration planes and the matrix once per launch, the per-bin outputs
     (mean, sigma, count, threshold). The staged copy of the values that the
     two kernels exchange is an implementation choice and is not charged."""
@@ -153,7 +153,7 @@ CLIP_SOURCES = ["k_stage.cu", "k_clip.cu"]
 
 
 def measured_traffic(F):
-    """DRAM bytes (read + write) of k_stage + k_integrate_clip per launch of F
+    """DRAM bytes (read + write) of k_stage_ring + k_clip_warp per launch of F
     frames, from the ncu capture recorded in profiles/roofline_traffic.json,
     scaled from its frame count; None when absent or when the kernel
     sources changed since the capture."""
@@ -213,7 +213,12 @@ def run_ours(args):
     out = sep.alloc_outputs(F, kcap, pcap)
     stream = torch.cuda.current_stream()
     tune_ms = None
-    if not args.no_autotune:
+    if args.clip_plan:
+        # a fixed clip schedule "T1,T2:W1,W2,W3" (size-class thresholds in
+        # entries : threads per block of each class), for reproducible profiles
+        thr, tpb = args.clip_plan.split(":")
+        sep.set_plan([int(x) for x in tpb.split(",")], [int(x) for x in thr.split(",") if x])
+    elif not args.no_autotune:
         # the library's autotuner picks the clip schedule on a sample of the batch
         tune_ms = sep.autotune(dev[: min(F, 128)], stream=stream)
     plan = sep.get_plan()
@@ -347,7 +352,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (4.58 GB/batch), no flush", "parallelism": f"replicas x{world}",
                        "kept_capacity": kcap, "peak_capacity": pcap, "precision": args.precision,
                        "clip_schedule": plan, "autotune_sample_ms": tune_ms},
-            "roofline": {"bound": "hbm", "kernel": "k_stage + k_integrate_clip", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": "k_stage_ring + k_clip_warp", "achieved": round(achieved, 1),
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": measured_traffic(F),
                          "peak_source": src, "kernel_ms": round(k_ms, 4), "kernel_leg": clip_leg,
@@ -734,6 +739,7 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--clip-plan", default="", help="fixed clip schedule 'T1,T2:W1,W2,W3' instead of the autotuner")
     ap.add_argument("--chunk-frames", type=int, default=64)
     ap.add_argument("--surrogate-train-frames", type=int, default=256)
     ap.add_argument("--mixed-frames", type=int, default=24)
