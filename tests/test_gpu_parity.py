@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from parity import Frame, check_clip, check_frame, check_kept, check_peaks
+from parity import MEAN_FLOOR, Frame, check_clip, check_frame, check_kept, check_peaks
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -113,7 +113,7 @@ def jf_small():
 # the compensated and FP64-merged modes meet the relative tolerance without
 # the mean's absolute floor; the plain mode (FP32 sums throughout) keeps it
 @pytest.mark.parametrize("precision,floor", [(SEP_PREC_DWORD, 0.0), (SEP_PREC_FP64MERGE, 0.0), (SEP_PREC_KAHAN, 0.0),
-                                             (SEP_PREC_PLAIN, 1e-7)])
+                                             (SEP_PREC_PLAIN, MEAN_FLOOR)])
 def test_jungfrau_raw_split_parity(jf_small, precision, floor):
     det, mask, cal, fr, W = jf_small
     sep = Separator.from_detector(det, mask=mask, calib=cal, precision=precision)
