@@ -30,11 +30,24 @@ def build_cmd():
             os.path.join(_HERE, "synth.c"), "-lm", "-o", _SO]
 
 
+_SO_GPU = os.path.join(_HERE, "_build", "libsynth_gpu.so")
+_lib_gpu = None
+
+
+def build_gpu_cmd():
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared", "-Xcompiler", "-fPIC",
+            "-fmad=false", os.path.join(_HERE, "synth_gpu.cu"), "-o", _SO_GPU]
+
+
 def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     src = os.path.join(_HERE, "synth.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         subprocess.run(build_cmd(), check=True)
+    src = os.path.join(_HERE, "synth_gpu.cu")
+    if force or not os.path.exists(_SO_GPU) or os.path.getmtime(_SO_GPU) < os.path.getmtime(src):
+        subprocess.run(build_gpu_cmd(), check=True)
     return _SO
 
 
@@ -257,3 +270,63 @@ def philox(ctr, key):
     o = np.zeros(4, np.uint32)
     lib().synth_philox4x32_10(_p(c), _p(k), _p(o))
     return o
+
+
+def lib_gpu():
+    global _lib_gpu
+    if _lib_gpu is None:
+        if not os.path.exists(_SO_GPU):
+            build()
+        L = C.CDLL(_SO_GPU)
+        L.synth_gpu_scratch_bytes.argtypes = [C.POINTER(_Spec), C.c_int32]
+        L.synth_gpu_scratch_bytes.restype = C.c_size_t
+        L.synth_gpu_frames.argtypes = [C.POINTER(_Spec), C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.synth_gpu_frames.restype = C.c_int
+        _lib_gpu = L
+    return _lib_gpu
+
+
+def _spec_struct(det, spec):
+    return _Spec(det.rows, det.cols, det.center_px[0], det.center_px[1], spec.bg_kind,
+                 spec.bg_scale[0], spec.bg_scale[1], spec.bg_clip[0], spec.bg_clip[1],
+                 spec.hit_rate, spec.spots[0], spec.spots[1], spec.amp[0], spec.amp[1],
+                 int(spec.amp_log), spec.sigma[0], spec.sigma[1], int(spec.out_raw),
+                 spec.read_noise_adu, spec.seed)
+
+
+def frames_gpu(det: Detector, spec: FrameSpec, frame0: int, n: int, out, calib_dev=None, mask_dev=None,
+               scratch=None, stream=None):
+    """The frames of :func:`frames` generated on the GPU (same model, same
+    Philox streams; a rare pixel may differ by one count, see synth_gpu.cu).
+    ``out``: a device tensor of n * npix uint16 (raw) or float32 words;
+    ``calib_dev``: device (ped, gain) planes [3 * npix] for raw frames;
+    ``mask_dev``: device uint8 [npix] or None; ``scratch``: a device uint8
+    tensor of at least :func:`gpu_scratch_bytes` bytes (allocated when None);
+    ``stream``: a torch CUDA stream (default: the current one)."""
+    import torch
+    s = _spec_struct(det, spec)
+    need = lib_gpu().synth_gpu_scratch_bytes(C.byref(s), n)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=out.device)
+    if scratch.numel() < need:
+        raise ValueError("scratch too small")
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device)
+    ped = gain = None
+    if spec.out_raw:
+        if calib_dev is None:
+            raise ValueError("raw frames need calibration planes on the device")
+        ped, gain = (C.c_void_p(calib_dev[0].data_ptr()), C.c_void_p(calib_dev[1].data_ptr()))
+    rc = lib_gpu().synth_gpu_frames(C.byref(s), frame0, n, ped, gain,
+                                    None if mask_dev is None else C.c_void_p(mask_dev.data_ptr()),
+                                    C.c_void_p(out.data_ptr()), C.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                    C.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"synth_gpu_frames failed ({rc})")
+    return out
+
+
+def gpu_scratch_bytes(det: Detector, spec: FrameSpec, n: int) -> int:
+    s = _spec_struct(det, spec)
+    return int(lib_gpu().synth_gpu_scratch_bytes(C.byref(s), n))
