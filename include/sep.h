@@ -214,7 +214,7 @@ sep_status sep_csr_info(const sep_csr* csr, int64_t* npix, int32_t* nbins, int64
 /* Staging order: the order of the pixels with at least one matrix entry that
  * sorts the entries inside each coefficient group of a row (so one staging
  * tile writes consecutive slots of a bin's row). Pixels are grouped by tiles
- * of 32 rows x 32 columns (tiles in row-major order); inside a tile, by
+ * of 64 rows x 64 columns (tiles in row-major order); inside a tile, by
  * centre bin, then radius of the pixel centre, then pixel index. perm_inv
  * [npos] receives the pixel of each position (may be NULL); *npos the number
  * of positions. (A frame's staged copy holds one value per matrix entry, in

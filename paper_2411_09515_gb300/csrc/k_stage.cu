@@ -179,12 +179,21 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs a) {
 // held), kRing frames ahead, and reads them back when their frame comes.
 // A thread reads only what it copied itself, so the ring needs no barrier.
 // Four frames per step share the two barriers around the write-out.
+constexpr int kRing = 8;   // frames ahead (a multiple of the 4 frames of a step)
+
+// Dynamic shared memory of k_stage_ring: four corrected tiles, then the ring.
+template <int DT>
+constexpr size_t ring_smem_bytes() {
+  return sizeof(float) * 4 * kTileSlots + (size_t)kRing * kStageThreads * (DT == SEP_DTYPE_U16_JF ? 8 : 16);
+}
+
 template <int DT, bool NORM>
 __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
   constexpr int kVec = DT == SEP_DTYPE_U16_JF ? 8 : 16;   // bytes of 4 raw words
-  constexpr int kRing = 8;   // frames ahead (a multiple of the 4 frames of a step)
-  __shared__ float tv[4][kTileSlots];
-  __shared__ __align__(16) unsigned char ring[kRing][kStageThreads * kVec];
+  extern __shared__ __align__(16) unsigned char stage_smem[];
+  float(*tv)[kTileSlots] = reinterpret_cast<float(*)[kTileSlots]>(stage_smem);
+  unsigned char(*ring)[kStageThreads * kVec] =
+      reinterpret_cast<unsigned char(*)[kStageThreads * kVec]>(stage_smem + sizeof(float) * 4 * kTileSlots);
   const int t = blockIdx.x;
   const int tid = threadIdx.x;
   const int eb = __ldg(a.tile_ebase + t), ne = __ldg(a.tile_ebase + t + 1) - eb;
@@ -299,9 +308,27 @@ __global__ void __launch_bounds__(kStageThreads) k_stage_ring(StageArgs a) {
 }
 
 template <int DT, bool NORM>
-void launch_v(const StageArgs& a, dim3 grid, bool vec, cudaStream_t s) {
-  if (vec) k_stage_ring<DT, NORM><<<grid, kStageThreads, 0, s>>>(a);
-  else k_stage<DT, NORM, false><<<grid, kStageThreads, 0, s>>>(a);
+cudaError_t launch_v(const StageArgs& a, dim3 grid, bool vec, cudaStream_t s) {
+  if (vec) {
+    constexpr size_t smem = ring_smem_bytes<DT>();
+    if (smem > 48 * 1024) {
+      // opt in once per device (the attribute only needs to be set before
+      // the first launch; later calls find it set)
+      static bool set[64] = {};
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+      if (!set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage_ring<DT, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        set[dev] = true;
+      }
+    }
+    k_stage_ring<DT, NORM><<<grid, kStageThreads, smem, s>>>(a);
+  } else {
+    k_stage<DT, NORM, false><<<grid, kStageThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -315,14 +342,11 @@ cudaError_t launch_stage(const StageArgs& a, int32_t dtype, bool has_norm, cudaS
   // or listed at 16-byte aligned addresses
   bool vec = a.cols % 4 == 0;
   if (!a.fptr) vec = vec && ((uintptr_t)a.frames % 16 == 0);
-  if (dtype == SEP_DTYPE_U16_JF) {
-    if (has_norm) launch_v<SEP_DTYPE_U16_JF, true>(a, grid, vec && !a.fptr, s);
-    else launch_v<SEP_DTYPE_U16_JF, false>(a, grid, vec && !a.fptr, s);
-  } else {
-    if (has_norm) launch_v<SEP_DTYPE_F32, true>(a, grid, vec && !a.fptr, s);
-    else launch_v<SEP_DTYPE_F32, false>(a, grid, vec && !a.fptr, s);
-  }
-  return cudaGetLastError();
+  if (dtype == SEP_DTYPE_U16_JF)
+    return has_norm ? launch_v<SEP_DTYPE_U16_JF, true>(a, grid, vec && !a.fptr, s)
+                    : launch_v<SEP_DTYPE_U16_JF, false>(a, grid, vec && !a.fptr, s);
+  return has_norm ? launch_v<SEP_DTYPE_F32, true>(a, grid, vec && !a.fptr, s)
+                  : launch_v<SEP_DTYPE_F32, false>(a, grid, vec && !a.fptr, s);
 }
 
 }  // namespace sep

@@ -245,7 +245,8 @@ std::string build_csr_host(const sep_geometry& gm, const uint8_t* mask, const fl
       int m = 0;
       for (int a = 0; a < s; ++a)
         for (int b = 0; b < s; ++b) sb[m++] = bin_index(radial(g, row, col, off[a], off[b]), lo, hi, B);
-      std::sort(sb, sb + m);
+      for (int x = 1; x < m; ++x)   // m <= 4: insertion sort
+        for (int y = x; y > 0 && sb[y - 1] > sb[y]; --y) std::swap(sb[y - 1], sb[y]);
       int32_t* eb = &pb[(size_t)i * maxe];
       uint8_t* ek = &pk[(size_t)i * maxe];
       int n = 0;

@@ -83,7 +83,7 @@ struct HostCsr {
   std::vector<int32_t> tile_sc;     // [nnz][2] (slot, pixel index in the tile or -1: padding), by tile
 };
 
-constexpr int kTileH = 32, kTileW = 32;   // staging tiles (rows x columns)
+constexpr int kTileH = 64, kTileW = 64;   // staging tiles (rows x columns)
 
 // Returns an empty string on success, else the reason.
 std::string build_csr_host(const sep_geometry& g, const uint8_t* mask, const float* norm, HostCsr* out);

@@ -112,7 +112,7 @@ def test_invalid_geometry_rejected(bad):
     assert e.value.status == B.SEP_ERR_ARG
 
 
-TILE = (32, 32)   # staging tile (rows, columns) of the library
+TILE = (64, 64)   # staging tile (rows, columns) of the library
 
 
 def compare_with_oracle(det, mask=None):
