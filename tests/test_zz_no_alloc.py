@@ -1,10 +1,10 @@
 """The allocation-free sparsification entry point, through the C ABI.
 
 sep_sparsify_noalloc serves callers that must not allocate device memory at
-call time (code recorded into a CUDA graph, real-time acquisition threads,
-fixed device-memory budgets): it runs sep_sparsify's kernels with scratch in
-a static device array. This file is collected last on purpose, so that a
-stop-at-first-failure run has already run every other test.
+call time (real-time acquisition threads, fixed device-memory budgets): it
+runs sep_sparsify's checks and kernels with scratch in a static device
+array. This file is collected last on purpose, so that a stop-at-first-
+failure run has already run every other test.
 """
 import numpy as np
 import pytest
@@ -77,3 +77,53 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch():
         B.sep_sparsify_noalloc(sep.ctx, sep.csr, None, fr, B.SEP_DTYPE_F32, F, sep.params, mean, mean, idx, val, 16,
                                nk)
     assert e.value.status == B.SEP_ERR_ARG and "static array" in str(e.value)
+
+
+def test_noalloc_allocates_nothing_where_sparsify_grows_its_scratch():
+    """Free device memory is unchanged across a call on a batch larger than
+    any the context has seen; sep_sparsify on the same batch grows the
+    context's scratch (so the measurement can see an allocation)."""
+    det = synth.det_config1()
+    sep = Separator.from_detector(det)
+    small, big = _frames(det, [1]), _frames(det, [1, 2, 3, 4, 5, 6, 7, 8] * 8)
+    cap = det.npix // 8
+
+    def outputs(F):
+        return (torch.empty((F, cap), dtype=torch.int32, device="cuda"),
+                torch.empty((F, cap), dtype=torch.float32, device="cuda"),
+                torch.empty((F,), dtype=torch.int32, device="cuda"))
+
+    ic_s, ic_b = sep.integrate_clip(small), sep.integrate_clip(big)
+    o_s, o_b = outputs(small.shape[0]), outputs(big.shape[0])
+    # first call: the library's module and its static array are loaded
+    B.sep_sparsify_noalloc(sep.ctx, sep.csr, None, small, B.SEP_DTYPE_F32, small.shape[0], sep.params,
+                           ic_s["mean"], ic_s["sigma"], *o_s[:2], cap, o_s[2])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    B.sep_sparsify_noalloc(sep.ctx, sep.csr, None, big, B.SEP_DTYPE_F32, big.shape[0], sep.params,
+                           ic_b["mean"], ic_b["sigma"], *o_b[:2], cap, o_b[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    B.sep_sparsify(sep.ctx, sep.csr, None, big, B.SEP_DTYPE_F32, big.shape[0], sep.params, ic_b["mean"],
+                   ic_b["sigma"], *o_b[:2], cap, o_b[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free0
+    assert sep.device_status() == 0
+
+
+def test_noalloc_refuses_the_params_sparsify_refuses():
+    det = synth.det_config1()
+    sep = Separator.from_detector(det)
+    fr = _frames(det, [1])
+    ic = sep.integrate_clip(fr)
+    idx = torch.zeros((1, 16), dtype=torch.int32, device="cuda")
+    val = torch.zeros((1, 16), dtype=torch.float32, device="cuda")
+    nk = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    for field, bad in (("n_iter", -1), ("k_clip", 0.0), ("patch", 4), ("precision", 99)):
+        p = B.make_params(sep.params.n_iter, sep.params.k_clip, sep.params.k_pick, sep.params.patch,
+                          sep.params.min_count, sep.params.precision)
+        setattr(p, field, bad)
+        for fn in (B.sep_sparsify, B.sep_sparsify_noalloc):
+            with pytest.raises(SepError) as e:
+                fn(sep.ctx, sep.csr, None, fr, B.SEP_DTYPE_F32, 1, p, ic["mean"], ic["sigma"], idx, val, 16, nk)
+            assert e.value.status == B.SEP_ERR_ARG, (field, fn.__name__)
