@@ -104,10 +104,17 @@ def test_noalloc_allocates_nothing_where_sparsify_grows_its_scratch():
                            ic_b["mean"], ic_b["sigma"], *o_b[:2], cap, o_b[2])
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
-    B.sep_sparsify(sep.ctx, sep.csr, None, big, B.SEP_DTYPE_F32, big.shape[0], sep.params, ic_b["mean"],
-                   ic_b["sigma"], *o_b[:2], cap, o_b[2])
+    # the measurement sees an allocation: sep_sparsify on a batch whose
+    # scratch (8 MiB of bitmap) exceeds the driver's 2 MiB allocation granule
+    huge = big.repeat(16, 1)
+    ic_h = sep.integrate_clip(huge)
+    o_h = outputs(huge.shape[0])
     torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] < free0
+    free1 = torch.cuda.mem_get_info()[0]
+    B.sep_sparsify(sep.ctx, sep.csr, None, huge, B.SEP_DTYPE_F32, huge.shape[0], sep.params, ic_h["mean"],
+                   ic_h["sigma"], *o_h[:2], cap, o_h[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1
     assert sep.device_status() == 0
 
 
