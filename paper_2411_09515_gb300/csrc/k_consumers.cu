@@ -84,6 +84,7 @@ __global__ void k_unstage(const float* stage, int64_t stride, const int32_t* pos
 constexpr int kCompactThreads = 1024;
 constexpr int kWordsPerThread = 8;
 constexpr int64_t kTileWords = (int64_t)kCompactThreads * kWordsPerThread;   // bitmap words per CTA
+constexpr int kEmitList = 8192;   // kept pixels a CTA lists in shared memory at once
 
 // Phase 1 of the ordered compaction: kept pixels per tile of the bitmap.
 __global__ void __launch_bounds__(256) k_count_bits(const uint32_t* bitmap, int64_t words, int32_t* tile_cnt,
@@ -160,18 +161,36 @@ __global__ void __launch_bounds__(kCompactThreads) k_emit_kept(PixArgs p, const 
 #pragma unroll
   for (int j = 0; j < kWordsPerThread; ++j) cnt += __popc(wv[j]);
   int tile_total;
-  int64_t pos = base + block_exclusive_scan<kCompactThreads>(cnt, &tile_total, sh);
+  const int first = block_exclusive_scan<kCompactThreads>(cnt, &tile_total, sh);   // this thread's first, in the tile
+  // The tile's kept pixels go through a shared list, kEmitList at a time:
+  // each thread lists its own pixels at their ranks, then consecutive
+  // threads take consecutive entries, so the value loads of the whole list
+  // are in flight together and the stores are coalesced.
+  __shared__ int32_t lst[kEmitList];
+  const int64_t n_tile = (int64_t)tile_total < cap - base ? (int64_t)tile_total : cap - base;
+  for (int r0 = 0; r0 < n_tile; r0 += kEmitList) {
+    if (first < r0 + kEmitList && first + cnt > r0) {
+      int rank = first;
 #pragma unroll
-  for (int j = 0; j < kWordsPerThread; ++j) {
-    uint32_t m = wv[j];
-    while (m && pos < cap) {
-      const int bit = __ffs(m) - 1;
-      m &= m - 1u;
-      const int64_t i = (w0 + j) * 32 + bit;
-      idx[g * cap + pos] = (int32_t)i;
-      val[g * cap + pos] = value_of<DT, NORM>(p, frame, f, i);
-      ++pos;
+      for (int j = 0; j < kWordsPerThread; ++j) {
+        uint32_t m = wv[j];
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1u;
+          if (rank >= r0 && rank < r0 + kEmitList) lst[rank - r0] = (int32_t)((w0 + j) * 32 + bit);
+          ++rank;
+        }
+      }
     }
+    __syncthreads();
+    const int nr = (int)(n_tile - r0 < kEmitList ? n_tile - r0 : kEmitList);
+    for (int k = threadIdx.x; k < nr; k += kCompactThreads) {
+      const int64_t pos = base + r0 + k;
+      const int32_t i = lst[k];
+      idx[g * cap + pos] = i;
+      val[g * cap + pos] = value_of<DT, NORM>(p, frame, f, i);
+    }
+    __syncthreads();
   }
 }
 
