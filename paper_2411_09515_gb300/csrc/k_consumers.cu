@@ -346,6 +346,7 @@ __global__ void k_scatter_list(const int32_t* idx, const int32_t* n_kept, int64_
 constexpr int kPeakThreads = 256;
 constexpr int kPeakChunk = 256;          // kept entries per flag chunk (8 flag words)
 constexpr int kPeakCtasPerFrame = 64;
+constexpr int kPeakList = 4096;         // peaks a record CTA lists in shared memory at once
 
 __device__ __forceinline__ bool is_kept(const uint32_t* bm, int64_t j) { return (bm[j >> 5] >> (j & 31)) & 1u; }
 
@@ -439,49 +440,60 @@ __global__ void __launch_bounds__(1024) k_peak_emit(PixArgs p, int32_t nbins, co
   const int h = patch >> 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t* fl = flags + f * ((int64_t)n_chunks * 8);
-  // one warp per chunk; one lane per flag bit of a word
-  for (int c = warp; c < nch; c += 32) {
-    int64_t rank = chunk_base[c];
-    for (int wd = 0; wd < 8; ++wd) {
-      const uint32_t m = fl[c * 8 + wd];
-      if (m == 0) continue;
-      if ((m >> lane) & 1u) {
-        const int64_t pos = rank + __popc(m & ((1u << lane) - 1u));
-        const int64_t k = (int64_t)c * kPeakChunk + wd * 32 + lane;
-        const int64_t i = idx[g * kcap + k];
-        if (pos < pcap) {
-          const int r0 = (int)(i / p.cols), c0 = (int)(i - (int64_t)r0 * p.cols);
-          const int rlo = max(r0 - h, 0), rhi = min(r0 + h, p.rows - 1);
-          const int clo = max(c0 - h, 0), chi = min(c0 + h, p.cols - 1);
-          float I = 0.f, sy = 0.f, sx = 0.f, s2 = 0.f;
-          int nk = 0;
-          for (int r = rlo; r <= rhi; ++r)
-            for (int cc = clo; cc <= chi; ++cc) {
-              const int64_t j = (int64_t)r * p.cols + cc;
-              if (!is_kept(bm, j)) continue;
-              const int32_t bj = __ldg(p.bop + j);
-              const float vj = value_of<DT, NORM>(p, frame, f, j);
-              // background of the pixel's bin, or the profile at its centre
-              const float w = vj - (INTERP ? profile_at(mu, bj, p.ia, p.it, j, nbins) : __ldg(mu + bj));
-              const float s = INTERP ? profile_at(sd, bj, p.ia, p.it, j, nbins) : __ldg(sd + bj);
-              ++nk;
-              I += w;
-              sy += w * ((float)r + 0.5f);
-              sx += w * ((float)cc + 0.5f);
-              s2 += s * s;
-            }
-          sep_peak rec;
-          rec.idx = (int32_t)i;
-          rec.I = I;
-          rec.y = sy / I;
-          rec.x = sx / I;
-          rec.sigma = sqrtf(s2);
-          rec.npix = nk;
-          peaks[g * pcap + pos] = rec;
+  // the flagged entries go through a shared list, kPeakList at a time: a
+  // warp per chunk and a lane per flag bit list them at their ranks, then a
+  // thread per listed peak writes its record (all patches in flight together)
+  __shared__ int32_t plist[kPeakList];
+  const int64_t n_out = total < pcap ? total : pcap;
+  for (int64_t r0 = 0; r0 < n_out; r0 += kPeakList) {
+    for (int c = warp; c < nch; c += 32) {
+      int64_t rank = chunk_base[c];
+      if (rank >= r0 + kPeakList) continue;
+      for (int wd = 0; wd < 8; ++wd) {
+        const uint32_t m = fl[c * 8 + wd];
+        if (m == 0) continue;
+        if ((m >> lane) & 1u) {
+          const int64_t pos = rank + __popc(m & ((1u << lane) - 1u));
+          if (pos >= r0 && pos < r0 + kPeakList) plist[pos - r0] = c * kPeakChunk + wd * 32 + lane;
         }
+        rank += __popc(m);
       }
-      rank += __popc(m);
     }
+    __syncthreads();
+    const int nr = (int)(n_out - r0 < kPeakList ? n_out - r0 : kPeakList);
+    for (int t = threadIdx.x; t < nr; t += 1024) {
+      const int64_t pos = r0 + t;
+      const int64_t i = idx[g * kcap + plist[t]];
+      const int rr0 = (int)(i / p.cols), cc0 = (int)(i - (int64_t)rr0 * p.cols);
+      const int rlo = max(rr0 - h, 0), rhi = min(rr0 + h, p.rows - 1);
+      const int clo = max(cc0 - h, 0), chi = min(cc0 + h, p.cols - 1);
+      float I = 0.f, sy = 0.f, sx = 0.f, s2 = 0.f;
+      int nk = 0;
+      for (int r = rlo; r <= rhi; ++r)
+        for (int cc = clo; cc <= chi; ++cc) {
+          const int64_t j = (int64_t)r * p.cols + cc;
+          if (!is_kept(bm, j)) continue;
+          const int32_t bj = __ldg(p.bop + j);
+          const float vj = value_of<DT, NORM>(p, frame, f, j);
+          // background of the pixel's bin, or the profile at its centre
+          const float w = vj - (INTERP ? profile_at(mu, bj, p.ia, p.it, j, nbins) : __ldg(mu + bj));
+          const float sdv = INTERP ? profile_at(sd, bj, p.ia, p.it, j, nbins) : __ldg(sd + bj);
+          ++nk;
+          I += w;
+          sy += w * ((float)r + 0.5f);
+          sx += w * ((float)cc + 0.5f);
+          s2 += sdv * sdv;
+        }
+      sep_peak rec;
+      rec.idx = (int32_t)i;
+      rec.I = I;
+      rec.y = sy / I;
+      rec.x = sx / I;
+      rec.sigma = sqrtf(s2);
+      rec.npix = nk;
+      peaks[g * pcap + pos] = rec;
+    }
+    __syncthreads();
   }
 }
 
