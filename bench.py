@@ -220,7 +220,7 @@ def run_ours(args):
         sep.set_plan([int(x) for x in tpb.split(",")], [int(x) for x in thr.split(",") if x])
     elif not args.no_autotune:
         # the library's autotuner picks the clip schedule on a sample of the batch
-        tune_ms = sep.autotune(dev[: min(F, 128)], stream=stream)
+        tune_ms = sep.autotune(dev[: min(F, 256)], stream=stream)
     plan = sep.get_plan()
     # launches of our kernels per step: staging, one clip launch per size
     # class of the schedule (it also marks the kept pixels), two for the

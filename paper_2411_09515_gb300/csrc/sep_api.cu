@@ -1180,21 +1180,32 @@ sep_status sep_autotune(sep_ctx* ctx, sep_csr* csr, const sep_calib* calib, cons
   }
   sep::ClipArgs base = clip_args(ctx, csr, ctx->d_stage, n_frames, params, d_out, d_out + per,
                                  reinterpret_cast<int32_t*>(d_out + 2 * per), nullptr, nullptr, nullptr);
+  // the trials mark kept pixels into the context's bitmap, as a batch does
+  // (its contents are scratch here)
+  const int64_t words = bitmap_words(csr->npix);
+  if (!params->interpolate && ensure_scratch(ctx, words * n_frames, 0) == SEP_OK) {
+    base.bitmap = ctx->d_bitmap;
+    base.words = words;
+  }
   for (size_t i = 0; i < cands.size(); ++i) {
     const Cand& c = cands[i];
     if ((st = make_plan(ctx, csr, c.nc, c.t, c.b)) != SEP_OK) break;
     cudaError_t e = enqueue_clip(ctx, csr, base, params->precision, 0, s);   // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = enqueue_clip(ctx, csr, base, params->precision, 2, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    // the fastest of three timed runs
+    float ms = 1e30f;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = enqueue_clip(ctx, csr, base, params->precision, 2, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e == cudaSuccess) ms = std::min(ms, t);
+    }
     if (e != cudaSuccess) {
       st = cuda_fail(ctx, e, "autotune trial");
       break;
     }
-    ms *= 0.5f;
     if (ms < best) {
       best = ms;
       best_i = (int)i;
