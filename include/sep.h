@@ -194,9 +194,10 @@ sep_status sep_get_device_status(sep_ctx* ctx, sep_stream stream, int32_t* statu
  *  norm_host: rows*cols floats, the normalisation of Eq. 1 (denominator);
  *             may be NULL (= 1 everywhere). Must be > 0 on valid pixels.
  * Rows of the matrix are bins. Within a row, entries are grouped by
- * coefficient (largest first, then weight-0 entries), each group padded to
- * a multiple of 4 entries and ordered by staging position (see
- * sep_csr_staging). Every valid
+ * coefficient (largest first, then weight-0 entries) and ordered by staging
+ * position (see sep_csr_staging); the entries of one staging tile form a
+ * run, padded (col -1, coefficient 0) to a multiple of 8 entries, so rows
+ * and groups hold multiples of 8 entries. Every valid
  * pixel also gets its centre bin (the bin its threshold is taken from in
  * sparsification, Section 3); where that bin has no coefficient of the
  * pixel, an entry of weight 0 is added for it.

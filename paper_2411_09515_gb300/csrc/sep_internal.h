@@ -58,7 +58,7 @@ constexpr uint32_t kPad = 1u << 29;
 struct HostCsr {
   int32_t rows = 0, cols = 0, nbins = 0, split = 1;
   double lo = 0, hi = 0;
-  std::vector<int32_t> rowptr;   // [nbins + 1], multiples of 4
+  std::vector<int32_t> rowptr;   // [nbins + 1], multiples of 8
   std::vector<int32_t> grp;      // [nbins][4]: end of coefficient class 0..3 within the row
   std::vector<uint32_t> ent;     // [nnz] packed
   std::vector<float> coef;       // [nnz] c_{i,r} (0 for centre-only entries)
