@@ -19,7 +19,7 @@
 //   bits 25..26  k - 1 where k / split^2 is the coefficient c_{i,r} (k = 1..4)
 //   bit  27      the entry's bin is the pixel's centre bin (threshold bin)
 //   bit  28      zero coefficient: the entry exists only to carry bit 27
-//   bit  29      padding (no pixel): groups are padded to 4 entries
+//   bit  29      padding (no pixel): per-tile runs are padded to 8 entries
 namespace sep {
 // Restores the calling thread's current device when a C-ABI entry point
 // returns: entry points select their context's device for their own calls
