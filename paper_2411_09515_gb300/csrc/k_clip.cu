@@ -83,9 +83,9 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float so, float co)
 // mean's own scale.
 __device__ __forceinline__ float choose_shift(float mu, float sd) { return fabsf(mu) <= 2.0f * sd ? 0.0f : mu; }
 
-// State shared by the CTA between passes (written by one thread). The
-// mean is kept as an unevaluated FP32 pair mu_hi + mu_lo (FP64MERGE keeps a
-// double).
+// State of an item's clip loop (every lane of its warp holds the same
+// copy, evaluated from bit-identical totals). The mean is kept as an
+// unevaluated FP32 pair mu_hi + mu_lo (FP64MERGE keeps a double).
 struct Bcast {
   double mu_d, sd_d;   // FP64MERGE
   float mu_hi, mu_lo, sd;
@@ -109,7 +109,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ float round_up_pair(float hi, float lo) { return lo > 0.0f ? nextafterf(hi, INFINITY) : hi; }
 __device__ __forceinline__ float round_dn_pair(float hi, float lo) { return lo < 0.0f ? nextafterf(hi, -INFINITY) : hi; }
 
-// Mean and deviation of one set from its shifted sums, one thread:
+// Mean and deviation of one set from its shifted sums (each lane of the
+// item's warp, on the same totals):
 //   mu = K + A1 / Omega,  VV = B2 - 2 (mu - K) B1 + (mu - K)^2 OO,  sd = sqrt(VV / OO)
 // Sums arrive as FP32 pairs (value = hi + lo). The divisions act on a small
 // correction and on a ratio, where FP32 is exact to ~1e-7 relative; the
@@ -283,7 +284,7 @@ __device__ __forceinline__ void clip_step(Bcast& st, float n_set, const float (&
   st.Kf = choose_shift(st.mu_hi, st.sd);
 }
 
-// Lane 0 of warp 0: a pass's totals as (count, Omega, A1, OO, B1, B2) pairs.
+// A pass's totals as (count, Omega, A1, OO, B1, B2) pairs (every lane).
 template <int MODE>
 __device__ __forceinline__ void unpack_totals(const float* th, const float* tl, float& n_set, float (&h)[6],
                                               float (&l)[6]) {
@@ -313,9 +314,8 @@ __device__ __forceinline__ void unpack_totals(const float* th, const float* tl, 
 }
 
 // ---------------------------------------------------------------------------
-// Clip by tail replay, one warp per bin and frame (the default kernel; the
-// surrogate variants above keep full passes of a whole CTA over a copy of
-// the row's values in shared memory).
+// Clip by tail replay, one warp per bin and frame (the plain path and the
+// surrogate's record and inference variants).
 //
 // Every set of the clip loop is a value interval and the intervals are
 // nested (Eq. 19 is cumulative). An interval C = [cLo, cHi] that lies inside
