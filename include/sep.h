@@ -58,16 +58,18 @@ typedef int32_t sep_status;
 #define SEP_DTYPE_F32     0   /* float32 corrected signal (photons) per pixel */
 #define SEP_DTYPE_U16_JF  1   /* raw Jungfrau word: 2 gain bits (15:14) + 14-bit ADC */
 
-/* Precision of the per-bin moments (Section 2.2's reductions). Per-thread
- * sums are FP32 over a few dozen entries about a shift near the mean; the
- * modes differ in how partial sums are merged and the moments finalised:
+/* Precision of the per-bin moments (Section 2.2's reductions). One warp
+ * owns a bin and frame; each lane sums its share of the row in FP32 about a
+ * shift near the mean; the modes differ in how the lanes' sums are merged
+ * and the moments finalised:
  * PLAIN:     plain FP32 merges and finalisation.
- * KAHAN:     Kahan-compensated per-thread sums, error-free FP32 pair merges,
+ * KAHAN:     Kahan-compensated per-lane sums, error-free FP32 pair merges,
  *            double-word (FP32 pair) finalisation.
- * FP64MERGE: FP64 cross-warp merge and FP64 finalisation on one thread.
- * DWORD:     plain per-thread sums, error-free FP32 pair ("double-word")
- *            cross-warp merge and finalisation, no FP64 instruction (the
- *            default: FP64 is a small fraction of the FP32 rate on GB300).
+ * FP64MERGE: FP64 merge across the warp and FP64 finalisation.
+ * DWORD:     plain per-lane sums, error-free FP32 pair ("double-word")
+ *            merge across the warp and finalisation, no FP64 instruction
+ *            (the default: FP64 is a small fraction of the FP32 rate on
+ *            GB300).
  * Except in PLAIN, clip bounds and the sparsification threshold are rounded
  * outward-exact, so a float value is compared with the extended bound. */
 #define SEP_PREC_PLAIN     0
