@@ -677,12 +677,15 @@ def mixed_eval(n_frames, steps, warmup, kcap, pcap):
     seps = [Separator.from_detector(d, mask=m, context=ctx) for d, m in zip(dets, masks)]
     frames = []
     per = {0: [], 1: [], 2: []}
+    # frames generated on the GPU (the host generator's model and streams)
+    masks_d = [torch.from_numpy(np.ascontiguousarray(m, np.uint8)).cuda() for m in masks]
     for g, d in enumerate(pattern):
         spec = synth.spec_mixed(seed=1000 + g, hit_rate=float(rng.uniform(0.1, 0.5)))
-        fr = synth.frames(dets[d], spec, g, 1, mask=masks[d])[0][0]
-        t = torch.from_numpy(fr).cuda()
+        t = torch.empty(dets[d].npix, dtype=torch.float32, device="cuda")
+        synth.frames_gpu(dets[d], spec, g, 1, t, mask_dev=masks_d[d])
         frames.append((d, t))
         per[d].append(t)
+    torch.cuda.synchronize()
     tuned = {}
     for d in range(3):
         sample = torch.stack(per[d][:8])
@@ -779,7 +782,7 @@ def main():
     ap.add_argument("--chunk-frames", type=int, default=64)
     ap.add_argument("--surrogate-train-frames", type=int, default=100000)
     ap.add_argument("--surrogate-eval-frames", type=int, default=1024)
-    ap.add_argument("--mixed-frames", type=int, default=24)
+    ap.add_argument("--mixed-frames", type=int, default=96)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["plain", "kahan", "fp64merge", "dword"], default="dword")
     ap.add_argument("--workload", choices=["jf4m", "mixed"], default="jf4m")
