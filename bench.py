@@ -365,7 +365,7 @@ def run_ours(args):
                     **e2e_leg},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
-            "cpu_baseline": cpu,
+            "cpu_baseline": {k: v for k, v in cpu.items() if k != "precision"} if cpu else None,
             # each precision mode's error against the FP64 oracle on the same frames
             "precision": cpu.get("precision") if cpu else None,
             "surrogate": sur,
