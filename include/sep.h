@@ -24,7 +24,10 @@
  *    current CUDA device as they found it.
  *  - The library never exits, aborts or traps.
  *  - Not thread-safe per context: calls on one sep_ctx must not overlap in
- *    host threads.
+ *    host threads, and their device work must not overlap either (the
+ *    context's scratch, staging buffer and work-queue counters serve one
+ *    call at a time): issue a context's calls on one stream, or order the
+ *    streams with events.
  */
 #ifndef SEP_H_
 #define SEP_H_

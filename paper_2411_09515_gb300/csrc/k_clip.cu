@@ -901,23 +901,6 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
     __syncthreads();
   }
 
-  const int b = a.bin_list ? __ldg(a.bin_list + blockIdx.x) : (int)blockIdx.x;
-  const int f0 = blockIdx.y * a.frames_per_cta;
-  const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
-  const int r0 = __ldg(a.rowptr + b);
-  const int n = __ldg(a.rowptr + b + 1) - r0;      // multiple of 4
-  const int nq = n >> 2;
-  int ge[4];   // end of coefficient class 0..3 in the row; weight-0 carriers follow
-#pragma unroll
-  for (int c = 0; c < 4; ++c) ge[c] = __ldg(a.grp + 4 * b + c);
-
-  if (MODE == MODE_ENTRY) {
-    for (int e = threadIdx.x; e < n; e += 32 * kWarps) {
-      const uint32_t u = __ldg(a.ent + r0 + e);
-      wts[e] = (u & (kZero | kPad)) ? 0.0f : __ldg(a.w + r0 + e);
-    }
-    __syncthreads();
-  }
   // optional counters (added by lane 0 as they occur): items, pass B
   // scans, overflows, replay steps, tail entries listed, items marked from
   // the tail, full passes
@@ -926,178 +909,216 @@ __global__ void __launch_bounds__(32 * kWarps, kWarpsPerSM / kWarps) k_clip_warp
   };
   unsigned long long su[2] = {0, 0};   // surrogate: items whose predicted core held / that re-placed it
 
-  for (int f = f0 + warp; f < f1; f += kWarps) {
-    // this item's values: entry e of the row at slot r0 + e of the staged frame
-    const Row row{reinterpret_cast<const float4*>(a.stage + (int64_t)f * a.npos + r0)};
-    const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
-    stat(0, 1);
-    // ------------- pass A: where to place the core -------------
-    float cLo, cHi, K;
-    float pLo = 0.0f, pHi = 0.0f, pK = 0.0f;   // SURR 2: the plain placement, for a retry
-    float feat[kIn], m1 = 0.0f, s1 = 0.0f;
-    (void)feat;
-    {
-      float ss[NF], cz[NF];
-      uint32_t ci[NI];
-      // (rows of 2048 entries and more: every 4th group of 4, 512 and more:
-      // every 2nd)
-      const int step = nq >= 512 ? 4 : (nq >= 128 ? 2 : 1);
-      lane_full_sums<MODE>(row, wts, ge, lane, step, ss, ci);
-#pragma unroll
-      for (int v = 0; v < NF; ++v) cz[v] = 0.0f;
-      float n_set, h[6], l[6], lo, hi, mu, sd;
-      warp_totals<MODE, SEP_PREC_PLAIN>(ss, cz, ci, n_set, h, l);
-      approx_interval(n_set * (float)step, h, a.k_clip, a.cutoff, a.error_model, a.dark_var, lo, hi, mu, sd);
-      const float mg = __fmul_rn(kCoreMargin, sd);
-      cLo = __fadd_rn(lo, mg);
-      cHi = __fsub_rn(hi, mg);
-      K = choose_shift(mu, sd);
-      if (SURR != 0) {
-        m1 = mu;
-        s1 = sd;
-        sample_features<MODE>(row, wts, ge, lane, step, n_set, h[0], m1, s1, feat);
-      }
-      if (SURR == 2) {
-        // the predicted final interval, and the core half a deviation inside it
-        pLo = cLo;
-        pHi = cHi;
-        pK = K;
-        float u0, u1;
-        warp_mlp(w_s, nm_s, feat, lane, u0, u1);
-        const float mh = fmaf(s1, u0, m1), sh = s1 * expf(fminf(u1, 20.0f));
-        if (s1 > 0.0f && sh > 0.0f && fabsf(mh) <= FLT_MAX && sh <= FLT_MAX) {
-          const float half = __fmul_rn(a.k_clip, sh), mgs = __fmul_rn(kSurrMargin, sh);
-          cLo = __fadd_rn(__fsub_rn(mh, half), mgs);
-          cHi = __fsub_rn(__fadd_rn(mh, half), mgs);
-        }
-      }
+  // Units of work: a bin of this launch (in the launch's order, longest rows
+  // first) and a group of frames_per_cta frames, x fastest. A persistent
+  // launch (a.queue set) sizes its grid to the resident CTAs and every CTA
+  // takes the next unit from the queue counter until none is left; else
+  // CTA (x, y) runs unit y * gridDim.x + x alone.
+  __shared__ int unit_s;
+  for (int it = 0;; ++it) {
+    int unit;
+    if (a.queue) {
+      if (threadIdx.x == 0) unit_s = atomicAdd(a.queue, 1);
+      __syncthreads();
+      unit = unit_s;
+    } else {
+      unit = it == 0 ? (int)(blockIdx.y * gridDim.x + blockIdx.x) : a.units;
     }
-    // ------------- the loop of Eq. 19: replay on core + tail, or full passes -------------
-    Bcast st;
-    st.Ln = -FLT_MAX;
-    st.Hn = FLT_MAX;
-    st.L = -FLT_MAX;
-    st.H = FLT_MAX;
-    st.n_cur = -1.0f;
-    st.steps = -1;
-    st.done = 0;
-    st.Kf = K;
-    bool ovf = false, scan = true, retried = SURR != 2;
-    int m = 0, scans = 0;
-    float cn = 0.0f, ch[6], cl[6];
-    for (;;) {
-      const float Ln = st.Ln, Hn = st.Hn;
-      if (scan) {
-        // pass B: the core's sums and the tail, for the core placed last
-        float ss[NF], cc[NF];
+    if (unit >= a.units) break;
+    const int ux = unit % a.units_x;
+    const int b = a.bin_list ? __ldg(a.bin_list + ux) : ux;
+    const int f0 = (unit / a.units_x) * a.frames_per_cta;
+    const int f1 = min(f0 + a.frames_per_cta, a.n_frames);
+    const int r0 = __ldg(a.rowptr + b);
+    const int n = __ldg(a.rowptr + b + 1) - r0;      // multiple of 4
+    const int nq = n >> 2;
+    int ge[4];   // end of coefficient class 0..3 in the row; weight-0 carriers follow
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ge[c] = __ldg(a.grp + 4 * b + c);
+
+    if (MODE == MODE_ENTRY) {
+      for (int e = threadIdx.x; e < n; e += 32 * kWarps) {
+        const uint32_t u = __ldg(a.ent + r0 + e);
+        wts[e] = (u & (kZero | kPad)) ? 0.0f : __ldg(a.w + r0 + e);
+      }
+      __syncthreads();
+    }
+
+    for (int f = f0 + warp; f < f1; f += kWarps) {
+      // this item's values: entry e of the row at slot r0 + e of the staged frame
+      const Row row{reinterpret_cast<const float4*>(a.stage + (int64_t)f * a.npos + r0)};
+      const int64_t o = (a.orow ? a.orow[f] : (int64_t)f * a.nbins) + b;
+      stat(0, 1);
+      // ------------- pass A: where to place the core -------------
+      float cLo, cHi, K;
+      float pLo = 0.0f, pHi = 0.0f, pK = 0.0f;   // SURR 2: the plain placement, for a retry
+      float feat[kIn], m1 = 0.0f, s1 = 0.0f;
+      (void)feat;
+      {
+        float ss[NF], cz[NF];
         uint32_t ci[NI];
-        const bool fit =
-            lane_core_sums<MODE, KAHAN>(row, wts, ge, lane, cLo, cHi, K, tail, a.tcap, m, ss, cc, ci);
-        ovf = __any_sync(0xffffffffu, !fit);
-        ++scans;
-        if (a.clip_stats) {
-          const unsigned listed = __reduce_add_sync(0xffffffffu, (unsigned)m);
-          stat(1, 1);
-          stat(2, ovf ? 1 : 0);
-          stat(4, listed);
+        // (rows of 2048 entries and more: every 4th group of 4, 512 and more:
+        // every 2nd)
+        const int step = nq >= 512 ? 4 : (nq >= 128 ? 2 : 1);
+        lane_full_sums<MODE>(row, wts, ge, lane, step, ss, ci);
+#pragma unroll
+        for (int v = 0; v < NF; ++v) cz[v] = 0.0f;
+        float n_set, h[6], l[6], lo, hi, mu, sd;
+        warp_totals<MODE, SEP_PREC_PLAIN>(ss, cz, ci, n_set, h, l);
+        approx_interval(n_set * (float)step, h, a.k_clip, a.cutoff, a.error_model, a.dark_var, lo, hi, mu, sd);
+        const float mg = __fmul_rn(kCoreMargin, sd);
+        cLo = __fadd_rn(lo, mg);
+        cHi = __fsub_rn(hi, mg);
+        K = choose_shift(mu, sd);
+        if (SURR != 0) {
+          m1 = mu;
+          s1 = sd;
+          sample_features<MODE>(row, wts, ge, lane, step, n_set, h[0], m1, s1, feat);
         }
-        if (!retried) {
-          // first pass B only (the plain placement is inside the first
-          // interval, not necessarily inside a later one): when the
-          // predicted core left more entries outside it than the tail holds
-          // (a heavy-tailed bin), the plain placement instead
-          retried = true;
-          if (ovf) {
-            cLo = pLo;
-            cHi = pHi;
-            K = pK;
-            continue;
+        if (SURR == 2) {
+          // the predicted final interval, and the core half a deviation inside it
+          pLo = cLo;
+          pHi = cHi;
+          pK = K;
+          float u0, u1;
+          warp_mlp(w_s, nm_s, feat, lane, u0, u1);
+          const float mh = fmaf(s1, u0, m1), sh = s1 * expf(fminf(u1, 20.0f));
+          if (s1 > 0.0f && sh > 0.0f && fabsf(mh) <= FLT_MAX && sh <= FLT_MAX) {
+            const float half = __fmul_rn(a.k_clip, sh), mgs = __fmul_rn(kSurrMargin, sh);
+            cLo = __fadd_rn(__fsub_rn(mh, half), mgs);
+            cHi = __fsub_rn(__fadd_rn(mh, half), mgs);
           }
         }
-        if (!ovf) warp_totals<MODE, PREC>(ss, cc, ci, cn, ch, cl);
-        scan = false;
       }
-      float n_set, h[6], l[6], Kf;
-      if (!ovf) {
-        // a step of the replay: the core sums plus the tail inside [Ln, Hn]
-        float ts[5], tc[5], th[5], tl[5];
-        uint32_t tn;
-        lane_tail_sums<MODE, KAHAN>(tail, wts, m, Ln, Hn, K, ts, tc, tn);
-        warp_sum<5, TPREC>(ts, tc, th, tl);
-        tn = __reduce_add_sync(0xffffffffu, tn);
-        stat(3, 1);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          h[v] = ch[v];
-          l[v] = cl[v];
-          add_pair<PREC>(h[v], l[v], th[v], tl[v]);
+      // ------------- the loop of Eq. 19: replay on core + tail, or full passes -------------
+      Bcast st;
+      st.Ln = -FLT_MAX;
+      st.Hn = FLT_MAX;
+      st.L = -FLT_MAX;
+      st.H = FLT_MAX;
+      st.n_cur = -1.0f;
+      st.steps = -1;
+      st.done = 0;
+      st.Kf = K;
+      bool ovf = false, scan = true, retried = SURR != 2;
+      int m = 0, scans = 0;
+      float cn = 0.0f, ch[6], cl[6];
+      for (;;) {
+        const float Ln = st.Ln, Hn = st.Hn;
+        if (scan) {
+          // pass B: the core's sums and the tail, for the core placed last
+          float ss[NF], cc[NF];
+          uint32_t ci[NI];
+          const bool fit =
+              lane_core_sums<MODE, KAHAN>(row, wts, ge, lane, cLo, cHi, K, tail, a.tcap, m, ss, cc, ci);
+          ovf = __any_sync(0xffffffffu, !fit);
+          ++scans;
+          if (a.clip_stats) {
+            const unsigned listed = __reduce_add_sync(0xffffffffu, (unsigned)m);
+            stat(1, 1);
+            stat(2, ovf ? 1 : 0);
+            stat(4, listed);
+          }
+          if (!retried) {
+            // first pass B only (the plain placement is inside the first
+            // interval, not necessarily inside a later one): when the
+            // predicted core left more entries outside it than the tail holds
+            // (a heavy-tailed bin), the plain placement instead
+            retried = true;
+            if (ovf) {
+              cLo = pLo;
+              cHi = pHi;
+              K = pK;
+              continue;
+            }
+          }
+          if (!ovf) warp_totals<MODE, PREC>(ss, cc, ci, cn, ch, cl);
+          scan = false;
         }
-        h[5] = l[5] = 0.0f;
-        n_set = cn + (float)tn;
-        Kf = K;
-      } else {
-        // a tail overflowed: a full pass over [Ln, Hn]
-        float ss[NF], cc[NF];
-        uint32_t ci[NI];
-        Kf = st.Kf;
-        lane_range_sums<MODE, KAHAN>(row, wts, ge, lane, Ln, Hn, Kf, ss, cc, ci);
-        stat(6, 1);
-        warp_totals<MODE, PREC>(ss, cc, ci, n_set, h, l);
-      }
-      clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model, a.dark_var);
-      if (st.done) break;
-      if (!ovf && (cLo < st.Ln || cHi > st.Hn)) {
-        // the next interval cuts into the core: place it inside and scan again
-        const float mg = __fmul_rn(kCoreMargin, st.sd);
-        cLo = __fadd_rn(st.Ln, mg);
-        cHi = __fsub_rn(st.Hn, mg);
-        K = st.Kf;
-        scan = true;
-      }
-    }
-    if (lane == 0) {
-      a.mean[o] = st.mu_hi;
-      a.sigma[o] = st.sd;
-      a.count[o] = (int32_t)st.n_cur;
-      if (a.bounds) {
-        a.bounds[2 * o] = st.L;
-        a.bounds[2 * o + 1] = st.H;
-      }
-      if (a.iters) a.iters[o] = st.steps;
-      if (SURR == 1) {
-        // training record: the features and the result as normalised targets
-        for (int k = 0; k < kIn; ++k) a.rec_feat[o * kIn + k] = feat[k];
-        const bool ok = s1 > 0.0f && st.sd > 0.0f && st.n_cur >= 2.0f;
-        a.rec_target[o * 2] = ok ? (st.mu_hi - m1) / s1 : __int_as_float(0x7fc00000);
-        a.rec_target[o * 2 + 1] = ok ? logf(st.sd / s1) : __int_as_float(0x7fc00000);
-      }
-    }
-    if (SURR == 2) su[(scans == 1 && !ovf) ? 0 : 1] += 1;
-    // threshold of sparsification (Section 3) from the final state
-    const float thr = pick_threshold<PREC>(st, a.k_pick);
-    if (a.thr_out && lane == 0) a.thr_out[o] = thr;
-    if (a.bitmap) {
-      // kept pixels of this bin: its centre entries whose value exceeds the
-      // threshold (only kept pixels touch the pixel table and the bitmap)
-      uint32_t* bm = a.bitmap + (int64_t)f * a.words;
-      const int32_t* cp = a.cpix + r0;
-      // without an overflow and with thr at or above the core, no core entry
-      // exceeds thr: the lane's tail, then the weight-0 carriers of the row;
-      // else every entry (padding slots hold NaN, never above a threshold)
-      const bool from_tail = MODE != MODE_ENTRY && !ovf && thr >= cHi;
-      if (from_tail) {
-        stat(5, 1);
-        for (int k = 0; k < m; ++k)
-          if (__uint_as_float(tail[32 * k].x) > thr) mark_pixel(bm, cp, (int64_t)(tail[32 * k].y & 0xffffu));
-      }
-      scan_row(row, from_tail ? ge[3] >> 2 : 0, nq, lane, [&](const float4& v4, int q) {
-        const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+        float n_set, h[6], l[6], Kf;
+        if (!ovf) {
+          // a step of the replay: the core sums plus the tail inside [Ln, Hn]
+          float ts[5], tc[5], th[5], tl[5];
+          uint32_t tn;
+          lane_tail_sums<MODE, KAHAN>(tail, wts, m, Ln, Hn, K, ts, tc, tn);
+          warp_sum<5, TPREC>(ts, tc, th, tl);
+          tn = __reduce_add_sync(0xffffffffu, tn);
+          stat(3, 1);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (xs[j] > thr) mark_pixel(bm, cp, 4 * q + j);
-      });
+          for (int v = 0; v < 5; ++v) {
+            h[v] = ch[v];
+            l[v] = cl[v];
+            add_pair<PREC>(h[v], l[v], th[v], tl[v]);
+          }
+          h[5] = l[5] = 0.0f;
+          n_set = cn + (float)tn;
+          Kf = K;
+        } else {
+          // a tail overflowed: a full pass over [Ln, Hn]
+          float ss[NF], cc[NF];
+          uint32_t ci[NI];
+          Kf = st.Kf;
+          lane_range_sums<MODE, KAHAN>(row, wts, ge, lane, Ln, Hn, Kf, ss, cc, ci);
+          stat(6, 1);
+          warp_totals<MODE, PREC>(ss, cc, ci, n_set, h, l);
+        }
+        clip_step<PREC>(st, n_set, h, l, Kf, Ln, Hn, a.n_iter, a.k_clip, false, a.cutoff, a.error_model, a.dark_var);
+        if (st.done) break;
+        if (!ovf && (cLo < st.Ln || cHi > st.Hn)) {
+          // the next interval cuts into the core: place it inside and scan again
+          const float mg = __fmul_rn(kCoreMargin, st.sd);
+          cLo = __fadd_rn(st.Ln, mg);
+          cHi = __fsub_rn(st.Hn, mg);
+          K = st.Kf;
+          scan = true;
+        }
+      }
+      if (lane == 0) {
+        a.mean[o] = st.mu_hi;
+        a.sigma[o] = st.sd;
+        a.count[o] = (int32_t)st.n_cur;
+        if (a.bounds) {
+          a.bounds[2 * o] = st.L;
+          a.bounds[2 * o + 1] = st.H;
+        }
+        if (a.iters) a.iters[o] = st.steps;
+        if (SURR == 1) {
+          // training record: the features and the result as normalised targets
+          for (int k = 0; k < kIn; ++k) a.rec_feat[o * kIn + k] = feat[k];
+          const bool ok = s1 > 0.0f && st.sd > 0.0f && st.n_cur >= 2.0f;
+          a.rec_target[o * 2] = ok ? (st.mu_hi - m1) / s1 : __int_as_float(0x7fc00000);
+          a.rec_target[o * 2 + 1] = ok ? logf(st.sd / s1) : __int_as_float(0x7fc00000);
+        }
+      }
+      if (SURR == 2) su[(scans == 1 && !ovf) ? 0 : 1] += 1;
+      // threshold of sparsification (Section 3) from the final state
+      const float thr = pick_threshold<PREC>(st, a.k_pick);
+      if (a.thr_out && lane == 0) a.thr_out[o] = thr;
+      if (a.bitmap) {
+        // kept pixels of this bin: its centre entries whose value exceeds the
+        // threshold (only kept pixels touch the pixel table and the bitmap)
+        uint32_t* bm = a.bitmap + (int64_t)f * a.words;
+        const int32_t* cp = a.cpix + r0;
+        // without an overflow and with thr at or above the core, no core entry
+        // exceeds thr: the lane's tail, then the weight-0 carriers of the row;
+        // else every entry (padding slots hold NaN, never above a threshold)
+        const bool from_tail = MODE != MODE_ENTRY && !ovf && thr >= cHi;
+        if (from_tail) {
+          stat(5, 1);
+          for (int k = 0; k < m; ++k)
+            if (__uint_as_float(tail[32 * k].x) > thr) mark_pixel(bm, cp, (int64_t)(tail[32 * k].y & 0xffffu));
+        }
+        scan_row(row, from_tail ? ge[3] >> 2 : 0, nq, lane, [&](const float4& v4, int q) {
+          const float xs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (xs[j] > thr) mark_pixel(bm, cp, 4 * q + j);
+        });
+      }
+      __syncwarp();   // the tail is rewritten by the warp's next frame
     }
-    __syncwarp();   // the tail is rewritten by the warp's next frame
+    // the next unit rewrites unit_s and the shared row weights
+    __syncthreads();
   }
   if (SURR == 2 && a.surr_stats && lane == 0) {
     if (su[0]) atomicAdd(a.surr_stats, su[0]);
@@ -1119,6 +1140,19 @@ int smem_optin() {
   return cached[dev];
 }
 
+// Multiprocessors of the current device (cached).
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
 template <int MODE, int PREC, int kWarps, int SURR>
 cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   // shared memory: the weights of a row (per-entry weights only), then
@@ -1133,6 +1167,23 @@ cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
   a.tcap = (int32_t)tcap;
   const size_t smem = (size_t)(wbytes + kWarps * 256 * tcap + (SURR == 2 ? kNNorm * 4 + ((kNParams * 2 + 15) & ~15) : 0));
   auto k = k_clip_warp<MODE, PREC, kWarps, SURR>;
+  // resident CTAs per multiprocessor of this instance at this shared-memory
+  // size, cached per device (the first query comes before any capture: the
+  // attribute pass below asks it). A stale or missing value changes only the
+  // grid of a persistent launch, never its results (0: not persistent).
+  auto resident = [&]() -> int {
+    static int occ_smem[64][8], occ_val[64][8] = {}, occ_next[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    for (int i = 0; i < 8; ++i)
+      if (occ_val[dev][i] > 0 && occ_smem[dev][i] == (int)smem) return occ_val[dev][i];
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, 32 * kWarps, smem) != cudaSuccess) v = 0;
+    const int i = occ_next[dev]++ & 7;
+    occ_smem[dev][i] = (int)smem;
+    occ_val[dev][i] = v;
+    return v;
+  };
   if (mode != 2) {
     // the attribute only grows: size classes sharing this instance may set
     // it in any order before a capture
@@ -1144,9 +1195,27 @@ cudaError_t launch_warp_t(ClipArgs a, int n_ctas, int mode, cudaStream_t s) {
       if (e != cudaSuccess) return e;
       attr[dev] = (int)smem;
     }
-    if (mode == 1) return cudaSuccess;
+    if (mode == 1) {
+      (void)resident();
+      return cudaSuccess;
+    }
   }
-  dim3 grid(n_ctas, (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta);
+  const int gy = (a.n_frames + a.frames_per_cta - 1) / a.frames_per_cta;
+  a.units_x = n_ctas;
+  a.units = n_ctas * gy;
+  dim3 grid(n_ctas, gy);
+  if (a.queue) {
+    // persistent: as many CTAs as stay resident, while the units outnumber them
+    const int per_sm = resident();
+    const int64_t slots = (int64_t)sm_count() * per_sm;
+    if (per_sm > 0 && slots < a.units) {
+      grid = dim3((unsigned)slots, 1);
+      cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s);
+      if (e != cudaSuccess) return e;
+    } else {
+      a.queue = nullptr;
+    }
+  }
   k<<<grid, 32 * kWarps, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -311,7 +311,10 @@ cudaError_t enqueue_stage(sep_ctx* ctx, const sep_csr* csr, const sep_calib* cal
 cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int32_t precision, int mode,
                          cudaStream_t s, bool allow_fork = true) {
   const bool split = csr->h.split > 1;
+  // each launch its own work-queue counter (launches of a call run concurrently)
+  auto take_queue = [&]() { return ctx->d_queue + (ctx->queue_next++ % sep_ctx::kQueueSlots); };
   if (csr->plan.empty()) {
+    a.queue = take_queue();
     a.bin_list = nullptr;
     a.cap = std::max(csr->h.max_row, 4);
     a.frames_per_cta = frames_per_cta(ctx, a.n_frames, csr->h.nbins, kDefaultTpb);
@@ -320,6 +323,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
   const int nc = (int)csr->plan.size();
   if (nc == 1 || mode == 1 || !allow_fork) {
     for (const auto& k : csr->plan) {
+      a.queue = take_queue();
       a.bin_list = k.d_bins;
       a.cap = k.cap;
       a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins, k.tpb);
@@ -333,6 +337,7 @@ cudaError_t enqueue_clip(sep_ctx* ctx, const sep_csr* csr, sep::ClipArgs a, int3
     const auto& k = csr->plan[i];
     cudaStream_t si = i == 0 ? s : ctx->aux[i];
     if (i > 0) e = cudaStreamWaitEvent(si, ctx->ev_fork, 0);
+    a.queue = take_queue();
     a.bin_list = k.d_bins;
     a.cap = k.cap;
     a.frames_per_cta = frames_per_cta(ctx, a.n_frames, k.n_bins, k.tpb);
@@ -375,6 +380,8 @@ sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->d_surr, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_clip_stats, SEP_CLIP_STATS * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_clip_stats, 0, SEP_CLIP_STATS * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_queue, sep_ctx::kQueueSlots * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_queue, 0, sep_ctx::kQueueSlots * sizeof(int32_t));
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
@@ -382,6 +389,7 @@ sep_status sep_ctx_create(int32_t device, sep_ctx** out) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_surr) cudaFree(c->d_surr);
     if (c->d_clip_stats) cudaFree(c->d_clip_stats);
+    if (c->d_queue) cudaFree(c->d_queue);
     delete c;
     return SEP_ERR_CUDA;
   }
@@ -399,6 +407,7 @@ void sep_ctx_destroy(sep_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_surr) cudaFree(ctx->d_surr);
   if (ctx->d_clip_stats) cudaFree(ctx->d_clip_stats);
+  if (ctx->d_queue) cudaFree(ctx->d_queue);
   if (ctx->d_bitmap) cudaFree(ctx->d_bitmap);
   if (ctx->d_thr) cudaFree(ctx->d_thr);
   if (ctx->d_aux) cudaFree(ctx->d_aux);

@@ -132,6 +132,11 @@ struct ClipArgs {
   const float* mlp_norm = nullptr;
   unsigned long long* surr_stats = nullptr;   // [2]: bins whose predicted core held, bins that re-placed it
   int32_t tcap = 0;                    // tail slots per thread of the tail-replay kernel (set at launch)
+  // persistent launch: each CTA takes units (a bin of the launch and a group
+  // of frames_per_cta frames) from the counter *queue, which the launch
+  // zeroes, until none is left; null: one unit per CTA
+  int32_t* queue = nullptr;
+  int32_t units_x = 0, units = 0;      // bins of the launch, units in all (set at launch)
   unsigned long long* clip_stats = nullptr;   // [SEP_CLIP_STATS] counters of the tail replay, or null
 };
 
@@ -258,6 +263,11 @@ struct sep_ctx {
   size_t desc_len = 0;
   unsigned long long* d_surr = nullptr;   // surrogate counters: settled, fell back
   unsigned long long* d_clip_stats = nullptr;   // [SEP_CLIP_STATS] tail-replay counters
+  // work-queue counters of the persistent clip launches, taken in turn (one
+  // per launch in flight: a call forks at most 4 x 4 clip launches)
+  static constexpr int kQueueSlots = 64;
+  int32_t* d_queue = nullptr;
+  uint32_t queue_next = 0;
   bool clip_stats_on = false;                   // clip launches count into d_clip_stats
   float* d_stage = nullptr;    // staged pixel values of the batch in flight
   size_t stage_len = 0;
