@@ -149,25 +149,57 @@ def algorithmic_bytes_path(F, npix, nnz, nbins, kept_per_frame, peaks_per_frame)
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
 
 
-CLIP_SOURCES = ["k_stage.cu", "k_clip.cu"]
+CLIP_SOURCES = ["k_stage.cu", "k_clip.cu", "sep_internal.h", "sep_device.cuh"]
+
+
+def strip_comments(src: str) -> str:
+    """C++ source without its comments, runs of white space made one space
+    (string and character literals kept as written)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == "/" and src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif c == "/" and src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def source_fingerprint(names=CLIP_SOURCES):
+    """SHA-256 of the staging and clip kernel sources without comments: the
+    code the traffic capture measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2411_09515_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(strip_comments(f.read()).encode())
+        h.update(b"\0")
+    return h.hexdigest()
 
 
 def measured_traffic(F):
     """DRAM bytes (read + write) of k_stage_ring + k_clip_warp per launch of F
     frames, from the ncu capture recorded in profiles/roofline_traffic.json,
-    scaled from its frame count; None when absent or when the kernel
-    sources changed since the capture."""
-    import hashlib
+    scaled from its frame count; None when absent or when the kernels' code
+    changed since the capture."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    h = hashlib.sha256()
-    for name in CLIP_SOURCES:
-        with open(os.path.join(ROOT, "paper_2411_09515_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    if rec.get("sources_sha256") != h.hexdigest():
+    if rec.get("sources_sha256") != source_fingerprint():
         return None
     return int(rec["bytes_per_frame"] * F)
 

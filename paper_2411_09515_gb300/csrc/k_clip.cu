@@ -6,7 +6,8 @@
 // values are one contiguous run), accumulates the weighted moments
 // (Eqs. 8-13) and runs the clip loop of Eq. 19 (Section 2.4) by tail replay
 // (described with the kernel below). The warps of a CTA take other frames
-// of the same bin and never synchronise.
+// of the same bin and wait for one another only when the CTA takes its next
+// unit of work (a persistent launch draws units from a work-queue counter).
 //
 // Moments are accumulated about a shift K: with d = v - K, per set S
 //   Omega = sum w, A1 = sum w d, OO = sum w^2, B1 = sum w^2 d, B2 = sum w^2 d^2,
@@ -342,8 +343,8 @@ __device__ __forceinline__ void unpack_totals(const float* th, const float* tl, 
 // lives in shared memory, so many items fit an SM. Every total is a warp
 // butterfly, which leaves bit-identical totals on all lanes (addition, and
 // the error-free pair sum, are commutative), so every lane evaluates each
-// clip step itself: no lane waits for another and the CTA never
-// synchronises (its warps take other frames of the same bin).
+// clip step itself: no lane waits for another, and the warps of a CTA
+// (other frames of the same bin) meet only between units of work.
 constexpr float kCoreMargin = 1.0f;   // core margin inside the clip interval, in deviations
 constexpr int kLoadsAhead = 4;        // 16-byte loads in flight per lane in a scan of the row
 constexpr int kWarpsPerSM = 16;       // resident warps per SM the register budget is sized for

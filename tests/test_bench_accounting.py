@@ -34,3 +34,22 @@ def test_whole_path_bytes_per_frame():
     assert abs(got - want) < 1e-6
     # about 9.2-9.4 MB per frame at 512 frames: the raw frame dominates
     assert 9.2e6 < got < 9.4e6
+
+
+def test_traffic_record_follows_the_code_not_the_comments():
+    b = _bench()
+    code = 'int f(int x) { // twice\n  /* the "input" */ return x * 2; }\nconst char* s = "// kept /* too */";\n'
+    assert b.strip_comments(code) == 'int f(int x) { return x * 2; } const char* s = "// kept /* too */";'
+    # a comment or a blank line changes nothing, an operator does
+    assert b.strip_comments(code.replace("// twice", "// three times\n\n")) == b.strip_comments(code)
+    assert b.strip_comments(code.replace("x * 2", "x * 3")) != b.strip_comments(code)
+    assert b.strip_comments("a = '\\'' ; /* c */ b") == "a = '\\'' ; b"
+    # the recorded capture scales with the frames while its fingerprint is the code's
+    import json
+    with open(os.path.join(HERE, "..", "profiles", "roofline_traffic.json")) as f:
+        rec = json.load(f)
+    got = b.measured_traffic(512)
+    if rec["sources_sha256"] == b.source_fingerprint():
+        assert got == int(rec["bytes_per_frame"] * 512)
+    else:
+        assert got is None
