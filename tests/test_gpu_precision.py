@@ -7,7 +7,7 @@ the bins whose clip decisions are outside the 1e-5 band, kept-pixel
 mismatches outside the band, and the peak centroid error in pixels. The
 default mode must meet the parity tolerances; the others are reported.
 Set SEP_PRECISION_REPORT=path to write the numbers as JSON, and
-SEP_PRECISION_FRAMES to change the Jungfrau-4M study's frame count (8).
+SEP_PRECISION_FRAMES to change the Jungfrau-4M study's frame count (32).
 """
 import json
 import os
@@ -98,9 +98,9 @@ def test_precision_modes_small():
 
 def test_precision_modes_jf4m():
     """The study on Jungfrau-4M frames, every mode held to the parity
-    tolerance (8 frames by default; SEP_PRECISION_FRAMES=256 for the full
+    tolerance (32 frames by default; SEP_PRECISION_FRAMES=256 for the full
     study)."""
-    r = study(synth.det_jf4m(), int(os.environ.get("SEP_PRECISION_FRAMES", "8")))
+    r = study(synth.det_jf4m(), int(os.environ.get("SEP_PRECISION_FRAMES", "32")))
     _emit(r)
     assert r["gain_level_pixels"][1] > 0 and r["gain_level_pixels"][3] > 0
     for name in MODES:
